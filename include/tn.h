@@ -1,0 +1,222 @@
+/*
+ * tn.h -- C ABI of the sliced tensor-network contraction library for
+ * random-circuit sampling on one GB300 (sm_103a).
+ *
+ * Method (arXiv 2406.18889, "Leapfrogging Sycamore"):
+ *   - Sec. III "Composition of our algorithm": amplitudes of k groups of 2^l
+ *     correlated bitstrings are computed by contracting a fraction f of the
+ *     sliced sub-networks; the top-k strings by p(s) = |phi(s)|^2 / f are kept.
+ *   - Sec. III "Optimizing tensor contraction": slicing fixes the values of
+ *     chosen edges; the network is the sum of its sub-networks over all value
+ *     assignments; each sub-network is a sequence of pairwise contractions.
+ *   - Eq. (1): linear XEB of a selection.
+ *
+ * Conventions
+ *   - Every call returns a tn_status; TN_OK is 0.  On failure
+ *     tn_last_error() returns a message for the calling host thread.
+ *   - Arguments are validated before any device work is queued; an invalid
+ *     call leaves device memory untouched.
+ *   - Device pointers are caller-owned (the library never frees them).  The
+ *     plan owns only its own device copy of the network and its step table.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls queue work on it and return without synchronising,
+ *     except where a function says it synchronises.
+ *   - A plan is immutable after creation and may be shared by host threads;
+ *     concurrent calls must use distinct workspaces and output buffers.
+ *   - Complex numbers are interleaved (re, im); complex64 = 2 x float,
+ *     complex128 = 2 x double.
+ *   - Bit order: qubit 0 is the most significant bit of an n-bit index.
+ */
+#ifndef TN_H_
+#define TN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TN_OK = 0,
+  TN_ERR_INVALID_ARG = 1, /* bad pointer, size, id or descriptor */
+  TN_ERR_OOM = 2,         /* device or host allocation failed */
+  TN_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the code) */
+  TN_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  TN_ERR_UNSUPPORTED = 5, /* valid but not supported (e.g. a non power-of-two dim) */
+  TN_ERR_NUMERIC = 6      /* a NaN or infinity was detected */
+} tn_status;
+
+typedef enum {
+  TN_PREC_C64 = 0,  /* complex64 storage, FP32 complex multiply-add on CUDA cores */
+  TN_PREC_BF16 = 1, /* bf16 complex storage, real tensor-core GEMMs, FP32 accumulate */
+  TN_PREC_FP16 = 2  /* fp16 complex storage, real tensor-core GEMMs, FP32 accumulate */
+} tn_precision;
+
+/* tn_plan_options.flags */
+#define TN_FLAG_HOIST_INVARIANT 0x1u /* contract slice-independent subtrees once, at plan creation */
+#define TN_FLAG_NO_GRAPH 0x2u        /* launch kernels directly instead of replaying a CUDA graph */
+#define TN_FLAG_PLAN_ONLY 0x4u       /* host-side planning only: no device memory is touched and
+                                        contraction calls on the plan fail (for inspection) */
+
+typedef struct tn_plan_s* tn_plan_t;
+
+/*
+ * Host-side tensor network (paper Sec. III: gate tensors, initial states and
+ * projectors; all edges have power-of-two dimensions).
+ *   n_leaves, n_edges : counts (n_leaves >= 1, n_edges >= 1).
+ *   leaf_rank[n_leaves]: number of edges of each leaf (0..32).
+ *   leaf_edges        : concatenated edge ids, leaf-major; within a leaf the
+ *                       first edge is the slowest-varying axis of its data.
+ *   edge_dim[n_edges] : dimension of each edge (power of two, >= 2).
+ *   leaf_data         : host complex128, the leaves' elements concatenated in
+ *                       leaf order, each row-major in its leaf_edges order.
+ *                       Copied during tn_plan_create.
+ *   n_open, open_edges: output edges of one block; element j of a block packs
+ *                       them with open_edges[0] most significant.
+ *   block_edge        : the block (group) hyper-edge g, shared by every
+ *                       closed-qubit projector and kept to the output; -1 when
+ *                       there is a single block.
+ * Every edge other than open/block edges must appear in exactly two leaves.
+ */
+typedef struct {
+  int32_t n_leaves;
+  int32_t n_edges;
+  const int32_t* leaf_rank;
+  const int32_t* leaf_edges;
+  const int64_t* edge_dim;
+  const void* leaf_data;
+  int32_t n_open;
+  const int32_t* open_edges;
+  int32_t block_edge;
+} tn_network_desc;
+
+/*
+ * Contraction tree and slicing set (paper Sec. III: pairwise contraction
+ * path; sliced edges).
+ *   n_steps, pairs[2*n_steps]: SSA pairs -- leaf i has id i, step t creates
+ *                       id n_leaves + t; every id is consumed exactly once and
+ *                       the last step is the root (n_steps = n_leaves - 1).
+ *   n_sliced, sliced_edges: bit i of a slice id is the value of
+ *                       sliced_edges[i]; each must be a dimension-2 bond (two
+ *                       leaves, not an output edge).  0 <= n_sliced <= 62.
+ */
+typedef struct {
+  int32_t n_steps;
+  const int32_t* pairs;
+  int32_t n_sliced;
+  const int32_t* sliced_edges;
+} tn_tree_desc;
+
+/*
+ * prec            : arithmetic of the per-slice contractions (tn_precision).
+ * flags           : TN_FLAG_* bits.
+ * max_slice_batch : slices contracted together per launch sequence (power of
+ *                   two, 1..65536); the workspace scales with it.
+ * mem_cap_bytes   : reject the plan (TN_ERR_OOM) if the workspace exceeds this
+ *                   (0 = no cap).
+ */
+typedef struct {
+  int32_t prec;
+  uint32_t flags;
+  int32_t max_slice_batch;
+  int64_t mem_cap_bytes;
+} tn_plan_options;
+
+/*
+ * Build a plan: validates the network and tree, assigns every intermediate a
+ * memory layout (contracted dimensions of both operands in one order, free
+ * dimensions in the output's order, so most steps need no transpose), plans
+ * workspace offsets, and copies the leaves to the device in complex64.
+ * Synchronises `stream`.  *out is set only on success; destroy with
+ * tn_plan_destroy.
+ */
+tn_status tn_plan_create(const tn_network_desc* net, const tn_tree_desc* tree,
+                         const tn_plan_options* opt, void* stream, tn_plan_t* out);
+
+tn_status tn_plan_destroy(tn_plan_t plan);
+
+/*
+ * Cost model of one slice (paper Table I conventions):
+ *   useful_flops_per_slice : 8 * sum over per-slice steps of batch*M*N*K
+ *                            ("8 is the complex number product factor").
+ *   algo_bytes_per_slice   : sum over per-slice steps of the bytes of both
+ *                            operands and the result at the plan's precision.
+ *   peak_intermediate_bytes: largest single intermediate for one slice.
+ *   workspace_bytes        : device workspace tn_contract_slices needs.
+ * Any output pointer may be NULL.
+ */
+tn_status tn_plan_query(tn_plan_t plan, int64_t* useful_flops_per_slice,
+                        int64_t* algo_bytes_per_slice, int64_t* peak_intermediate_bytes,
+                        int64_t* workspace_bytes);
+
+/* Per-step description for profiling and tests: the step's GEMM shape and
+ * whether it runs once per slice batch (variant) or once per plan.  kinds[t]
+ * bit 0 = variant, bit 1 = needs an operand/output transpose. */
+tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64_t* m,
+                        int64_t* n, int64_t* k, int32_t* kinds, int32_t* n_steps_out);
+
+/*
+ * Contract the sub-networks `slice_ids[0..n_slices)` (host array; each id in
+ * [0, 2^n_sliced), duplicates allowed and counted twice) and add them into
+ * amps.  amps: device complex128 [G][2^l] (G = block edge dimension or 1);
+ * accumulate = 0 overwrites amps with the sum, 1 adds to it.  Each slice is
+ * computed in the plan's precision and summed across slices in FP64, in slice
+ * order within a batch and batch by batch (deterministic).  workspace: device,
+ * >= workspace_bytes of tn_plan_query, 256-byte aligned.  n_slices = 0 with
+ * accumulate = 0 zeroes amps.
+ */
+tn_status tn_contract_slices(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices,
+                             void* amps, int accumulate, void* workspace, size_t ws_bytes,
+                             void* stream);
+
+/*
+ * Several plans (e.g. many small circuits with uneven trees) in one call:
+ * plan p contracts slice_ids[p][0..n_slices[p]) into amps[p].  Plans run one
+ * after another on `stream` sharing `workspace` (size >= the largest
+ * workspace_bytes among them).
+ */
+tn_status tn_contract_slices_batched(const tn_plan_t* plans, int32_t n_plans,
+                                     const int64_t* const* slice_ids, const int64_t* n_slices,
+                                     void* const* amps, int accumulate, void* workspace,
+                                     size_t ws_bytes, void* stream);
+
+/*
+ * Top-k post-processing (paper Sec. III): p = (re*re + im*im) * inv_f in FP64
+ * (each product and the sum rounded separately, no fused multiply-add), then
+ * the k largest p ordered by (p descending, full index ascending).
+ *   amps          : device complex128 [G][B], B = 2^l.
+ *   global_mode   : 0 = k per block (outputs [G][k]); 1 = k over all G*B
+ *                   (outputs [k]).
+ *   block_base_idx: device int64 [G], the closed bits of each block as an
+ *                   n-bit index with every open bit 0.
+ *   open_bit_pos  : host int64 [l], bit position (0 = LSB) of open edge i
+ *                   (open edge 0 is the most significant bit of j).
+ *   out_idx, out_p: device int64 / double outputs.
+ * Constraints: 1 <= k <= B (per block) or k <= G*B (global), k <= 512,
+ * B <= 2^16.  A NaN probability makes the call return TN_ERR_NUMERIC after
+ * synchronising the stream.
+ */
+tn_status tn_topk_postprocess(const void* amps, int64_t G, int64_t B, int32_t k, double inv_f,
+                              int global_mode, const int64_t* block_base_idx,
+                              const int64_t* open_bit_pos, int32_t l, int64_t* out_idx,
+                              double* out_p, void* stream);
+
+/*
+ * Linear XEB, Eq. (1): 2^n_qubits / n_sel * sum(q) - 1, the sum in FP64 in a
+ * fixed order.  q: device double [n_sel] (ideal probabilities of the selected
+ * strings).  Synchronises `stream` and writes *out_xeb (host).
+ */
+tn_status tn_xeb(const double* q, int64_t n_sel, int32_t n_qubits, double* out_xeb, void* stream);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* tn_last_error(void);
+
+/* Library version string. */
+const char* tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TN_H_ */

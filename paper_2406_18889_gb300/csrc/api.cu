@@ -1,0 +1,219 @@
+// The C ABI declared in include/tn.h.  Validation happens before any device
+// work; no C++ exception crosses the boundary.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+struct tn_plan_s {
+  std::unique_ptr<tn::Plan> p;
+};
+
+namespace tn {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+struct Failure {
+  tn_status code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(tn_status code, const std::string& msg) { throw Failure{code, msg}; }
+
+template <class F>
+static tn_status guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return TN_OK;
+  } catch (const Failure& e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return TN_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return TN_ERR_INVALID_ARG;
+  } catch (...) {
+    g_last_error = "unknown failure";
+    return TN_ERR_INVALID_ARG;
+  }
+}
+
+static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
+                         size_t ws_bytes, cudaStream_t s) {
+  TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
+  TN_CHECK(amps != nullptr, TN_ERR_INVALID_ARG, "amps is null");
+  TN_CHECK(n >= 0, TN_ERR_INVALID_ARG, "n_slices < 0");
+  TN_CHECK(n == 0 || ids != nullptr, TN_ERR_INVALID_ARG, "slice_ids is null");
+  TN_CHECK(accumulate == 0 || accumulate == 1, TN_ERR_INVALID_ARG, "accumulate must be 0 or 1");
+  const int64_t S = int64_t(1) << P.sliced.size();
+  for (int64_t i = 0; i < n; ++i)
+    TN_CHECK(ids[i] >= 0 && ids[i] < S, TN_ERR_INVALID_ARG, "slice id out of range");
+  if (n > 0) {
+    TN_CHECK(ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & 255) == 0, TN_ERR_INVALID_ARG,
+             "workspace must be non-null and 256-byte aligned");
+    TN_CHECK((int64_t)ws_bytes >= P.ws_bytes, TN_ERR_INVALID_ARG, "workspace too small");
+  }
+  if (n == 0) {
+    if (!accumulate) launch_zero(amps, (size_t)(P.G * P.J * 16), s);
+    TN_CUDA(cudaGetLastError());
+    return;
+  }
+  std::vector<int64_t> chunk(P.B);
+  for (int64_t start = 0; start < n; start += P.B) {
+    int32_t nv = (int32_t)std::min<int64_t>(P.B, n - start);
+    for (int b = 0; b < P.B; ++b) chunk[b] = ids[start + (b < nv ? b : 0)];
+    // pageable host -> device: the source is staged before the call returns
+    TN_CUDA(cudaMemcpyAsync(P.d_slice_ids, chunk.data(), sizeof(int64_t) * P.B, cudaMemcpyHostToDevice, s));
+    TN_CUDA(cudaMemcpyAsync(P.d_n_valid, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    run_batch(P, ws, amps, start == 0 ? accumulate : 1, s);
+  }
+  TN_CUDA(cudaGetLastError());
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" {
+
+tn_status tn_plan_create(const tn_network_desc* net, const tn_tree_desc* tree, const tn_plan_options* opt,
+                         void* stream, tn_plan_t* out) {
+  return guarded([&] {
+    TN_CHECK(out != nullptr, TN_ERR_INVALID_ARG, "out is null");
+    auto p = build_plan(net, tree, opt, (cudaStream_t)stream);
+    auto* h = new tn_plan_s{std::move(p)};
+    *out = h;
+  });
+}
+
+tn_status tn_plan_destroy(tn_plan_t plan) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    delete plan;
+  });
+}
+
+tn_status tn_plan_query(tn_plan_t plan, int64_t* flops, int64_t* bytes, int64_t* peak, int64_t* ws) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    const Plan& P = *plan->p;
+    if (flops) *flops = (int64_t)P.useful_flops_per_slice;
+    if (bytes) *bytes = (int64_t)P.algo_bytes_per_slice;
+    if (peak) *peak = (int64_t)P.peak_intermediate_bytes;
+    if (ws) *ws = P.ws_bytes;
+  });
+}
+
+tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64_t* m, int64_t* n,
+                        int64_t* k, int32_t* kinds, int32_t* n_steps_out) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    const Plan& P = *plan->p;
+    if (n_steps_out) *n_steps_out = (int32_t)P.steps.size();
+    TN_CHECK(max_steps >= 0, TN_ERR_INVALID_ARG, "max_steps < 0");
+    int cnt = std::min<int>(max_steps, (int)P.steps.size());
+    for (int t = 0; t < cnt; ++t) {
+      const Step& S = P.steps[t];
+      if (batch) batch[t] = S.gp.nbt;
+      if (m) m[t] = S.gp.M;
+      if (n) n[t] = S.gp.N;
+      if (k) k[t] = S.gp.K;
+      if (kinds) kinds[t] = (S.variant ? 1 : 0) | (S.post_perm ? 2 : 0) | (S.hoisted ? 4 : 0);
+    }
+  });
+}
+
+tn_status tn_contract_slices(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices, void* amps,
+                             int accumulate, void* workspace, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    contract_one(*plan->p, slice_ids, n_slices, amps, accumulate, workspace, ws_bytes, (cudaStream_t)stream);
+  });
+}
+
+tn_status tn_contract_slices_batched(const tn_plan_t* plans, int32_t n_plans, const int64_t* const* slice_ids,
+                                     const int64_t* n_slices, void* const* amps, int accumulate,
+                                     void* workspace, size_t ws_bytes, void* stream) {
+  return guarded([&] {
+    TN_CHECK(n_plans >= 0, TN_ERR_INVALID_ARG, "n_plans < 0");
+    TN_CHECK(n_plans == 0 || (plans && slice_ids && n_slices && amps), TN_ERR_INVALID_ARG, "null array");
+    // validate every plan's arguments before queuing any work
+    for (int32_t i = 0; i < n_plans; ++i) {
+      TN_CHECK(plans[i] != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+      const Plan& P = *plans[i]->p;
+      TN_CHECK(amps[i] != nullptr, TN_ERR_INVALID_ARG, "amps is null");
+      TN_CHECK(n_slices[i] >= 0 && (n_slices[i] == 0 || slice_ids[i]), TN_ERR_INVALID_ARG, "bad slice list");
+      const int64_t S = int64_t(1) << P.sliced.size();
+      for (int64_t j = 0; j < n_slices[i]; ++j)
+        TN_CHECK(slice_ids[i][j] >= 0 && slice_ids[i][j] < S, TN_ERR_INVALID_ARG, "slice id out of range");
+      if (n_slices[i] > 0)
+        TN_CHECK((int64_t)ws_bytes >= P.ws_bytes && workspace, TN_ERR_INVALID_ARG, "workspace too small");
+    }
+    for (int32_t i = 0; i < n_plans; ++i)
+      contract_one(*plans[i]->p, slice_ids[i], n_slices[i], amps[i], accumulate, workspace, ws_bytes,
+                   (cudaStream_t)stream);
+  });
+}
+
+tn_status tn_topk_postprocess(const void* amps, int64_t G, int64_t B, int32_t k, double inv_f, int global_mode,
+                              const int64_t* block_base_idx, const int64_t* open_bit_pos, int32_t l,
+                              int64_t* out_idx, double* out_p, void* stream) {
+  return guarded([&] {
+    TN_CHECK(amps && block_base_idx && out_idx && out_p, TN_ERR_INVALID_ARG, "null pointer");
+    TN_CHECK(G >= 1 && B >= 1 && B <= 65536, TN_ERR_INVALID_ARG, "bad G or B");
+    TN_CHECK(l >= 0 && l <= 16 && (int64_t(1) << l) == B, TN_ERR_INVALID_ARG, "B must equal 2^l");
+    TN_CHECK(l == 0 || open_bit_pos, TN_ERR_INVALID_ARG, "open_bit_pos is null");
+    TN_CHECK(global_mode == 0 || global_mode == 1, TN_ERR_INVALID_ARG, "global_mode must be 0 or 1");
+    TN_CHECK(k >= 1 && k <= 512 && k <= (global_mode ? G * B : B), TN_ERR_INVALID_ARG, "k out of range");
+    TN_CHECK(global_mode || G <= 0x7fffffff, TN_ERR_INVALID_ARG, "too many blocks");
+    TN_CHECK(inv_f > 0 && inv_f == inv_f, TN_ERR_INVALID_ARG, "inv_f must be positive");
+    TopkParams tp{};
+    tp.G = G;
+    tp.Bsz = B;
+    tp.k = k;
+    tp.l = l;
+    tp.global_mode = global_mode;
+    tp.inv_f = inv_f;
+    for (int i = 0; i < l; ++i) {
+      TN_CHECK(open_bit_pos[i] >= 0 && open_bit_pos[i] < 63, TN_ERR_INVALID_ARG, "open bit position out of range");
+      tp.open_pos[i] = (int8_t)open_bit_pos[i];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int* d_flag = nullptr;
+    TN_CUDA(cudaMallocAsync(&d_flag, sizeof(int), s));
+    TN_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+    launch_topk((const double2*)amps, tp, block_base_idx, out_idx, out_p, d_flag, s);
+    int h_flag = 0;
+    TN_CUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TN_CUDA(cudaFreeAsync(d_flag, s));
+    TN_CUDA(cudaStreamSynchronize(s));
+    TN_CHECK(h_flag == 0, TN_ERR_NUMERIC, "NaN probability in top-k input");
+  });
+}
+
+tn_status tn_xeb(const double* q, int64_t n_sel, int32_t n_qubits, double* out_xeb, void* stream) {
+  return guarded([&] {
+    TN_CHECK(q && out_xeb, TN_ERR_INVALID_ARG, "null pointer");
+    TN_CHECK(n_sel >= 1, TN_ERR_INVALID_ARG, "empty selection");
+    TN_CHECK(n_qubits >= 1 && n_qubits <= 1000, TN_ERR_INVALID_ARG, "n_qubits out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* d_out = nullptr;
+    TN_CUDA(cudaMallocAsync(&d_out, sizeof(double), s));
+    launch_xeb(q, n_sel, n_qubits, d_out, s);
+    TN_CUDA(cudaMemcpyAsync(out_xeb, d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TN_CUDA(cudaFreeAsync(d_out, s));
+    TN_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+const char* tn_last_error(void) { return g_last_error.c_str(); }
+
+const char* tn_version(void) { return "tn-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

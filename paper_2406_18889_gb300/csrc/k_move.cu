@@ -1,0 +1,225 @@
+// Data-movement kernels: bit-permutation transpose, sliced-leaf gather, leaf
+// upload, and the FP64 cross-slice accumulation.
+//
+// Every tensor here has 2^r complex elements (all edge dimensions are powers
+// of two), so a change of dimension order is a permutation of the r index
+// bits.  These kernels are HBM-bound: each element is read once and written
+// once.
+#include "tn_internal.h"
+
+namespace tn {
+
+// ------------------------------------------------------------ bit permute
+// A CTA moves one tile: the input's 5 fastest bits (coalesced 256-byte reads)
+// together with the bits that become the output's 5 fastest (coalesced
+// writes), staged through shared memory; the remaining bits index the grid.
+namespace {
+
+constexpr int kTileMaxBits = 10;
+
+struct PermTile {
+  int nt;                   // tile bits
+  int tin[kTileMaxBits];    // input bit position of tile bit i (read order)
+  int tpos_w[kTileMaxBits]; // tile bit index of the i-th write-order bit
+  int tout_w[kTileMaxBits]; // output bit position of the i-th write-order bit
+  int ng;                   // grid bits
+  int gin[kMaxBits];
+  int gout[kMaxBits];
+};
+
+__global__ void __launch_bounds__(256) bit_permute_kernel(const float2* __restrict__ in,
+                                                          float2* __restrict__ out, PermTile pt) {
+  __shared__ float2 tile[(1 << kTileMaxBits) + (1 << kTileMaxBits) / 16];
+  const int64_t blk = blockIdx.x;
+  int64_t base_in = 0, base_out = 0;
+  for (int j = 0; j < pt.ng; ++j) {
+    int64_t bit = (blk >> j) & 1;
+    base_in |= bit << pt.gin[j];
+    base_out |= bit << pt.gout[j];
+  }
+  const int n = 1 << pt.nt;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int64_t off = base_in;
+#pragma unroll 4
+    for (int i = 0; i < pt.nt; ++i) off |= (int64_t)((t >> i) & 1) << pt.tin[i];
+    tile[t + (t >> 4)] = in[off];
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < n; u += blockDim.x) {
+    int64_t off = base_out;
+    int t = 0;
+#pragma unroll 4
+    for (int i = 0; i < pt.nt; ++i) {
+      int bit = (u >> i) & 1;
+      off |= (int64_t)bit << pt.tout_w[i];
+      t |= bit << pt.tpos_w[i];
+    }
+    out[off] = tile[t + (t >> 4)];
+  }
+}
+
+__global__ void copy_kernel(const float2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) out[i] = in[i];
+}
+
+}  // namespace
+
+void launch_bit_permute_c64(const void* in, void* out, const BitPermute& bp, cudaStream_t s) {
+  const int R = bp.nbits;
+  bool identity = true;
+  for (int i = 0; i < R; ++i) identity &= bp.out_bit[i] == i;
+  if (identity) {
+    int64_t n = int64_t(1) << R;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    copy_kernel<<<blocks, 256, 0, s>>>((const float2*)in, (float2*)out, n);
+    return;
+  }
+  const int a = std::min(5, R);
+  int in_of_out[kMaxBits];
+  for (int i = 0; i < R; ++i) in_of_out[bp.out_bit[i]] = i;
+  bool in_tile[kMaxBits] = {};
+  PermTile pt{};
+  pt.nt = 0;
+  for (int i = 0; i < a; ++i) {
+    in_tile[i] = true;
+    pt.tin[pt.nt++] = i;
+  }
+  for (int o = 0; o < a; ++o) {
+    int i = in_of_out[o];
+    if (!in_tile[i]) {
+      in_tile[i] = true;
+      pt.tin[pt.nt++] = i;
+    }
+  }
+  // widen the tile while it stays within kTileMaxBits (more work per CTA)
+  for (int i = a; i < R && pt.nt < 8; ++i)
+    if (!in_tile[i]) {
+      in_tile[i] = true;
+      pt.tin[pt.nt++] = i;
+    }
+  // write order: tile bits sorted by output position
+  int order[kTileMaxBits];
+  for (int i = 0; i < pt.nt; ++i) order[i] = i;
+  for (int i = 0; i < pt.nt; ++i)
+    for (int j = i + 1; j < pt.nt; ++j)
+      if (bp.out_bit[pt.tin[order[j]]] < bp.out_bit[pt.tin[order[i]]]) std::swap(order[i], order[j]);
+  for (int i = 0; i < pt.nt; ++i) {
+    pt.tpos_w[i] = order[i];
+    pt.tout_w[i] = bp.out_bit[pt.tin[order[i]]];
+  }
+  pt.ng = 0;
+  for (int i = 0; i < R; ++i)
+    if (!in_tile[i]) {
+      pt.gin[pt.ng] = i;
+      pt.gout[pt.ng] = bp.out_bit[i];
+      ++pt.ng;
+    }
+  int64_t blocks = int64_t(1) << pt.ng;
+  TN_CHECK(blocks < (int64_t(1) << 31), TN_ERR_UNSUPPORTED, "transpose grid too large");
+  bit_permute_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float2*)in, (float2*)out, pt);
+}
+
+// ------------------------------------------------------------ leaf upload
+namespace {
+__global__ void strided_copy_c128_kernel(const double2* __restrict__ in, float2* __restrict__ out,
+                                         StridedCopy sc, int64_t n) {
+  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  int64_t rem = o, off = 0;
+  for (int d = sc.nd - 1; d >= 0; --d) {
+    int64_t c = rem % sc.dims[d];
+    rem /= sc.dims[d];
+    off += c * sc.in_stride[d];
+  }
+  double2 v = in[off];
+  out[o] = make_float2((float)v.x, (float)v.y);
+}
+}  // namespace
+
+void launch_strided_copy_c128_to_c64(const void* in, void* out, const StridedCopy& sc, int64_t n_out,
+                                     cudaStream_t s) {
+  if (n_out <= 0) return;
+  int64_t blocks = (n_out + 255) / 256;
+  strided_copy_c128_kernel<<<(unsigned)blocks, 256, 0, s>>>((const double2*)in, (float2*)out, sc, n_out);
+}
+
+// ------------------------------------------------------------ slice gather
+namespace {
+__global__ void gather_kernel(const GatherLeaf* __restrict__ tab, const int64_t* __restrict__ ids, int B,
+                              const char* __restrict__ pbase, char* __restrict__ wbase) {
+  const GatherLeaf& g = tab[blockIdx.y];
+  const int64_t total = g.rest * B;
+  const float2* src = (const float2*)(pbase + g.src_off);
+  float2* dst = (float2*)(wbase + g.dst_off);
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = x / g.rest, r = x % g.rest;
+    int64_t sid = ids[b];
+    int64_t sel = 0;
+    for (int i = 0; i < g.n_sel; ++i) sel += ((sid >> g.slice_bit[i]) & 1) * g.sel_stride[i];
+    int64_t o = (r / g.inner) * B * g.inner + b * g.inner + r % g.inner;
+    dst[o] = src[sel + r];
+  }
+}
+}  // namespace
+
+void launch_gather_leaves(const GatherLeaf* d_table, int n_leaves, int64_t max_rest,
+                          const int64_t* d_slice_ids, int B, const char* plan_base, char* ws_base,
+                          cudaStream_t s) {
+  if (n_leaves == 0) return;
+  int64_t per = max_rest * B;
+  unsigned bx = (unsigned)std::min<int64_t>((per + 255) / 256, 64);
+  TN_CHECK(n_leaves <= 65535, TN_ERR_UNSUPPORTED, "too many sliced leaves");
+  gather_kernel<<<dim3(bx, n_leaves), 256, 0, s>>>(d_table, d_slice_ids, B, plan_base, ws_base);
+}
+
+// ------------------------------------------------------------ accumulate
+// amps[g][j] = (accumulate ? amps[g][j] : 0) + sum_{b < n_valid} root[b][g][j]
+// in FP64, b ascending (the cross-slice sum of paper Sec. III slicing).
+namespace {
+__global__ void accumulate_kernel(const float2* __restrict__ root, int64_t sb, int64_t sg, int64_t sj,
+                                  int64_t G, int64_t J, const int32_t* __restrict__ n_valid,
+                                  double2* __restrict__ amps, int accumulate) {
+  int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x >= G * J) return;
+  int64_t g = x / J, j = x % J;
+  const int nv = *n_valid;
+  double re = 0.0, im = 0.0;
+  const float2* p = root + g * sg + j * sj;
+  for (int b = 0; b < nv; ++b) {
+    float2 v = p[b * sb];
+    re += (double)v.x;
+    im += (double)v.y;
+  }
+  if (accumulate) {
+    double2 a = amps[x];
+    re = a.x + re;
+    im = a.y + im;
+  }
+  amps[x] = make_double2(re, im);
+}
+__global__ void zero_kernel(uint4* p, int64_t n16) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = make_uint4(0, 0, 0, 0);
+}
+}  // namespace
+
+void launch_accumulate_c64(const void* root, int64_t sb, int64_t sg, int64_t sj, int64_t G, int64_t J,
+                           const int32_t* d_n_valid, int B, void* amps, int accumulate, cudaStream_t s) {
+  (void)B;
+  int64_t n = G * J;
+  accumulate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)root, sb, sg, sj, G, J,
+                                                                 d_n_valid, (double2*)amps, accumulate);
+}
+
+void launch_zero(void* p, size_t bytes, cudaStream_t s) {
+  // bytes is a multiple of 16 (complex128 buffers)
+  int64_t n16 = (int64_t)(bytes / 16);
+  if (n16 == 0) return;
+  unsigned blocks = (unsigned)std::min<int64_t>((n16 + 255) / 256, 4096);
+  zero_kernel<<<blocks, 256, 0, s>>>((uint4*)p, n16);
+}
+
+}  // namespace tn

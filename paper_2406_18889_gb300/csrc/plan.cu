@@ -1,0 +1,701 @@
+// Plan construction and execution (host side).
+//
+// arXiv 2406.18889, Sec. III "Optimizing tensor contraction":
+//  * a sliced sub-network fixes the values of the sliced edges; the network is
+//    the sum over all assignments.  Here the slices of one batch are
+//    contracted together: every tensor that depends on a sliced leaf carries
+//    an extra "slice-batch" edge (one entry per slice of the batch), which is
+//    a batch index when both operands carry it and a free index when only one
+//    does -- slice-independent operands are then reused across the batch.
+//  * dimension order: "placing the contracted dimensions of input tensors at
+//    the end, the same order of contracted dimensions in both inputs, input
+//    dimensions in the order of the output", assigned greedily from the root.
+//    Here each step's operands must be stored as three contiguous blocks
+//    (batch, free, contracted) so that the step is one strided batched GEMM;
+//    the root-down pass picks, per step, the contracted order and block
+//    arrangement for which the producing steps can write their results
+//    directly, and inserts a transpose only where no choice allows it.
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+
+#include "plan.h"
+
+namespace tn {
+
+namespace {
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  return r;
+}
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+std::vector<int> set_inter(const std::vector<int>& a, const std::vector<int>& b) {
+  std::vector<int> r;
+  std::set_intersection(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+std::vector<int> set_minus(const std::vector<int>& a, const std::vector<int>& b) {
+  std::vector<int> r;
+  std::set_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+bool contains(const std::vector<int>& v, int e) { return std::find(v.begin(), v.end(), e) != v.end(); }
+
+// edges of `group` in the order they appear in `layout`
+std::vector<int> order_by(const std::vector<int>& group, const std::vector<int>& layout) {
+  std::vector<int> r;
+  for (int e : layout)
+    if (contains(group, e)) r.push_back(e);
+  return r;
+}
+
+// Does `layout` consist of one contiguous run per non-empty group?
+bool decomposes(const std::vector<int>& layout, const std::vector<const std::vector<int>*>& groups) {
+  int prev = -1;
+  std::vector<char> seen(groups.size(), 0);
+  for (int e : layout) {
+    int g = -1;
+    for (size_t i = 0; i < groups.size(); ++i)
+      if (contains(*groups[i], e)) {
+        g = (int)i;
+        break;
+      }
+    if (g < 0) return false;
+    if (g != prev) {
+      if (seen[g]) return false;
+      seen[g] = 1;
+      prev = g;
+    }
+  }
+  return true;
+}
+
+struct Arena {
+  std::vector<std::pair<int64_t, int64_t>> live;  // (off, bytes), sorted by off
+  int64_t peak = 0;
+  int64_t alloc(int64_t bytes) {
+    bytes = round_up(std::max<int64_t>(bytes, 1), 256);
+    int64_t off = 0;
+    for (auto& b : live) {
+      if (b.first - off >= bytes) break;
+      off = std::max(off, b.first + b.second);
+    }
+    live.push_back({off, bytes});
+    std::sort(live.begin(), live.end());
+    peak = std::max(peak, off + bytes);
+    return off;
+  }
+  void release(int64_t off) {
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i].first == off) {
+        live.erase(live.begin() + i);
+        return;
+      }
+  }
+};
+
+}  // namespace
+
+Plan::~Plan() {
+  if (graph) cudaGraphExecDestroy(graph);
+  if (capture_stream) cudaStreamDestroy(capture_stream);
+  if (d_plan) cudaFree(d_plan);
+  if (d_slice_ids) cudaFree(d_slice_ids);
+  if (d_n_valid) cudaFree(d_n_valid);
+  if (d_gather) cudaFree(d_gather);
+}
+
+// ---------------------------------------------------------------- layouts
+namespace {
+
+struct Builder {
+  Plan& P;
+  explicit Builder(Plan& p) : P(p) {}
+
+  int64_t dims_prod(const std::vector<int>& es) const {
+    int64_t r = 1;
+    for (int e : es) r *= P.dim[e];
+    return r;
+  }
+  std::map<int, int64_t> strides(const std::vector<int>& layout) const {
+    std::map<int, int64_t> s;
+    int64_t acc = 1;
+    for (int i = (int)layout.size() - 1; i >= 0; --i) {
+      s[layout[i]] = acc;
+      acc *= P.dim[layout[i]];
+    }
+    return s;
+  }
+  // stride of a contiguous block = stride of its fastest edge (0 if empty)
+  int64_t block_stride(const std::vector<int>& block, const std::map<int, int64_t>& st) const {
+    if (block.empty()) return 0;
+    return st.at(block.back());
+  }
+  int producer(int node) const { return P.nodes[node].leaf ? -1 : node - P.n_leaves; }
+
+  // cost (elements moved) for node x to be stored in layout L
+  double placement_cost(int x, const std::vector<int>& L) const {
+    int q = producer(x);
+    if (q < 0) return 0.0;
+    const Step& Q = P.steps[q];
+    if (decomposes(L, {&Q.bt, &Q.m, &Q.n})) return 0.0;
+    return 2.0 * (double)P.nodes[x].elems;
+  }
+  // small preference terms: the operand's innermost block should be long
+  // (coalesced loads) and preferably the contracted block
+  double inner_penalty(const std::vector<std::vector<int>>& blocks, const std::vector<int>& kblock,
+                       double elems) const {
+    const std::vector<int>* inner = nullptr;
+    for (auto it = blocks.rbegin(); it != blocks.rend(); ++it)
+      if (dims_prod(*it) > 1) {
+        inner = &*it;
+        break;
+      }
+    if (!inner) return 0.0;
+    double sz = (double)dims_prod(*inner);
+    double pen = 0.0;
+    if (sz < 16) pen += elems * 0.25 * (16.0 - sz) / 16.0;
+    if (inner != &kblock && (inner->empty() || inner->front() != (kblock.empty() ? -2 : kblock.front())))
+      pen += elems * 0.01;
+    return pen;
+  }
+
+  std::vector<std::vector<int>> k_candidates(const Step& S) const {
+    std::vector<std::vector<int>> out;
+    out.push_back(S.k);  // ascending edge ids
+    for (int operand = 0; operand < 2; ++operand) {
+      int q = producer(operand == 0 ? S.a : S.b);
+      if (q < 0) continue;
+      const Step& Q = P.steps[q];
+      std::array<const std::vector<int>*, 3> gs = {&Q.bt, &Q.m, &Q.n};
+      std::array<int, 3> perm = {0, 1, 2};
+      do {
+        std::vector<int> kk;
+        for (int gi : perm)
+          for (int e : *gs[gi])
+            if (contains(S.k, e)) kk.push_back(e);
+        if (kk.size() == S.k.size()) out.push_back(kk);
+      } while (std::next_permutation(perm.begin(), perm.end()));
+    }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return out;
+  }
+
+  void assign_layouts() {
+    // root: [slice batch][block][open edges]
+    Node& R = P.nodes[P.root];
+    std::vector<int> rl;
+    if (R.variant) rl.push_back(P.batch_edge);
+    if (P.block_edge >= 0) rl.push_back(P.block_edge);
+    for (int e : P.open_edges) rl.push_back(e);
+    R.layout = rl;
+    for (int t = (int)P.steps.size() - 1; t >= 0; --t) {
+      Step& S = P.steps[t];
+      const std::vector<int>& Lc = P.nodes[S.c].layout;
+      if (decomposes(Lc, {&S.bt, &S.m, &S.n})) {
+        S.lc_nat = Lc;
+        S.post_perm = false;
+      } else {
+        std::vector<int> nat;
+        for (auto* g : {&S.bt, &S.m, &S.n})
+          for (int e : order_by(*g, Lc)) nat.push_back(e);
+        S.lc_nat = nat;
+        S.post_perm = true;
+      }
+      std::vector<int> bt_o = order_by(S.bt, S.lc_nat);
+      std::vector<int> m_o = order_by(S.m, S.lc_nat);
+      std::vector<int> n_o = order_by(S.n, S.lc_nat);
+      double ea = (double)P.nodes[S.a].elems, eb = (double)P.nodes[S.b].elems;
+      double best = 1e300;
+      std::vector<int> best_a, best_b;
+      for (const auto& k_o : k_candidates(S)) {
+        // operand A blocks {bt, m, k}; operand B blocks {bt, k, n}
+        std::array<const std::vector<int>*, 3> A3 = {&bt_o, &m_o, &k_o};
+        std::array<const std::vector<int>*, 3> B3 = {&bt_o, &n_o, &k_o};
+        std::array<int, 3> pa = {0, 1, 2};
+        do {
+          std::vector<int> la;
+          std::vector<std::vector<int>> ablocks;
+          for (int i : pa) {
+            ablocks.push_back(*A3[i]);
+            la.insert(la.end(), A3[i]->begin(), A3[i]->end());
+          }
+          double ca = placement_cost(S.a, la) + inner_penalty(ablocks, k_o, ea);
+          if (ca >= best) continue;
+          std::array<int, 3> pb = {0, 1, 2};
+          do {
+            std::vector<int> lb;
+            std::vector<std::vector<int>> bblocks;
+            for (int i : pb) {
+              bblocks.push_back(*B3[i]);
+              lb.insert(lb.end(), B3[i]->begin(), B3[i]->end());
+            }
+            double cb = placement_cost(S.b, lb) + inner_penalty(bblocks, k_o, eb);
+            if (ca + cb < best) {
+              best = ca + cb;
+              best_a = la;
+              best_b = lb;
+            }
+          } while (std::next_permutation(pb.begin(), pb.end()));
+        } while (std::next_permutation(pa.begin(), pa.end()));
+      }
+      P.nodes[S.a].layout = best_a;
+      P.nodes[S.b].layout = best_b;
+    }
+  }
+
+  void fill_gemm(Step& S) {
+    auto sa = strides(P.nodes[S.a].layout);
+    auto sb = strides(P.nodes[S.b].layout);
+    auto sc = strides(S.lc_nat);
+    std::vector<int> bt_o = order_by(S.bt, S.lc_nat);
+    std::vector<int> m_o = order_by(S.m, S.lc_nat);
+    std::vector<int> n_o = order_by(S.n, S.lc_nat);
+    std::vector<int> k_o = order_by(S.k, P.nodes[S.a].layout);
+    GemmParams& g = S.gp;
+    g.nbt = dims_prod(bt_o);
+    g.M = dims_prod(m_o);
+    g.N = dims_prod(n_o);
+    g.K = dims_prod(k_o);
+    g.sa_bt = block_stride(order_by(S.bt, P.nodes[S.a].layout), sa);
+    g.sa_m = block_stride(order_by(S.m, P.nodes[S.a].layout), sa);
+    g.sa_k = block_stride(k_o, sa);
+    g.sb_bt = block_stride(order_by(S.bt, P.nodes[S.b].layout), sb);
+    g.sb_k = block_stride(order_by(S.k, P.nodes[S.b].layout), sb);
+    g.sb_n = block_stride(order_by(S.n, P.nodes[S.b].layout), sb);
+    g.sc_bt = block_stride(bt_o, sc);
+    g.sc_m = block_stride(m_o, sc);
+    g.sc_n = block_stride(n_o, sc);
+    // consistency: group orders agree across operands (guaranteed by construction)
+    TN_CHECK(order_by(S.bt, P.nodes[S.a].layout) == bt_o && order_by(S.bt, P.nodes[S.b].layout) == bt_o &&
+                 order_by(S.m, P.nodes[S.a].layout) == m_o && order_by(S.n, P.nodes[S.b].layout) == n_o &&
+                 order_by(S.k, P.nodes[S.b].layout) == k_o,
+             TN_ERR_INVALID_ARG, "internal: inconsistent operand layouts");
+    TN_CHECK(decomposes(P.nodes[S.a].layout, {&S.bt, &S.m, &S.k}) &&
+                 decomposes(P.nodes[S.b].layout, {&S.bt, &S.k, &S.n}) &&
+                 decomposes(S.lc_nat, {&S.bt, &S.m, &S.n}),
+             TN_ERR_INVALID_ARG, "internal: operand not blockwise");
+    S.cost = (double)g.nbt * g.M * g.N * g.K;
+  }
+
+  BitPermute bit_perm(const std::vector<int>& from, const std::vector<int>& to) const {
+    // bit position of (edge, sub-bit) in a layout; bit 0 = fastest
+    auto positions = [&](const std::vector<int>& L) {
+      std::map<int, int> base;
+      int acc = 0;
+      for (int i = (int)L.size() - 1; i >= 0; --i) {
+        base[L[i]] = acc;
+        acc += ilog2(P.dim[L[i]]);
+      }
+      return std::make_pair(base, acc);
+    };
+    auto [fb, nb] = positions(from);
+    auto [tb, nb2] = positions(to);
+    TN_CHECK(nb == nb2 && nb <= kMaxBits, TN_ERR_UNSUPPORTED, "tensor too large to transpose");
+    BitPermute bp{};
+    bp.nbits = nb;
+    for (int e : from)
+      for (int s = 0; s < ilog2(P.dim[e]); ++s) bp.out_bit[fb[e] + s] = tb[e] + s;
+    return bp;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- build
+std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc* tree,
+                                 const tn_plan_options* opt, cudaStream_t stream) {
+  auto Pp = std::make_unique<Plan>();
+  Plan& P = *Pp;
+  TN_CHECK(net && tree && opt, TN_ERR_INVALID_ARG, "null descriptor");
+  TN_CHECK(net->n_leaves >= 1 && net->n_edges >= 1, TN_ERR_INVALID_ARG, "empty network");
+  TN_CHECK(net->leaf_rank && net->leaf_edges && net->edge_dim && net->leaf_data, TN_ERR_INVALID_ARG,
+           "null network array");
+  TN_CHECK(opt->prec == TN_PREC_C64, TN_ERR_UNSUPPORTED,
+           "this build contracts in complex64 only (bf16/fp16 not available)");
+  TN_CHECK(opt->max_slice_batch >= 1 && opt->max_slice_batch <= 65536 && is_pow2(opt->max_slice_batch),
+           TN_ERR_INVALID_ARG, "max_slice_batch must be a power of two in [1, 65536]");
+  P.prec = opt->prec;
+  P.flags = opt->flags;
+  P.elem_bytes = 8;
+  P.n_leaves = net->n_leaves;
+  P.n_edges = net->n_edges;
+  P.dim.assign(net->edge_dim, net->edge_dim + net->n_edges);
+  for (int64_t d : P.dim) TN_CHECK(is_pow2(d), TN_ERR_UNSUPPORTED, "edge dimensions must be powers of two");
+  // leaves
+  std::vector<int> count(P.n_edges, 0);
+  int64_t pos = 0, eoff = 0;
+  P.leaf_edges.resize(P.n_leaves);
+  P.leaf_off.resize(P.n_leaves);
+  for (int i = 0; i < P.n_leaves; ++i) {
+    int r = net->leaf_rank[i];
+    TN_CHECK(r >= 0 && r <= 32, TN_ERR_INVALID_ARG, "leaf rank out of range");
+    int64_t el = 1;
+    for (int j = 0; j < r; ++j) {
+      int e = net->leaf_edges[pos + j];
+      TN_CHECK(e >= 0 && e < P.n_edges, TN_ERR_INVALID_ARG, "leaf edge id out of range");
+      TN_CHECK(!contains(P.leaf_edges[i], e), TN_ERR_INVALID_ARG, "edge repeated within a leaf");
+      P.leaf_edges[i].push_back(e);
+      count[e]++;
+      el *= P.dim[e];
+      TN_CHECK(el <= (int64_t(1) << 40), TN_ERR_UNSUPPORTED, "leaf too large");
+    }
+    pos += r;
+    P.leaf_off[i] = eoff;
+    eoff += el;
+  }
+  const int64_t total_leaf_elems = eoff;
+  TN_CHECK(net->n_open >= 0 && (net->n_open == 0 || net->open_edges), TN_ERR_INVALID_ARG, "bad open edges");
+  P.open_edges.assign(net->open_edges, net->open_edges + net->n_open);
+  P.block_edge = net->block_edge;
+  TN_CHECK(P.block_edge >= -1 && P.block_edge < P.n_edges, TN_ERR_INVALID_ARG, "bad block edge");
+  std::vector<int> outputs = P.open_edges;
+  if (P.block_edge >= 0) outputs.push_back(P.block_edge);
+  {
+    std::vector<int> so = outputs;
+    std::sort(so.begin(), so.end());
+    TN_CHECK(std::adjacent_find(so.begin(), so.end()) == so.end(), TN_ERR_INVALID_ARG, "output edge repeated");
+    for (int e : so) TN_CHECK(e >= 0 && e < P.n_edges, TN_ERR_INVALID_ARG, "output edge id out of range");
+  }
+  for (int e = 0; e < P.n_edges; ++e) {
+    if (e == P.block_edge) {
+      TN_CHECK(count[e] >= 1, TN_ERR_INVALID_ARG, "block edge unused");
+    } else if (contains(P.open_edges, e)) {
+      TN_CHECK(count[e] == 1, TN_ERR_INVALID_ARG, "open edge must appear in exactly one leaf");
+    } else {
+      TN_CHECK(count[e] == 2 || count[e] == 0, TN_ERR_INVALID_ARG, "bond must appear in exactly two leaves");
+    }
+  }
+  P.G = P.block_edge >= 0 ? P.dim[P.block_edge] : 1;
+  P.J = 1;
+  for (int e : P.open_edges) P.J *= P.dim[e];
+  TN_CHECK(P.G * P.J <= (int64_t(1) << 34), TN_ERR_UNSUPPORTED, "output too large");
+  // slicing
+  TN_CHECK(tree->n_sliced >= 0 && tree->n_sliced <= 62, TN_ERR_INVALID_ARG, "n_sliced out of range");
+  TN_CHECK(tree->n_sliced == 0 || tree->sliced_edges, TN_ERR_INVALID_ARG, "null sliced_edges");
+  for (int i = 0; i < tree->n_sliced; ++i) {
+    int e = tree->sliced_edges[i];
+    TN_CHECK(e >= 0 && e < P.n_edges && !contains(outputs, e) && count[e] == 2 && P.dim[e] == 2 &&
+                 !contains(P.sliced, e),
+             TN_ERR_INVALID_ARG, "sliced edge must be a distinct dimension-2 bond");
+    P.sliced.push_back(e);
+  }
+  P.batch_edge = P.n_edges;
+  P.B = P.sliced.empty() ? 1 : opt->max_slice_batch;
+  P.dim.push_back(P.B);
+  // tree replay
+  TN_CHECK(tree->n_steps == P.n_leaves - 1 && (tree->n_steps == 0 || tree->pairs), TN_ERR_INVALID_ARG,
+           "a tree over n leaves has n - 1 steps");
+  int n_nodes = P.n_leaves + tree->n_steps;
+  P.nodes.resize(n_nodes);
+  std::vector<char> sliced_mark(P.n_edges + 1, 0);
+  for (int e : P.sliced) sliced_mark[e] = 1;
+  std::vector<std::set<int>> occ(P.n_edges + 1);
+  for (int i = 0; i < P.n_leaves; ++i) {
+    Node& N = P.nodes[i];
+    N.leaf = true;
+    N.leaf_id = i;
+    N.plan_mem = true;
+    for (int e : P.leaf_edges[i]) {
+      if (sliced_mark[e])
+        N.variant = true;
+      else
+        N.edges.push_back(e);
+    }
+    if (N.variant) N.edges.push_back(P.batch_edge);
+    std::sort(N.edges.begin(), N.edges.end());
+    for (int e : N.edges) occ[e].insert(i);
+    N.elems = 1;
+    for (int e : N.edges) N.elems *= P.dim[e];
+  }
+  std::vector<char> consumed(n_nodes, 0);
+  std::set<int> keep(outputs.begin(), outputs.end());
+  keep.insert(P.batch_edge);
+  for (int t = 0; t < tree->n_steps; ++t) {
+    int a = tree->pairs[2 * t], b = tree->pairs[2 * t + 1];
+    int c = P.n_leaves + t;
+    TN_CHECK(a >= 0 && b >= 0 && a < c && b < c && a != b, TN_ERR_INVALID_ARG, "tree pair refers to a later id");
+    TN_CHECK(!consumed[a] && !consumed[b], TN_ERR_INVALID_ARG, "tree consumes an id twice");
+    consumed[a] = consumed[b] = 1;
+    Step S;
+    S.a = a;
+    S.b = b;
+    S.c = c;
+    const auto& X = P.nodes[a].edges;
+    const auto& Y = P.nodes[b].edges;
+    std::vector<int> shared = set_inter(X, Y);
+    std::vector<int> C;
+    std::vector<int> uni;
+    std::set_union(X.begin(), X.end(), Y.begin(), Y.end(), std::back_inserter(uni));
+    for (int e : uni) {
+      bool drop = false;
+      if (contains(shared, e) && !keep.count(e)) {
+        drop = true;
+        for (int o : occ[e])
+          if (o != a && o != b) drop = false;
+      }
+      if (!drop) C.push_back(e);
+    }
+    for (int e : X) occ[e].erase(a);
+    for (int e : Y) occ[e].erase(b);
+    for (int e : C) occ[e].insert(c);
+    Node& N = P.nodes[c];
+    N.edges = C;
+    N.variant = P.nodes[a].variant || P.nodes[b].variant;
+    N.elems = 1;
+    for (int e : C) N.elems *= P.dim[e];
+    TN_CHECK(N.elems <= (int64_t(1) << 40), TN_ERR_UNSUPPORTED, "intermediate too large");
+    P.nodes[a].consumer = t;
+    P.nodes[b].consumer = t;
+    S.bt = set_inter(shared, C);
+    S.k = set_minus(shared, C);
+    S.m = set_minus(X, Y);
+    S.n = set_minus(Y, X);
+    S.variant = N.variant;
+    P.steps.push_back(S);
+  }
+  P.root = n_nodes - 1;
+  {
+    std::vector<int> want = outputs;
+    if (P.nodes[P.root].variant) want.push_back(P.batch_edge);
+    std::sort(want.begin(), want.end());
+    TN_CHECK(P.nodes[P.root].edges == want, TN_ERR_INVALID_ARG,
+             "the tree does not contract the network to its open and block edges");
+  }
+  const bool hoist = (P.flags & TN_FLAG_HOIST_INVARIANT) && !P.sliced.empty();
+  for (auto& S : P.steps) S.hoisted = hoist && !S.variant;
+
+  Builder bld(P);
+  bld.assign_layouts();
+  // per-sub-network statistics (slice-batch edge at size 1)
+  for (auto& S : P.steps) {
+    bld.fill_gemm(S);
+    double bscale = P.nodes[S.c].variant ? (double)P.B : 1.0;
+    S.cost_one = S.cost / bscale;
+    double bytes = ((double)P.nodes[S.a].elems / (P.nodes[S.a].variant ? P.B : 1) +
+                    (double)P.nodes[S.b].elems / (P.nodes[S.b].variant ? P.B : 1) +
+                    (double)P.nodes[S.c].elems / (P.nodes[S.c].variant ? P.B : 1)) *
+                   P.elem_bytes;
+    P.useful_flops_per_slice += 8.0 * S.cost_one;
+    P.algo_bytes_per_slice += bytes;
+    P.peak_intermediate_bytes =
+        std::max(P.peak_intermediate_bytes,
+                 (double)P.nodes[S.c].elems / (P.nodes[S.c].variant ? P.B : 1) * P.elem_bytes);
+    if (S.post_perm) S.perm = bld.bit_perm(S.lc_nat, P.nodes[S.c].layout);
+  }
+  if (P.steps.empty()) {
+    // single leaf network: the leaf is the root
+  }
+
+  // ------------------------------------------------------------ memory plan
+  // plan memory: leaves (invariant in their layout; variant as full source
+  // with sliced edges outermost) and hoisted step results
+  int64_t poff = 0;
+  std::vector<int64_t> leaf_src_elems(P.n_leaves);
+  std::vector<std::vector<int>> leaf_src_layout(P.n_leaves);
+  for (int i = 0; i < P.n_leaves; ++i) {
+    Node& N = P.nodes[i];
+    std::vector<int> L;
+    if (N.variant) {
+      for (int e : P.sliced)
+        if (contains(P.leaf_edges[i], e)) L.push_back(e);
+      for (int e : N.layout)
+        if (e != P.batch_edge) L.push_back(e);
+    } else {
+      L = N.layout;
+    }
+    leaf_src_layout[i] = L;
+    int64_t el = 1;
+    for (int e : L) el *= P.dim[e];
+    leaf_src_elems[i] = el;
+    N.off = poff;
+    poff += round_up(el * P.elem_bytes, 256);
+  }
+  for (auto& S : P.steps)
+    if (S.hoisted) {
+      Node& N = P.nodes[S.c];
+      N.plan_mem = true;
+      N.off = poff;
+      poff += round_up(N.elems * P.elem_bytes, 256);
+    }
+  P.plan_bytes = poff;
+  // workspace: gathered variant leaves, per-call step results, transpose temps
+  Arena ws;
+  for (int i = 0; i < P.n_leaves; ++i)
+    if (P.nodes[i].variant) {
+      // the gathered copy lives in the workspace; remember the source offset
+      P.gather_node.push_back(i);
+      P.gather_src_off.push_back(P.nodes[i].off);
+    }
+  for (size_t gi = 0; gi < P.gather_node.size(); ++gi) {
+    Node& N = P.nodes[P.gather_node[gi]];
+    N.plan_mem = false;
+    N.off = ws.alloc(N.elems * P.elem_bytes);
+  }
+  // hoisted-step transposes need scratch at creation time only
+  int64_t create_scratch = 0;
+  for (auto& S : P.steps) {
+    if (S.hoisted) {
+      if (S.post_perm) create_scratch = std::max(create_scratch, P.nodes[S.c].elems * P.elem_bytes);
+      continue;
+    }
+    Node& N = P.nodes[S.c];
+    N.plan_mem = false;
+    N.off = ws.alloc(N.elems * P.elem_bytes);
+    if (S.post_perm) {
+      S.tmp_off = ws.alloc(N.elems * P.elem_bytes);
+      ws.release(S.tmp_off);
+    }
+    for (int x : {S.a, S.b})
+      if (!P.nodes[x].plan_mem) ws.release(P.nodes[x].off);
+  }
+  P.ws_bytes = round_up(std::max<int64_t>(ws.peak, 256), 256);
+  if (opt->mem_cap_bytes > 0)
+    TN_CHECK(P.ws_bytes <= opt->mem_cap_bytes, TN_ERR_OOM, "workspace exceeds mem_cap_bytes");
+  // root readout
+  {
+    Node& R = P.nodes[P.root];
+    auto st = bld.strides(R.layout);
+    P.root_sb = R.variant ? st.at(P.batch_edge) : 0;
+    P.root_sg = P.block_edge >= 0 ? st.at(P.block_edge) : 0;
+    P.root_sj = P.open_edges.empty() ? 0 : st.at(P.open_edges.back());
+  }
+  // gather table
+  for (size_t gi = 0; gi < P.gather_node.size(); ++gi) {
+    int i = P.gather_node[gi];
+    Node& N = P.nodes[i];
+    GatherLeaf g{};
+    g.src_off = P.gather_src_off[gi];
+    g.dst_off = N.off;
+    g.rest = N.elems / P.B;
+    auto st = bld.strides(N.layout);
+    g.inner = st.at(P.batch_edge);
+    std::vector<int> sl_here;
+    for (int e : leaf_src_layout[i])
+      if (sliced_mark[e]) sl_here.push_back(e);
+    TN_CHECK(sl_here.size() <= 8, TN_ERR_UNSUPPORTED, "a leaf holds more than 8 sliced edges");
+    g.n_sel = (int)sl_here.size();
+    for (int j = 0; j < g.n_sel; ++j) {
+      int e = sl_here[j];
+      g.slice_bit[j] = (int)(std::find(P.sliced.begin(), P.sliced.end(), e) - P.sliced.begin());
+      g.sel_stride[j] = g.rest << (g.n_sel - 1 - j);
+    }
+    P.gather.push_back(g);
+    P.gather_max_rest = std::max(P.gather_max_rest, g.rest);
+  }
+
+  if (P.flags & TN_FLAG_PLAN_ONLY) return Pp;
+  // ------------------------------------------------------------ device setup
+  TN_CUDA(cudaMalloc(&P.d_plan, std::max<int64_t>(P.plan_bytes, 256)));
+  TN_CUDA(cudaMalloc(&P.d_slice_ids, sizeof(int64_t) * P.B));
+  TN_CUDA(cudaMalloc(&P.d_n_valid, sizeof(int32_t)));
+  if (!P.gather.empty()) {
+    TN_CUDA(cudaMalloc(&P.d_gather, sizeof(GatherLeaf) * P.gather.size()));
+    TN_CUDA(cudaMemcpyAsync(P.d_gather, P.gather.data(), sizeof(GatherLeaf) * P.gather.size(),
+                            cudaMemcpyHostToDevice, stream));
+  }
+  // upload leaves: complex128 host -> device staging -> complex64 in plan layout
+  void* d_stage = nullptr;
+  TN_CUDA(cudaMalloc(&d_stage, std::max<int64_t>(total_leaf_elems * 16, 256)));
+  TN_CUDA(cudaMemcpyAsync(d_stage, net->leaf_data, total_leaf_elems * 16, cudaMemcpyHostToDevice, stream));
+  for (int i = 0; i < P.n_leaves; ++i) {
+    // host strides of leaf i (row-major in leaf_edges order)
+    std::map<int, int64_t> hs;
+    int64_t acc = 1;
+    for (int j = (int)P.leaf_edges[i].size() - 1; j >= 0; --j) {
+      hs[P.leaf_edges[i][j]] = acc;
+      acc *= P.dim[P.leaf_edges[i][j]];
+    }
+    StridedCopy sc{};
+    sc.nd = (int)leaf_src_layout[i].size();
+    TN_CHECK(sc.nd <= kMaxBits, TN_ERR_UNSUPPORTED, "leaf rank too large");
+    for (int d = 0; d < sc.nd; ++d) {
+      int e = leaf_src_layout[i][d];
+      sc.dims[d] = P.dim[e];
+      sc.in_stride[d] = hs.at(e);
+    }
+    const char* src = (const char*)d_stage + P.leaf_off[i] * 16;
+    void* dst = (char*)P.d_plan + (P.nodes[i].variant ? P.gather_src_off[std::find(P.gather_node.begin(),
+                                                                                      P.gather_node.end(), i) -
+                                                                            P.gather_node.begin()]
+                                                       : P.nodes[i].off);
+    launch_strided_copy_c128_to_c64(src, dst, sc, leaf_src_elems[i], stream);
+  }
+  // hoisted steps
+  void* d_scratch = nullptr;
+  if (create_scratch) TN_CUDA(cudaMalloc(&d_scratch, create_scratch));
+  for (auto& S : P.steps) {
+    if (!S.hoisted) continue;
+    GemmParams g = S.gp;
+    g.A = (char*)P.d_plan + P.nodes[S.a].off;
+    g.B = (char*)P.d_plan + P.nodes[S.b].off;
+    void* dst = (char*)P.d_plan + P.nodes[S.c].off;
+    g.C = S.post_perm ? d_scratch : dst;
+    launch_gemm_c64(g, 0, stream);
+    if (S.post_perm) launch_bit_permute_c64(d_scratch, dst, S.perm, stream);
+  }
+  TN_CUDA(cudaStreamSynchronize(stream));
+  TN_CUDA(cudaGetLastError());
+  cudaFree(d_stage);
+  if (d_scratch) cudaFree(d_scratch);
+  TN_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
+  return Pp;
+}
+
+// ---------------------------------------------------------------- execute
+static void enqueue_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t s) {
+  char* wb = (char*)ws;
+  char* pb = (char*)P.d_plan;
+  auto base = [&](int node) -> char* { return (P.nodes[node].plan_mem ? pb : wb) + P.nodes[node].off; };
+  if (!P.gather.empty())
+    launch_gather_leaves(P.d_gather, (int)P.gather.size(), P.gather_max_rest, P.d_slice_ids, P.B, pb, wb,
+                         s);
+  for (auto& S : P.steps) {
+    if (S.hoisted) continue;
+    GemmParams g = S.gp;
+    g.A = base(S.a);
+    g.B = base(S.b);
+    char* dst = base(S.c);
+    g.C = S.post_perm ? wb + S.tmp_off : dst;
+    launch_gemm_c64(g, 0, s);
+    if (S.post_perm) launch_bit_permute_c64(wb + S.tmp_off, dst, S.perm, s);
+  }
+  launch_accumulate_c64(base(P.root), P.root_sb, P.root_sg, P.root_sj, P.G, P.J, P.d_n_valid, P.B, amps,
+                        accumulate, s);
+}
+
+void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream) {
+  if (P.flags & TN_FLAG_NO_GRAPH) {
+    enqueue_batch(P, ws, amps, accumulate, stream);
+    TN_CUDA(cudaGetLastError());
+    return;
+  }
+  if (!P.graph || P.graph_ws != ws || P.graph_amps != amps || P.graph_acc != accumulate) {
+    if (P.graph) {
+      cudaGraphExecDestroy(P.graph);
+      P.graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    TN_CUDA(cudaStreamBeginCapture(P.capture_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_batch(P, ws, amps, accumulate, P.capture_stream);
+    cudaError_t e = cudaStreamEndCapture(P.capture_stream, &g);
+    if (e != cudaSuccess) fail(TN_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&P.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) fail(TN_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    P.graph_ws = ws;
+    P.graph_amps = amps;
+    P.graph_acc = accumulate;
+  }
+  TN_CUDA(cudaGraphLaunch(P.graph, stream));
+}
+
+}  // namespace tn

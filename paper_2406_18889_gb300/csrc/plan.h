@@ -1,0 +1,90 @@
+// Plan: the network, its contraction tree and slicing, every intermediate's
+// memory layout, the workspace map and the per-step kernel parameters.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+struct Node {
+  std::vector<int> edges;   // edge set of this tensor in one sub-network (+ batch edge if variant)
+  std::vector<int> layout;  // storage order, slowest first
+  int64_t elems = 1;
+  bool variant = false;     // depends on the slice (carries the slice-batch edge)
+  bool leaf = false;
+  int leaf_id = -1;
+  int consumer = -1;        // step consuming this node; -1 for the root
+  bool plan_mem = false;    // stored in plan-owned memory (leaves, hoisted results)
+  int64_t off = -1;         // byte offset in plan memory or workspace
+};
+
+struct Step {
+  int a = -1, b = -1, c = -1;          // node ids: operands and result
+  std::vector<int> bt, m, n, k;        // ordered index groups
+  std::vector<int> lc_nat;             // layout the GEMM writes
+  bool post_perm = false;              // lc_nat differs from node c's layout
+  bool variant = false;
+  bool hoisted = false;                // runs once at plan creation
+  int64_t tmp_off = -1;                // workspace offset of the natural-layout result
+  GemmParams gp{};                     // sizes and strides (pointers filled at launch)
+  BitPermute perm{};                   // lc_nat -> node c layout
+  double cost = 0;                     // complex MACs with the batch edge at its planned size
+  double cost_one = 0;                 // complex MACs of one sub-network
+};
+
+struct Plan {
+  // network
+  int n_leaves = 0, n_edges = 0;
+  std::vector<int64_t> dim;             // edge dims; index n_edges is the slice-batch edge
+  std::vector<std::vector<int>> leaf_edges;
+  std::vector<int64_t> leaf_off;        // element offset of each leaf in leaf_data
+  std::vector<int> open_edges;
+  int block_edge = -1;
+  int64_t G = 1, J = 1;
+  // tree
+  std::vector<int> sliced;              // sliced edge ids, bit i <-> sliced[i]
+  int batch_edge = -1;                  // = n_edges
+  int B = 1;                            // slice batch (power of two)
+  std::vector<Node> nodes;
+  std::vector<Step> steps;
+  int root = -1;
+  // options
+  int prec = TN_PREC_C64;
+  uint32_t flags = 0;
+  int elem_bytes = 8;
+  // memory
+  void* d_plan = nullptr;               // leaves + hoisted results
+  int64_t plan_bytes = 0;
+  int64_t ws_bytes = 0;
+  int64_t* d_slice_ids = nullptr;       // [B]
+  int32_t* d_n_valid = nullptr;
+  GatherLeaf* d_gather = nullptr;       // gather table (device)
+  std::vector<GatherLeaf> gather;       // host copy, pointers relative (filled per call)
+  std::vector<int> gather_node;         // node id of each gather entry
+  std::vector<int64_t> gather_src_off;  // plan-memory offset of each variant leaf's source
+  int64_t gather_max_rest = 0;
+  // root readout strides (elements)
+  int64_t root_sb = 0, root_sg = 0, root_sj = 1;
+  // statistics
+  double useful_flops_per_slice = 0, algo_bytes_per_slice = 0, peak_intermediate_bytes = 0;
+  // CUDA graph cache
+  cudaGraphExec_t graph = nullptr;
+  void* graph_ws = nullptr;
+  void* graph_amps = nullptr;
+  int graph_acc = -1;
+  cudaStream_t capture_stream = nullptr;
+
+  ~Plan();
+};
+
+std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc* tree,
+                                 const tn_plan_options* opt, cudaStream_t stream);
+
+// Queue one batch (n_valid <= B slice ids already in d_slice_ids) into amps.
+void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream);
+
+}  // namespace tn

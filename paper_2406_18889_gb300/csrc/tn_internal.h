@@ -1,0 +1,100 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tn.h"
+
+namespace tn {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  tn_status code;
+  std::string msg;
+};
+void set_error(const std::string& msg);
+[[noreturn]] void fail(tn_status code, const std::string& msg);
+
+#define TN_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      ::tn::fail(TN_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TN_CHECK(cond, code, msg) \
+  do {                            \
+    if (!(cond)) ::tn::fail(code, msg); \
+  } while (0)
+
+// ------------------------------------------------------------ kernel params
+constexpr int kMaxBits = 48;
+
+// C[bt][m][n] (+)= sum_k A[bt][m][k] * B[bt][k][n]; element strides per index.
+struct GemmParams {
+  int64_t nbt, M, N, K;
+  int64_t sa_bt, sa_m, sa_k;
+  int64_t sb_bt, sb_k, sb_n;
+  int64_t sc_bt, sc_m, sc_n;
+  const void* A;
+  const void* B;
+  void* C;
+};
+
+// out[pi(x)] = in[x] for a tensor of 2^nbits elements; out_bit[i] is the
+// output bit position of input bit i (bit 0 = fastest varying).
+struct BitPermute {
+  int nbits;
+  int out_bit[kMaxBits];
+};
+
+// Per-call gather of one sliced leaf into its batched copy (offsets in bytes
+// from the plan-memory and workspace bases):
+// dst[(r / inner) * B * inner + b * inner + r % inner] =
+//   src[sel_off(slice_ids[b]) + r],  r in [0, rest), b in [0, B)
+// sel_off(s) = sum_i ((s >> slice_bit[i]) & 1) * sel_stride[i]  (elements).
+struct GatherLeaf {
+  int64_t src_off;
+  int64_t dst_off;
+  int64_t rest, inner;
+  int32_t n_sel;
+  int32_t slice_bit[8];
+  int64_t sel_stride[8];
+};
+
+// Generic strided copy used for leaf upload: out element o (row-major over
+// dims[0..nd) ) = in[sum_d coord_d * in_stride[d]], converting complex128 to
+// complex64 (or copying complex64).
+struct StridedCopy {
+  int nd;
+  int64_t dims[kMaxBits];
+  int64_t in_stride[kMaxBits];
+};
+
+// ------------------------------------------------------------ launchers
+void launch_gemm_c64(const GemmParams& p, int accumulate, cudaStream_t s);
+void launch_bit_permute_c64(const void* in, void* out, const BitPermute& bp, cudaStream_t s);
+void launch_strided_copy_c128_to_c64(const void* in, void* out, const StridedCopy& sc,
+                                     int64_t n_out, cudaStream_t s);
+void launch_gather_leaves(const GatherLeaf* d_table, int n_leaves, int64_t max_rest,
+                          const int64_t* d_slice_ids, int B, const char* plan_base, char* ws_base,
+                          cudaStream_t s);
+void launch_accumulate_c64(const void* root, int64_t sb, int64_t sg, int64_t sj, int64_t G,
+                           int64_t J, const int32_t* d_n_valid, int B, void* amps, int accumulate,
+                           cudaStream_t s);
+void launch_zero(void* p, size_t bytes, cudaStream_t s);
+struct TopkParams {
+  int64_t G, Bsz;   // blocks and entries per block
+  int k, l, global_mode;
+  double inv_f;
+  int8_t open_pos[64];  // bit position of open edge i (i = 0 most significant in j)
+};
+void launch_topk(const double2* amps, const TopkParams& tp, const int64_t* block_base,
+                 int64_t* out_idx, double* out_p, int* d_flag, cudaStream_t s);
+void launch_xeb(const double* q, int64_t n, int n_qubits, double* d_out, cudaStream_t s);
+
+}  // namespace tn

@@ -1,0 +1,124 @@
+"""User-facing layer: circuit workload -> plan -> amplitudes -> top-k -> XEB.
+
+PyTorch provides device memory and streams only; every contraction, the
+FP64 slice sum, top-k and XEB run in the library's CUDA kernels through the C
+ABI (``binding``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import binding as B
+from .network import TensorNetwork, circuit_network
+from .pathfind import Tree, plan_tree
+
+PREC = {"c64": B.TN_PREC_C64, "bf16": B.TN_PREC_BF16, "fp16": B.TN_PREC_FP16}
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+    return torch
+
+
+def flatten_network(tn: TensorNetwork):
+    rank = [len(e) for e in tn.leaf_edges]
+    edges = [e for es in tn.leaf_edges for e in es]
+    data = np.concatenate([d.reshape(-1) for d in tn.leaf_data]) if tn.leaf_data else np.zeros(0, complex)
+    return rank, edges, data
+
+
+class Plan:
+    """A contraction plan living on the current CUDA device."""
+
+    def __init__(self, tn: TensorNetwork, tree: Tree, prec: str = "c64", flags: int = 0,
+                 max_slice_batch: int = 64, mem_cap_bytes: int = 0, stream=None):
+        torch = _torch()
+        self.tn, self.tree = tn, tree
+        self.n_slices_total = 1 << len(tree.sliced_edges)
+        rank, edges, data = flatten_network(tn)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = B.tn_plan_create(rank, edges, tn.edge_dim, data, tn.open_edges, tn.block_edge,
+                                       np.asarray(tree.pairs, dtype=np.int32).reshape(-1),
+                                       tree.sliced_edges, PREC[prec], flags, max_slice_batch,
+                                       mem_cap_bytes, s.cuda_stream)
+        self.info = B.tn_plan_query(self.handle)
+        self.G = tn.n_blocks
+        self.J = 1
+        for e in tn.open_edges:
+            self.J *= tn.edge_dim[e]
+        self.workspace = torch.empty(max(self.info["workspace_bytes"], 256), dtype=torch.uint8,
+                                     device="cuda")
+
+    def steps(self) -> dict:
+        return B.tn_plan_steps(self.handle)
+
+    def contract(self, slice_ids: Optional[Sequence[int]] = None, out=None, accumulate: bool = False,
+                 stream=None):
+        """amps [G, 2^l] complex128 = sum over the given slices (all when None)."""
+        torch = _torch()
+        if slice_ids is None:
+            slice_ids = np.arange(self.n_slices_total, dtype=np.int64)
+        if out is None:
+            out = torch.empty((self.G, self.J), dtype=torch.complex128, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        B.tn_contract_slices(self.handle, slice_ids, out.data_ptr(), int(accumulate),
+                             self.workspace.data_ptr(), self.workspace.numel(), s.cuda_stream)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.tn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def topk(amps, k: int, inv_f: float, block_base, open_bit_pos, global_mode: bool = False, stream=None):
+    """(idx int64, p float64) device tensors: [G, k] per block or [k] global."""
+    torch = _torch()
+    G, Bsz = amps.shape
+    shape = (k,) if global_mode else (G, k)
+    idx = torch.empty(shape, dtype=torch.int64, device="cuda")
+    p = torch.empty(shape, dtype=torch.float64, device="cuda")
+    base = block_base if hasattr(block_base, "data_ptr") else torch.as_tensor(
+        np.asarray(block_base, dtype=np.int64), device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    B.tn_topk_postprocess(amps.data_ptr(), G, Bsz, k, inv_f, int(global_mode), base.data_ptr(),
+                          np.asarray(open_bit_pos, dtype=np.int64), idx.data_ptr(), p.data_ptr(),
+                          s.cuda_stream)
+    return idx, p
+
+
+def xeb(q, n_qubits: int, stream=None) -> float:
+    torch = _torch()
+    q = q.reshape(-1).contiguous()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return B.tn_xeb(q.data_ptr(), q.numel(), n_qubits, s.cuda_stream)
+
+
+@dataclass
+class Prepared:
+    tn: TensorNetwork
+    tree: Tree
+
+
+def prepare(workload, n_sliced: Optional[int] = None, restarts: int = 4, seed: int = 0,
+            sliced_wires: Optional[Sequence] = None) -> Prepared:
+    """Network + contraction tree of a workload (host planning, once per circuit)."""
+    tn = circuit_network(workload.circuit, workload.open_qubits, workload.closed_qubits,
+                         workload.closed_bits)
+    sliced = None
+    if sliced_wires is not None:
+        sliced = [tn.edge_of_wire[tuple(w)] for w in sliced_wires]
+    s = workload.n_sliced if n_sliced is None else n_sliced
+    tree = plan_tree(tn, n_sliced=s, restarts=restarts, seed=seed, sliced=sliced)
+    return Prepared(tn, tree)

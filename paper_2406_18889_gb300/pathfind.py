@@ -1,0 +1,240 @@
+"""Contraction path and slicing search (host side, once per circuit).
+
+The paper searches contraction paths under a memory cap and slices edges
+until the largest intermediate fits (arXiv 2406.18889, Sec. III "Optimizing
+tensor contraction": slicing fixes edge values and sums the sub-networks,
+trading time for space).  Its own path optimiser is not described; this
+module uses a greedy rule with seeded random restarts:
+
+* greedy: repeatedly contract the pair of tensors sharing an edge with the
+  lowest score size(C) - alpha (size(A) + size(B)); restarts add seeded Gumbel
+  noise to the score in the log domain (temperature T) and sweep alpha; the
+  tree with the lowest cost wins.  Ties break on ids, so results are
+  deterministic for a given seed.
+* slicing: with a path fixed, repeatedly pick the bond whose removal most
+  reduces the largest intermediate (then the total cost), up to the requested
+  count or until the largest intermediate fits the cap.
+
+All sizes are log2 element counts (every edge dimension is a power of two).
+Costs are complex multiply-adds: a step costs the product of the dimensions of
+every edge of its two operands (batch x M x N x K).
+"""
+from __future__ import annotations
+
+import heapq
+import math
+from dataclasses import dataclass
+from typing import Dict, FrozenSet, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from .network import TensorNetwork
+
+
+@dataclass
+class Tree:
+    pairs: List[Tuple[int, int]]            # SSA: leaf i = i, step t makes n_leaves + t
+    sliced_edges: List[int]                  # slice id bit i <-> value of sliced_edges[i]
+    log2_max_intermediate: float             # of one sub-network
+    cost_per_slice: float                    # complex MACs of one sub-network
+    cost_variant_per_slice: float            # complex MACs of the steps that depend on a slice
+    n_leaves: int
+
+
+def log2dims(tn: TensorNetwork) -> List[float]:
+    out = []
+    for d in tn.edge_dim:
+        if d <= 0 or d & (d - 1):
+            raise ValueError("edge dimensions must be powers of two")
+        out.append(float(int(d).bit_length() - 1))
+    return out
+
+
+def _result(a: FrozenSet[int], b: FrozenSet[int], occ, keep, i, j) -> FrozenSet[int]:
+    out = set(a ^ b)
+    for e in a & b:
+        if e in keep or (occ[e] - {i, j}):
+            out.add(e)
+    return frozenset(out)
+
+
+def greedy(leaves: Sequence[FrozenSet[int]], lg: Sequence[float], keep: FrozenSet[int],
+           alpha: float = 1.0, temperature: float = 0.0, seed: int = 0) -> List[Tuple[int, int]]:
+    """Greedy pairwise order over ``leaves`` (edge sets); ``keep`` = output edges."""
+    rng = np.random.default_rng(seed)
+    live: Dict[int, FrozenSet[int]] = {i: frozenset(s) for i, s in enumerate(leaves)}
+    occ: Dict[int, set] = {}
+    for i, s in live.items():
+        for e in s:
+            occ.setdefault(e, set()).add(i)
+    size = lambda s: sum(lg[e] for e in s)  # noqa: E731
+    heap: list = []
+
+    def push(i, j):
+        if i > j:
+            i, j = j, i
+        c = _result(live[i], live[j], occ, keep, i, j)
+        sc = size(c)
+        score = 2.0 ** sc - alpha * (2.0 ** size(live[i]) + 2.0 ** size(live[j]))
+        if temperature > 0:
+            gumbel = -math.log(-math.log(rng.random() + 1e-300))
+            score = math.copysign(math.log2(abs(score) + 1.0), score) - temperature * gumbel
+        heapq.heappush(heap, (score, sc, i, j))
+
+    seen = set()
+    for e, ids in occ.items():
+        ids = sorted(ids)
+        for x in range(len(ids)):
+            for y in range(x + 1, len(ids)):
+                if (ids[x], ids[y]) not in seen:
+                    seen.add((ids[x], ids[y]))
+                    push(ids[x], ids[y])
+    pairs = []
+    nxt = len(leaves)
+    while len(live) > 1:
+        if heap:
+            _, _, i, j = heapq.heappop(heap)
+            if i not in live or j not in live:
+                continue
+        else:  # disconnected parts: outer product of the two smallest
+            ids = sorted(live, key=lambda t: (size(live[t]), t))
+            i, j = sorted(ids[:2])
+        c = _result(live[i], live[j], occ, keep, i, j)
+        pairs.append((i, j))
+        for e in live[i] | live[j]:
+            occ[e].discard(i)
+            occ[e].discard(j)
+        del live[i], live[j]
+        k = nxt
+        nxt += 1
+        live[k] = c
+        nbrs = set()
+        for e in c:
+            nbrs |= occ[e]
+            occ[e].add(k)
+        for m in sorted(nbrs):
+            push(m, k)
+    return pairs
+
+
+def replay(leaves: Sequence[FrozenSet[int]], pairs, keep: FrozenSet[int]):
+    """Edge sets of every node (leaves then steps) along ``pairs``."""
+    nodes = [frozenset(s) for s in leaves]
+    occ: Dict[int, set] = {}
+    for i, s in enumerate(nodes):
+        for e in s:
+            occ.setdefault(e, set()).add(i)
+    for (i, j) in pairs:
+        k = len(nodes)
+        c = _result(nodes[i], nodes[j], occ, keep, i, j)
+        for e in nodes[i] | nodes[j]:
+            occ[e].discard(i)
+            occ[e].discard(j)
+        for e in c:
+            occ[e].add(k)
+        nodes.append(c)
+    return nodes
+
+
+def _incidence(nodes, pairs, n_leaves, n_edges, lg):
+    """Per-node and per-step log2 sizes and edge-incidence matrices."""
+    node_sz = np.array([sum(lg[e] for e in s) for s in nodes])
+    node_inc = np.zeros((n_edges, len(nodes)), dtype=np.float64)
+    for k, s in enumerate(nodes):
+        for e in s:
+            node_inc[e, k] = lg[e]
+    step_sets = [nodes[i] | nodes[j] for (i, j) in pairs]
+    step_sz = np.array([sum(lg[e] for e in s) for s in step_sets])
+    step_inc = np.zeros((n_edges, len(pairs)), dtype=np.float64)
+    for t, s in enumerate(step_sets):
+        for e in s:
+            step_inc[e, t] = lg[e]
+    return node_sz, node_inc, step_sz, step_inc
+
+
+def tree_stats(leaves, pairs, lg, keep, sliced=()):
+    """(log2 max intermediate, cost per slice, variant cost per slice) of a path
+    whose sliced edges are removed from the leaves."""
+    sl = set(sliced)
+    stripped = [frozenset(x - sl) for x in leaves]
+    nodes = replay(stripped, pairs, keep)
+    L = len(leaves)
+    variant = [bool(set(x) & sl) for x in leaves]
+    mx = max(sum(lg[e] for e in s) for s in nodes)
+    cost = vcost = 0.0
+    for (i, j) in pairs:
+        c = 2.0 ** sum(lg[e] for e in (nodes[i] | nodes[j]))
+        v = variant[i] or variant[j]
+        variant.append(v)
+        cost += c
+        vcost += c if v else 0.0
+    del L
+    return mx, cost, vcost
+
+
+def choose_slices(leaves, pairs, lg, keep, n_edges: int, n_sliced: int = 0,
+                  cap_log2: Optional[float] = None) -> List[int]:
+    """Greedy slicing of bonds along a fixed path (vectorised over candidates)."""
+    nodes = replay(leaves, pairs, keep)
+    count: Dict[int, int] = {}
+    for s in leaves:
+        for e in s:
+            count[e] = count.get(e, 0) + 1
+    bonds = np.array(sorted(e for e, c in count.items() if c == 2 and e not in keep), dtype=np.int64)
+    node_sz, node_inc, step_sz, step_inc = _incidence(nodes, pairs, len(leaves), n_edges, lg)
+    chosen: List[int] = []
+    cur_node = node_sz.copy()
+    cur_step = step_sz.copy()
+    lg_arr = np.asarray(lg)
+    while True:
+        mx = cur_node.max()
+        if len(chosen) >= n_sliced and (cap_log2 is None or mx <= cap_log2):
+            break
+        mask = np.ones(len(bonds), dtype=bool)
+        for e in chosen:
+            mask &= bonds != e
+        cand = bonds[mask]
+        if cand.size == 0:
+            raise ValueError("no bond left to slice")
+        new_max = (cur_node[None, :] - node_inc[cand]).max(axis=1)
+        s_log = sum(lg[e] for e in chosen)
+        new_cost = np.exp2(cur_step[None, :] - step_inc[cand]).sum(axis=1) * np.exp2(s_log + lg_arr[cand])
+        order = np.lexsort((cand, new_cost, new_max))
+        e = int(cand[order[0]])
+        chosen.append(e)
+        cur_node = cur_node - node_inc[e]
+        cur_step = cur_step - step_inc[e]
+    return chosen
+
+
+SWEEP = [(1.0, 0.0), (2.0, 0.0), (1.0, 0.25), (1.5, 0.25), (2.0, 0.25), (2.0, 0.5), (1.5, 0.5),
+         (3.0, 0.5), (2.0, 0.75)]
+
+
+def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = None,
+              restarts: int = 4, seed: int = 0, sliced: Optional[Sequence[int]] = None) -> Tree:
+    """Search paths over the alpha/temperature sweep (``restarts`` seeds per noisy
+    setting), slice each (unless ``sliced`` is given), keep the cheapest total."""
+    lg = log2dims(tn)
+    keep = frozenset(tn.output_edges())
+    leaves = [frozenset(e) for e in tn.leaf_edges]
+    best = None
+    for (alpha, T) in SWEEP:
+        for r in range(restarts if T > 0 else 1):
+            pairs = greedy(leaves, lg, keep, alpha, T, seed + 1000 * r + 7)
+            if sliced is None:
+                sl = choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced, cap_log2) \
+                    if (n_sliced or cap_log2 is not None) else []
+            else:
+                sl = list(sliced)
+            mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
+            if cap_log2 is not None and mx > cap_log2:
+                continue
+            key = (cost * 2.0 ** len(sl), mx)
+            if best is None or key < best[0]:
+                best = (key, pairs, sl, mx, cost, vcost)
+    if best is None:
+        raise ValueError("no path fits the memory cap")
+    _, pairs, sl, mx, cost, vcost = best
+    return Tree(pairs=pairs, sliced_edges=list(sl), log2_max_intermediate=mx,
+                cost_per_slice=cost, cost_variant_per_slice=vcost, n_leaves=len(leaves))

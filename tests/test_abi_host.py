@@ -1,0 +1,127 @@
+"""Host-only checks of the C ABI: the library builds, loads and exports every
+declared symbol; plan validation and host-side planning (no device work)."""
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2406_18889_gb300 import build as Bd
+    Bd.build()
+    from paper_2406_18889_gb300 import binding
+    return binding
+
+
+def test_exports_every_declared_symbol(lib):
+    header = (ROOT / "include" / "tn.h").read_text()
+    declared = set(re.findall(r"^(?:tn_status|const char\*)\s+(tn_\w+)\(", header, re.M))
+    assert declared >= {"tn_plan_create", "tn_contract_slices", "tn_contract_slices_batched",
+                        "tn_topk_postprocess", "tn_xeb"}
+    L = lib.load()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(lib.EXPORTS) == declared
+    assert "sm_103a" in lib.tn_version()
+
+
+def _flat(prep):
+    from paper_2406_18889_gb300 import engine as E
+    return E.flatten_network(prep.tn)
+
+
+def _create(lib, prep, flags=None, **kw):
+    rank, edges, data = _flat(prep)
+    tn, tree = prep.tn, prep.tree
+    args = dict(leaf_rank=rank, leaf_edges=edges, edge_dim=tn.edge_dim, leaf_data=data,
+                open_edges=tn.open_edges, block_edge=tn.block_edge,
+                pairs=np.asarray(tree.pairs).reshape(-1), sliced_edges=tree.sliced_edges,
+                prec=0, flags=lib.TN_FLAG_PLAN_ONLY if flags is None else flags, max_slice_batch=8)
+    args.update(kw)
+    return lib.tn_plan_create(**args)
+
+
+@pytest.fixture(scope="module")
+def prep():
+    from paper_2406_18889_gb300 import engine as E
+    w = W.workload("grid3x4_d8", cycles=10, l=6, G=8)
+    return E.prepare(w, n_sliced=3, restarts=1)
+
+
+def test_plan_only_cost_model_matches_planner(lib, prep):
+    h = _create(lib, prep)
+    q = lib.tn_plan_query(h)
+    # useful flops per slice = 8 x complex MACs of one sub-network (Table I convention)
+    assert q["useful_flops_per_slice"] == pytest.approx(8 * prep.tree.cost_per_slice, rel=1e-12)
+    assert q["workspace_bytes"] > 0 and q["workspace_bytes"] % 256 == 0
+    st = lib.tn_plan_steps(h)
+    assert len(st["m"]) == len(prep.tree.pairs)
+    # every GEMM extent is a power of two and the variant steps are those above sliced leaves
+    for key in ("batch", "m", "n", "k"):
+        v = st[key]
+        assert np.all(v >= 1) and np.all((v & (v - 1)) == 0)
+    assert (st["kinds"] & 1).sum() >= 1
+    lib.tn_plan_destroy(h)
+
+
+def test_hoist_flag_marks_invariant_steps(lib, prep):
+    h = _create(lib, prep, flags=lib.TN_FLAG_PLAN_ONLY | lib.TN_FLAG_HOIST_INVARIANT)
+    k = lib.tn_plan_steps(h)["kinds"]
+    assert np.all(((k & 4) > 0) == ((k & 1) == 0))
+    lib.tn_plan_destroy(h)
+
+
+@pytest.mark.parametrize("mutate,status", [
+    ("bad_pair", 1), ("repeat_pair", 1), ("sliced_open", 1), ("sliced_twice", 1),
+    ("batch_not_pow2", 1), ("short_tree", 1), ("bf16_not_built", 5)])
+def test_plan_validation(lib, prep, mutate, status):
+    rank, edges, data = _flat(prep)
+    tn, tree = prep.tn, prep.tree
+    pairs = np.asarray(tree.pairs).reshape(-1).copy()
+    kw = {}
+    if mutate == "bad_pair":
+        pairs[0] = len(rank) + 5
+        kw["pairs"] = pairs
+    elif mutate == "repeat_pair":
+        pairs[2] = pairs[0]
+        pairs[3] = pairs[1]
+        kw["pairs"] = pairs
+    elif mutate == "sliced_open":
+        kw["sliced_edges"] = [tn.open_edges[0]]
+    elif mutate == "sliced_twice":
+        kw["sliced_edges"] = [tree.sliced_edges[0], tree.sliced_edges[0]]
+    elif mutate == "batch_not_pow2":
+        kw["max_slice_batch"] = 6
+    elif mutate == "short_tree":
+        kw["pairs"] = pairs[:-2]
+    elif mutate == "bf16_not_built":
+        kw["prec"] = 1
+    with pytest.raises(lib.TNError) as ei:
+        _create(lib, prep, **kw)
+    assert ei.value.status == status
+    assert lib.tn_last_error()
+
+
+def test_plan_only_rejects_contraction(lib, prep):
+    h = _create(lib, prep)
+    with pytest.raises(lib.TNError):
+        lib.tn_contract_slices(h, [0], 1 << 20, 0, 1 << 20, 1 << 30, 0)
+    lib.tn_plan_destroy(h)
+
+
+def test_topk_argument_validation(lib):
+    # rejected before any device work (so this runs without a GPU)
+    with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(0, 4, 1024, 8, 1.0, 0, 0, np.arange(10), 0, 0)
+    with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(16, 4, 1000, 8, 1.0, 0, 16, np.arange(10), 16, 16)  # B != 2^l
+    with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(16, 4, 1024, 0, 1.0, 0, 16, np.arange(10), 16, 16)  # k = 0
+    with pytest.raises(lib.TNError):
+        lib.tn_xeb(16, 0, 10)
