@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: sliced tensor-network contraction of a random circuit on GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch):
+  24-qubit 4x6 grid random circuit, 14 cycles (sqrt X/Y/W + fSim, ABCDCDAB),
+  6 sliced bonds (64 sub-networks), 10 open qubits (1024 amplitudes per block),
+  64 blocks of closed bitstrings; a step contracts all 64 slices with an FP64
+  cross-slice sum, keeps the top 64 strings per block and scores them by XEB.
+
+Metric: slices/s (whole job, all ranks) and useful complex TFLOP/s
+(8 x complex MACs of the sub-networks, the paper's Table I convention).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec c64] [--impl reference]
+
+N > 1 runs one process per GPU (torchrun); each rank samples its own 64
+blocks of the same circuit (independent problems, no collective on the data
+path) and the job's value is the sum over ranks; time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "grid4x6_d14"
+WORKLOAD_DESC = ("24-qubit 4x6 grid random circuit, 14 cycles, 6 sliced bonds (64 slices), "
+                 "l=10 open qubits (1024 amplitudes/block), G=64 blocks, top-64 per block")
+METRIC = "sliced-contraction slices/s (24-qubit 4x6 grid, 14 cycles, 64 slices) on 1 GB300"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def fp32_alu_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def max_over_ranks(x: float, dist, device="cpu") -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device="cpu") -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_workload(rank: int):
+    """The circuit is shared; rank r draws its own blocks of closed bitstrings."""
+    import workloads as W
+    w = W.workload(WORKLOAD)
+    if rank:
+        w.closed_bits = W.draw_closed_bitstrings(len(w.closed_qubits), w.G,
+                                                 seed=W.configs.SEED0 + 7919 * rank)
+    return w
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_slices_per_s(w, wires, slice_ids) -> float:
+    from oracle import einsum_tn as et
+    net = et.build_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    t0 = time.perf_counter()
+    et.contract_each_slice(net, wires, slice_ids)
+    return len(slice_ids) / (time.perf_counter() - t0)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def sliced_wires():
+    from paper_2406_18889_gb300 import engine as E
+    w = rank_workload(0)
+    prep = E.prepare(w)
+    return w, prep, [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w, prep, wires = sliced_wires()
+    sample = "1 slice of 64 per step, oracle O2 (naive FP64 einsum contractor, numpy matmul)"
+    for s in range(args.warmup):
+        oracle_slices_per_s(w, wires, [s % 64])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle_slices_per_s(w, wires, [(args.warmup + s) % 64])
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "complex128",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "arm": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_18889_gb300 import binding as B
+    from paper_2406_18889_gb300 import engine as E
+
+    w = rank_workload(rank)
+    prep = E.prepare(w)
+    plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch)
+    S = plan.n_slices_total
+    ids = np.arange(S, dtype=np.int64)
+    base_np = w.block_base()
+    pos = w.open_bit_pos()
+    base = torch.as_tensor(base_np, device="cuda")
+    amps = torch.empty((plan.G, plan.J), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    info = plan.info
+    useful_per_slice = info["useful_flops_per_slice"]
+
+    def step():
+        plan.contract(ids, out=amps)
+        idx, p = E.topk(amps, w.k, 1.0, base, pos)
+        x = E.xeb(p, w.n_qubits)  # f = 1: the selected p are the strings' probabilities
+        return idx, p, x
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # evict L2 (129 MB) between steps; not inside the timed events
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if dist:
+            dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms = max_over_ranks(ms, dist, "cuda")
+    slices = sum_over_ranks(float(S * args.steps), dist, "cuda")
+    value = slices / (ms / 1e3)
+
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "slices/s",
+                              "ms_per_step": ms / args.steps, "only_timed": True}), flush=True)
+        plan.close()
+        return
+    # e2e: same step through the C ABI with host buffers (pinned), copies inside the timing
+    h_base = torch.as_tensor(base_np).pin_memory()
+    h_idx = torch.empty((w.G, w.k), dtype=torch.int64).pin_memory()
+    h_p = torch.empty((w.G, w.k), dtype=torch.float64).pin_memory()
+    h_ids = torch.as_tensor(ids).pin_memory()
+    d_base = torch.empty_like(base)
+
+    def e2e_step():
+        d_base.copy_(h_base, non_blocking=True)
+        plan.contract(h_ids.numpy(), out=amps)  # slice ids travel host -> device inside the call
+        idx, p = E.topk(amps, w.k, 1.0, d_base, pos)
+        x = E.xeb(p, w.n_qubits)
+        h_idx.copy_(idx, non_blocking=True)
+        h_p.copy_(p, non_blocking=True)
+        torch.cuda.synchronize()
+        return x
+
+    for _ in range(2):
+        e2e_step()
+    e2e_ms = 0.0
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
+
+    e2e_value = slices / (e2e_ms / 1e3)
+    h2d = h_base.numel() * 8 + S * 8
+    d2h = (h_idx.numel() + h_p.numel()) * 8 + 8
+
+    # per-kernel roofline: one profiled pass (events around every launch)
+    prof = B.tn_contract_slices_profile(plan.handle, ids, amps.data_ptr(), 0, plan.workspace.data_ptr(),
+                                        plan.workspace.numel(), stream.cuda_stream)
+    kinds = prof["kind"]
+    names = {0: "gemm_c64", 1: "bit_permute", 2: "gather", 3: "accumulate_fp64"}
+    per_kind = {names[k]: {"launches": int((kinds == k).sum()), "ms": float(prof["ms"][kinds == k].sum())}
+                for k in np.unique(kinds)}
+    g = kinds == 0
+    gemm_tflops = float(prof["flops"][g].sum() / (prof["ms"][g].sum() / 1e3) / 1e12)
+    peak = fp32_alu_peak_tflops()
+    launches_per_step = prof["n_launches"] + 2  # + top-k + XEB
+    roofline = {"bound": "alu", "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": gemm_tflops / peak, "traffic": None,
+                "kernel": "gemm_c64 (all launches of one step)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "per_kind": per_kind}
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        _, _, wires = sliced_wires()
+        v = oracle_slices_per_s(rank_workload(0), wires, [0, 1])
+        cpu = {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "2 of the 64 slices, oracle O2 (naive FP64 einsum contractor, numpy matmul)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "complex64" if args.prec == "c64" else args.prec,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec,
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"{world} independent block sets (one per GPU)"},
+        "useful_tflops": value * useful_per_slice / 1e12,
+        "useful_flops_per_slice": useful_per_slice,
+        "wall_s": wall,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "slices/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches_per_step * args.steps),
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="c64", choices=["c64", "bf16", "fp16"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="run warm-up and timed steps only (for ncu launch lists)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

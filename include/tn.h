@@ -209,6 +209,21 @@ tn_status tn_topk_postprocess(const void* amps, int64_t G, int64_t B, int32_t k,
  */
 tn_status tn_xeb(const double* q, int64_t n_sel, int32_t n_qubits, double* out_xeb, void* stream);
 
+/*
+ * Profiling form of tn_contract_slices: the same work launched directly (no
+ * graph) with a CUDA event pair around every kernel; synchronises `stream`
+ * and reports, per kernel launch in launch order, its class (0 = GEMM,
+ * 1 = transpose, 2 = slice gather, 3 = FP64 accumulate), its duration in
+ * milliseconds, and its algorithmic FLOPs (8 * batch*M*N*K for a GEMM, else 0)
+ * and bytes (operands + result for a GEMM; bytes read + written otherwise).
+ * Arrays hold max_records entries; *n_records is set to the number of
+ * launches (which may exceed max_records: the rest are dropped).
+ */
+tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices,
+                                     void* amps, int accumulate, void* workspace, size_t ws_bytes,
+                                     void* stream, int32_t max_records, int32_t* kind, float* ms,
+                                     double* flops, double* bytes, int32_t* n_records);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* tn_last_error(void);
 

@@ -24,8 +24,8 @@ TN_FLAG_NO_GRAPH = 0x2
 TN_FLAG_PLAN_ONLY = 0x4
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
-           "tn_contract_slices", "tn_contract_slices_batched", "tn_topk_postprocess", "tn_xeb",
-           "tn_last_error", "tn_version")
+           "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
+           "tn_topk_postprocess", "tn_xeb", "tn_last_error", "tn_version")
 
 
 class TNError(RuntimeError):
@@ -76,6 +76,10 @@ def load() -> ctypes.CDLL:
     lib.tn_contract_slices.argtypes = [vp, p_i64, i64, vp, ctypes.c_int, vp, u64, vp]
     lib.tn_contract_slices_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(p_i64), p_i64,
                                                ctypes.POINTER(vp), ctypes.c_int, vp, u64, vp]
+    lib.tn_contract_slices_profile.argtypes = [vp, p_i64, i64, vp, ctypes.c_int, vp, u64, vp, i32, p_i32,
+                                               ctypes.POINTER(ctypes.c_float),
+                                               ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), p_i32]
     lib.tn_topk_postprocess.argtypes = [vp, i64, i64, i32, ctypes.c_double, ctypes.c_int, vp, p_i64,
                                         i32, vp, vp, vp]
     lib.tn_xeb.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double), vp]
@@ -150,6 +154,23 @@ def tn_contract_slices(plan: int, slice_ids, amps_ptr: int, accumulate: int, ws_
     _check(load().tn_contract_slices(ctypes.c_void_p(plan), _p(ids, ctypes.c_int64), len(ids),
                                      ctypes.c_void_p(amps_ptr), int(accumulate), ctypes.c_void_p(ws_ptr),
                                      int(ws_bytes), ctypes.c_void_p(stream)))
+
+
+def tn_contract_slices_profile(plan: int, slice_ids, amps_ptr: int, accumulate: int, ws_ptr: int,
+                               ws_bytes: int, stream: int = 0, max_records: int = 1 << 16) -> dict:
+    ids = _i64(slice_ids)
+    kind = np.zeros(max_records, np.int32)
+    ms = np.zeros(max_records, np.float32)
+    flops = np.zeros(max_records, np.float64)
+    nbytes = np.zeros(max_records, np.float64)
+    n = ctypes.c_int32()
+    _check(load().tn_contract_slices_profile(
+        ctypes.c_void_p(plan), _p(ids, ctypes.c_int64), len(ids), ctypes.c_void_p(amps_ptr), int(accumulate),
+        ctypes.c_void_p(ws_ptr), int(ws_bytes), ctypes.c_void_p(stream), max_records,
+        _p(kind, ctypes.c_int32), _p(ms, ctypes.c_float), _p(flops, ctypes.c_double),
+        _p(nbytes, ctypes.c_double), ctypes.byref(n)))
+    c = min(n.value, max_records)
+    return dict(kind=kind[:c], ms=ms[:c], flops=flops[:c], bytes=nbytes[:c], n_launches=n.value)
 
 
 def tn_contract_slices_batched(plans: Sequence[int], slice_ids: Sequence, amps_ptrs: Sequence[int],

@@ -45,7 +45,7 @@ static tn_status guarded(F&& f) {
 }
 
 static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
-                         size_t ws_bytes, cudaStream_t s) {
+                         size_t ws_bytes, cudaStream_t s, std::vector<LaunchRecord>* rec = nullptr) {
   TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
   TN_CHECK(amps != nullptr, TN_ERR_INVALID_ARG, "amps is null");
   TN_CHECK(n >= 0, TN_ERR_INVALID_ARG, "n_slices < 0");
@@ -71,7 +71,7 @@ static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int
     // pageable host -> device: the source is staged before the call returns
     TN_CUDA(cudaMemcpyAsync(P.d_slice_ids, chunk.data(), sizeof(int64_t) * P.B, cudaMemcpyHostToDevice, s));
     TN_CUDA(cudaMemcpyAsync(P.d_n_valid, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    run_batch(P, ws, amps, start == 0 ? accumulate : 1, s);
+    run_batch(P, ws, amps, start == 0 ? accumulate : 1, s, rec);
   }
   TN_CUDA(cudaGetLastError());
 }
@@ -210,6 +210,35 @@ tn_status tn_xeb(const double* q, int64_t n_sel, int32_t n_qubits, double* out_x
     TN_CUDA(cudaFreeAsync(d_out, s));
     TN_CUDA(cudaStreamSynchronize(s));
   });
+}
+
+tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices, void* amps,
+                                     int accumulate, void* workspace, size_t ws_bytes, void* stream,
+                                     int32_t max_records, int32_t* kind, float* ms, double* flops,
+                                     double* bytes, int32_t* n_records) {
+  std::vector<LaunchRecord> rec;
+  tn_status st = guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    TN_CHECK(max_records >= 0 && (max_records == 0 || (kind && ms && flops && bytes)), TN_ERR_INVALID_ARG,
+             "null record array");
+    cudaStream_t s = (cudaStream_t)stream;
+    contract_one(*plan->p, slice_ids, n_slices, amps, accumulate, workspace, ws_bytes, s, &rec);
+    TN_CUDA(cudaStreamSynchronize(s));
+    if (n_records) *n_records = (int32_t)rec.size();
+    for (int32_t i = 0; i < (int32_t)rec.size() && i < max_records; ++i) {
+      kind[i] = rec[i].kind;
+      flops[i] = rec[i].flops;
+      bytes[i] = rec[i].bytes;
+      float t = 0.f;
+      TN_CUDA(cudaEventElapsedTime(&t, rec[i].start, rec[i].stop));
+      ms[i] = t;
+    }
+  });
+  for (auto& r : rec) {
+    if (r.start) cudaEventDestroy(r.start);
+    if (r.stop) cudaEventDestroy(r.stop);
+  }
+  return st;
 }
 
 const char* tn_last_error(void) { return g_last_error.c_str(); }

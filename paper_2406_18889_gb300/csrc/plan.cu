@@ -651,13 +651,39 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
 }
 
 // ---------------------------------------------------------------- execute
-static void enqueue_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t s) {
+namespace {
+struct Recorder {
+  std::vector<LaunchRecord>* rec;
+  cudaStream_t s;
+  void begin(int kind, double flops, double bytes) {
+    if (!rec) return;
+    LaunchRecord r{kind, flops, bytes, nullptr, nullptr};
+    TN_CUDA(cudaEventCreate(&r.start));
+    TN_CUDA(cudaEventCreate(&r.stop));
+    TN_CUDA(cudaEventRecord(r.start, s));
+    rec->push_back(r);
+  }
+  void end() {
+    if (rec) TN_CUDA(cudaEventRecord(rec->back().stop, s));
+  }
+};
+}  // namespace
+
+static void enqueue_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t s,
+                          std::vector<LaunchRecord>* rec) {
   char* wb = (char*)ws;
   char* pb = (char*)P.d_plan;
+  Recorder R{rec, s};
+  const double eb = P.elem_bytes;
   auto base = [&](int node) -> char* { return (P.nodes[node].plan_mem ? pb : wb) + P.nodes[node].off; };
-  if (!P.gather.empty())
+  if (!P.gather.empty()) {
+    double bytes = 0;
+    for (auto& g : P.gather) bytes += 2.0 * g.rest * P.B * eb;
+    R.begin(2, 0, bytes);
     launch_gather_leaves(P.d_gather, (int)P.gather.size(), P.gather_max_rest, P.d_slice_ids, P.B, pb, wb,
                          s);
+    R.end();
+  }
   for (auto& S : P.steps) {
     if (S.hoisted) continue;
     GemmParams g = S.gp;
@@ -665,16 +691,26 @@ static void enqueue_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStr
     g.B = base(S.b);
     char* dst = base(S.c);
     g.C = S.post_perm ? wb + S.tmp_off : dst;
+    R.begin(0, 8.0 * S.cost,
+            eb * ((double)P.nodes[S.a].elems + (double)P.nodes[S.b].elems + (double)P.nodes[S.c].elems));
     launch_gemm_c64(g, 0, s);
-    if (S.post_perm) launch_bit_permute_c64(wb + S.tmp_off, dst, S.perm, s);
+    R.end();
+    if (S.post_perm) {
+      R.begin(1, 0, 2.0 * eb * (double)P.nodes[S.c].elems);
+      launch_bit_permute_c64(wb + S.tmp_off, dst, S.perm, s);
+      R.end();
+    }
   }
+  R.begin(3, 0, eb * (double)P.nodes[P.root].elems + 16.0 * P.G * P.J * (accumulate ? 2 : 1));
   launch_accumulate_c64(base(P.root), P.root_sb, P.root_sg, P.root_sj, P.G, P.J, P.d_n_valid, P.B, amps,
                         accumulate, s);
+  R.end();
 }
 
-void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream) {
-  if (P.flags & TN_FLAG_NO_GRAPH) {
-    enqueue_batch(P, ws, amps, accumulate, stream);
+void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream,
+               std::vector<LaunchRecord>* rec) {
+  if ((P.flags & TN_FLAG_NO_GRAPH) || rec) {
+    enqueue_batch(P, ws, amps, accumulate, stream, rec);
     TN_CUDA(cudaGetLastError());
     return;
   }
@@ -685,7 +721,13 @@ void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t strea
     }
     cudaGraph_t g = nullptr;
     TN_CUDA(cudaStreamBeginCapture(P.capture_stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_batch(P, ws, amps, accumulate, P.capture_stream);
+    try {
+      enqueue_batch(P, ws, amps, accumulate, P.capture_stream, nullptr);
+    } catch (...) {
+      cudaStreamEndCapture(P.capture_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
     cudaError_t e = cudaStreamEndCapture(P.capture_stream, &g);
     if (e != cudaSuccess) fail(TN_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&P.graph, g, 0);

@@ -84,7 +84,16 @@ struct Plan {
 std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc* tree,
                                  const tn_plan_options* opt, cudaStream_t stream);
 
+// Per-launch profiling record (tn_contract_slices_profile).
+struct LaunchRecord {
+  int kind;
+  double flops, bytes;
+  cudaEvent_t start, stop;
+};
+
 // Queue one batch (n_valid <= B slice ids already in d_slice_ids) into amps.
-void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream);
+// With `rec`, launches directly and brackets every kernel with an event pair.
+void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream,
+               std::vector<LaunchRecord>* rec = nullptr);
 
 }  // namespace tn
