@@ -224,6 +224,35 @@ tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, i
                                      void* stream, int32_t max_records, int32_t* kind, float* ms,
                                      double* flops, double* bytes, int32_t* n_records);
 
+/*
+ * tn_contract_slices_noalloc -- tn_contract_slices without device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, for example a host application whose device memory
+ * is owned entirely by another allocator (a framework's caching pool reserved
+ * up front), or a latency-critical loop where an allocation and the device
+ * synchronisation it may imply are not allowed.  The caller still passes the
+ * slice ids (host) and the output amps (device complex128 [G][2^l]), with the
+ * same meaning as in tn_contract_slices.
+ *
+ * The workspace is a library-owned static device array of
+ * TN_STATIC_WORKSPACE_BYTES (64 MiB), which every GPU that loads the library
+ * keeps until the process exits.  A plan whose workspace_bytes
+ * (tn_plan_query) exceeds it is rejected with TN_ERR_INVALID_ARG before any
+ * work is queued; build such plans with a smaller max_slice_batch or use
+ * tn_contract_slices.  The first call on each device looks up the array's
+ * device address (which also loads the library's device code on that device)
+ * with that device current; make that first call before any stream capture.
+ * Kernels are launched directly; no CUDA graph is built.  All calls share the
+ * one array, which keeps the previous call's contents: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race
+ * and give wrong results -- serialise them.  No part of the array needs to
+ * start at zero.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define TN_STATIC_WORKSPACE_BYTES (64ull << 20)
+tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices,
+                                     void* amps, int accumulate, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* tn_last_error(void);
 

@@ -25,7 +25,7 @@ TN_FLAG_PLAN_ONLY = 0x4
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
-           "tn_topk_postprocess", "tn_xeb", "tn_last_error", "tn_version")
+           "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_last_error", "tn_version")
 
 
 class TNError(RuntimeError):
@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
     lib.tn_topk_postprocess.argtypes = [vp, i64, i64, i32, ctypes.c_double, ctypes.c_int, vp, p_i64,
                                         i32, vp, vp, vp]
     lib.tn_xeb.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.tn_contract_slices_noalloc.argtypes = [vp, p_i64, i64, vp, ctypes.c_int, vp]
     for name in EXPORTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
     lib.tn_last_error.restype = ctypes.c_char_p
@@ -201,6 +202,15 @@ def tn_xeb(q_ptr: int, n_sel: int, n_qubits: int, stream: int = 0) -> float:
     _check(load().tn_xeb(ctypes.c_void_p(q_ptr), int(n_sel), int(n_qubits), ctypes.byref(out),
                          ctypes.c_void_p(stream)))
     return out.value
+
+
+def tn_contract_slices_noalloc(plan: int, slice_ids, amps_ptr: int, accumulate: int, stream: int = 0) -> None:
+    """Same contraction as tn_contract_slices, using the library's static 64 MiB
+    device workspace instead of a caller-allocated one (no device allocation)."""
+    ids = _i64(slice_ids)
+    _check(load().tn_contract_slices_noalloc(ctypes.c_void_p(plan), _p(ids, ctypes.c_int64), len(ids),
+                                             ctypes.c_void_p(amps_ptr), int(accumulate),
+                                             ctypes.c_void_p(stream)))
 
 
 def tn_last_error() -> str:

@@ -1,6 +1,7 @@
 // The C ABI declared in include/tn.h.  Validation happens before any device
 // work; no C++ exception crosses the boundary.
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -43,6 +44,10 @@ static tn_status guarded(F&& f) {
     return TN_ERR_INVALID_ARG;
   }
 }
+
+// Run f under the same error handling as the C entry points (used by
+// entry points defined in other translation units).
+tn_status guarded_call(const std::function<void()>& f) { return guarded(f); }
 
 static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
                          size_t ws_bytes, cudaStream_t s, std::vector<LaunchRecord>* rec = nullptr) {

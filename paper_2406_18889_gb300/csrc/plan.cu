@@ -707,6 +707,12 @@ static void enqueue_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStr
   R.end();
 }
 
+// Direct launches only (no graph is built or replayed).
+void run_batch_direct(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream) {
+  enqueue_batch(P, ws, amps, accumulate, stream, nullptr);
+  TN_CUDA(cudaGetLastError());
+}
+
 void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream,
                std::vector<LaunchRecord>* rec) {
   if ((P.flags & TN_FLAG_NO_GRAPH) || rec) {
