@@ -253,6 +253,18 @@ tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, i
 tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices,
                                      void* amps, int accumulate, void* stream);
 
+/*
+ * Self-test of the tensor-core GEMM on this device: random complex operands
+ * in fp16 (prec = TN_PREC_FP16) or bf16 (TN_PREC_BF16), A [nbt][M][K] and
+ * B [nbt][K][N] (complex extents), multiplied by the tcgen05 kernel (after
+ * expanding B to its real 2x2 form) and by a plain FP32 CUDA-core reference
+ * from the same 16-bit inputs.  *max_rel_err = max |C_tc - C_ref| /
+ * max |C_ref|.  Allocates and frees its own buffers; synchronises `stream`.
+ * Returns TN_ERR_TIMEOUT if a bounded device wait gave up.
+ */
+tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int32_t prec, uint64_t seed,
+                              double* max_rel_err, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* tn_last_error(void);
 

@@ -25,7 +25,8 @@ TN_FLAG_PLAN_ONLY = 0x4
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
-           "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_last_error", "tn_version")
+           "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_last_error",
+           "tn_version")
 
 
 class TNError(RuntimeError):
@@ -84,6 +85,8 @@ def load() -> ctypes.CDLL:
                                         i32, vp, vp, vp]
     lib.tn_xeb.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double), vp]
     lib.tn_contract_slices_noalloc.argtypes = [vp, p_i64, i64, vp, ctypes.c_int, vp]
+    lib.tn_selftest_gemm_tc.argtypes = [i64, i64, i64, i64, i32, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_double), vp]
     for name in EXPORTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
     lib.tn_last_error.restype = ctypes.c_char_p
@@ -211,6 +214,13 @@ def tn_contract_slices_noalloc(plan: int, slice_ids, amps_ptr: int, accumulate: 
     _check(load().tn_contract_slices_noalloc(ctypes.c_void_p(plan), _p(ids, ctypes.c_int64), len(ids),
                                              ctypes.c_void_p(amps_ptr), int(accumulate),
                                              ctypes.c_void_p(stream)))
+
+
+def tn_selftest_gemm_tc(nbt: int, M: int, N: int, K: int, prec: int, seed: int = 1, stream: int = 0) -> float:
+    out = ctypes.c_double()
+    _check(load().tn_selftest_gemm_tc(int(nbt), int(M), int(N), int(K), int(prec), int(seed),
+                                      ctypes.byref(out), ctypes.c_void_p(stream)))
+    return out.value
 
 
 def tn_last_error() -> str:

@@ -246,6 +246,34 @@ tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, i
   return st;
 }
 
+tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int32_t prec, uint64_t seed,
+                              double* max_rel_err, void* stream) {
+  return guarded([&] {
+    TN_CHECK(max_rel_err != nullptr, TN_ERR_INVALID_ARG, "max_rel_err is null");
+    TN_CHECK(prec == TN_PREC_BF16 || prec == TN_PREC_FP16, TN_ERR_INVALID_ARG, "prec must be bf16 or fp16");
+    TN_CHECK(nbt >= 1 && M >= 1 && N >= 1 && K >= 4 && nbt * M * K <= (int64_t(1) << 30) &&
+                 nbt * K * N <= (int64_t(1) << 30) && nbt * M * N <= (int64_t(1) << 30),
+             TN_ERR_INVALID_ARG, "self-test shape out of range");
+    TN_CHECK(K % 4 == 0 && nbt <= 65535, TN_ERR_INVALID_ARG, "K must be a multiple of 4");
+    cudaStream_t s = (cudaStream_t)stream;
+    int* d_err = nullptr;
+    TN_CUDA(cudaMalloc(&d_err, sizeof(int)));
+    TN_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    double r = 0;
+    try {
+      r = selftest_gemm_tc(nbt, M, N, K, prec == TN_PREC_BF16, seed, s, d_err);
+    } catch (...) {
+      cudaFree(d_err);
+      throw;
+    }
+    int h_err = 0;
+    TN_CUDA(cudaMemcpy(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaFree(d_err);
+    TN_CHECK(h_err == 0, TN_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait timed out");
+    *max_rel_err = r;
+  });
+}
+
 const char* tn_last_error(void) { return g_last_error.c_str(); }
 
 const char* tn_version(void) { return "tn-gb300 0.1 (sm_103a)"; }

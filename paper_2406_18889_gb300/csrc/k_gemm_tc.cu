@@ -1,0 +1,516 @@
+// Tensor-core GEMM (tcgen05 + TMA + TMEM) for the reduced-precision complex
+// path.
+//
+// A pairwise contraction (arXiv 2406.18889, Sec. III, per-step contraction) in
+// complex numbers is lowered to ONE real GEMM ("stacked 4M"): with complex
+// elements stored interleaved (re, im) in fp16/bf16,
+//   A'[m][2k+r]          = (Re A, Im A)[m][k]            (A used as stored)
+//   B'[2n+c][2k+r]       = [[Re B, -Im B], [Im B, Re B]]  (expanded from B)
+//   C'[m][2n+c] = sum_k' A'[m][k'] B'[2n+c][k']  = (Re C, Im C)[m][n]
+// so the real GEMM's output is already interleaved complex.  8 real flops per
+// complex multiply-add: the useful flop count of the paper's Table I
+// convention, with no 3M cancellation.
+//
+// Kernel: one CTA per 128 x BN output tile (real columns), 6 warps:
+//   warp 0      TMA producer: 3-D tiled loads of A' (box 64 x 128) and B'
+//               (box 64 x BN), 128-byte swizzle, into a 4-stage ring;
+//   warp 1      allocates BN TMEM columns, one thread issues tcgen05.mma
+//               (kind::f16, M = 128, N = BN, K = 16, FP32 accumulate in TMEM)
+//               and tcgen05.commit releases ring stages / signals the end;
+//   warps 2..5  epilogue: tcgen05.ld rows of the accumulator (warp w reads
+//               TMEM lanes 32*(w%4)..+31), scale by 2^shift, convert, store.
+// Every mbarrier wait is bounded by the global timer (2 s); on timeout the
+// kernel raises the device error flag and every role stops; the producer and
+// the MMA thread drain their own in-flight work (bounded) before TMEM is freed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstring>
+#include <string>
+
+#include "tn_internal.h"
+
+namespace tn {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // real k per stage: one 128-byte swizzle row of 16-bit values
+constexpr int STAGES = 4;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true when the phase with `parity` has completed; false on abort or timeout
+__device__ bool wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*(volatile int*)err) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
+                                            int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1 (tcgen05)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // version
+  d |= (uint64_t)2 << 61;             // swizzle: 128B
+  return d;
+}
+// instruction descriptor, kind::f16: D = F32, A/B = F16 (0) or BF16 (1), both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int n, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int BN>
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)STAGES * (BM + BN) * BK * 2 + 256;
+}
+
+template <int BN, bool BF16>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   TcGemmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + STAGES * BM * BK * 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * BN * BK * 2);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x, m_tile = blockIdx.y;
+  const int bt = blockIdx.z;
+  const int k_tiles = (int)((2 * p.K + BK - 1) / BK);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kt = 0; kt < k_tiles; ++kt) {
+        const int s = kt % STAGES;
+        const uint32_t use = kt / STAGES;
+        if (kt >= STAGES && !wait_bounded(&empty[s], (use & 1) ^ 1, p.err)) break;
+        mbar_expect_tx(&full[s], (uint32_t)((BM + BN) * BK * 2));
+        tma_load_3d(&tmA, &full[s], sA + s * BM * BK * 2, kt * BK, m_tile * BM, bt);
+        tma_load_3d(&tmB, &full[s], sB + s * BN * BK * 2, kt * BK, n_tile * BN, bt);
+        ++issued;
+      }
+      // drain: every issued load must have landed before the CTA can exit
+      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(&full[kt % STAGES], (kt / STAGES) & 1) && gtimer() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BN, BF16);
+      for (int kt = 0; kt < k_tiles; ++kt) {
+        const int s = kt % STAGES;
+        if (!wait_bounded(&full[s], (kt / STAGES) & 1, p.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
+        const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t ad = sw128_desc(a0 + kk * 32);
+          const uint64_t bd = sw128_desc(b0 + kk * 32);
+          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&empty[s]))
+                     : "memory");
+      }
+      // `done` completes when every MMA issued above has finished
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(done))
+                   : "memory");
+    }
+  } else {
+    // epilogue warps 2..5
+    const bool ok = wait_bounded(done, 0, p.err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int quarter = warp & 3;
+    const int64_t m = (int64_t)m_tile * BM + quarter * 32 + lane;
+    if (ok) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < p.M) {
+          const int64_t n0 = ((int64_t)n_tile * BN + c0) / 2;
+          const int64_t base = (int64_t)bt * p.sc_bt + m * p.sc_m;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t n = n0 + j;
+            if (n >= p.N) break;
+            const float re = __uint_as_float(v[2 * j]) * p.scale;
+            const float im = __uint_as_float(v[2 * j + 1]) * p.scale;
+            const int64_t o = base + n * p.sc_n;
+            if (p.out_kind == 2) {
+              reinterpret_cast<float2*>(p.C)[o] = make_float2(re, im);
+            } else if (p.out_kind == 1) {
+              reinterpret_cast<__nv_bfloat162*>(p.C)[o] = __floats2bfloat162_rn(re, im);
+            } else {
+              reinterpret_cast<__half2*>(p.C)[o] = __floats2half2_rn(re, im);
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // all MMAs must be complete before their accumulator is freed
+    if (lane == 0) {
+      const uint64_t t0 = gtimer();
+      while (!mbar_try_wait(done, 0) && gtimer() - t0 < kWaitNs) {
+      }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* ptr = nullptr;
+    TN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q));
+    TN_CHECK(q == cudaDriverEntryPointSuccess && ptr, TN_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// 3-D map over a 16-bit real matrix: dims {inner, rows, batch}, strides in bytes
+void make_map(CUtensorMap* map, const void* base, bool bf16, uint64_t inner, uint64_t rows, uint64_t batch,
+              uint64_t row_bytes, uint64_t batch_bytes, uint32_t box_rows) {
+  TN_CHECK((reinterpret_cast<uintptr_t>(base) & 15) == 0, TN_ERR_UNSUPPORTED, "TMA base not 16-byte aligned");
+  TN_CHECK(row_bytes % 16 == 0 && batch_bytes % 16 == 0, TN_ERR_UNSUPPORTED, "TMA stride not 16-byte aligned");
+  cuuint64_t dims[3] = {inner, rows, batch};
+  cuuint64_t strides[2] = {row_bytes, batch_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)BK, box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = encode_fn()(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                           const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  TN_CHECK(r == CUDA_SUCCESS, TN_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
+template <int BN, bool BF16>
+void launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const TcGemmParams& p, cudaStream_t s) {
+  const size_t sm = smem_bytes<BN>();
+  static bool attr = false;
+  if (!attr) {
+    TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  dim3 grid((unsigned)((2 * p.N + BN - 1) / BN), (unsigned)((p.M + BM - 1) / BM), (unsigned)p.nbt);
+  tc_gemm_kernel<BN, BF16><<<grid, 192, sm, s>>>(ma, mb, p);
+}
+
+}  // namespace
+
+bool tc_gemm_supported(int64_t nbt, int64_t M, int64_t N, int64_t K, int64_t sa_bt, int64_t sa_m, int64_t sa_k) {
+  return sa_k == 1 && K >= 4 && M >= 1 && N >= 1 && nbt >= 1 && nbt <= 65535 && sa_m % 4 == 0 &&
+         (nbt == 1 || sa_bt % 4 == 0) && (M + BM - 1) / BM <= 65535;
+}
+
+int tc_gemm_bn(int64_t N) {
+  const int64_t n2 = 2 * N;
+  return n2 >= 256 ? 256 : n2 >= 128 ? 128 : n2 >= 64 ? 64 : 32;
+}
+
+// A: complex 16-bit [bt][M][K] with k contiguous (strides sa_bt, sa_m in complex
+// elements); Bx: expanded real [bt][2N][pitch] (pitch = round_up(2K, 64)).
+void launch_gemm_tc(const void* A, int64_t sa_bt, int64_t sa_m, const void* Bx, const TcGemmParams& p, bool bf16,
+                    cudaStream_t s) {
+  if (p.nbt <= 0 || p.M <= 0 || p.N <= 0) return;
+  TN_CHECK(tc_gemm_supported(p.nbt, p.M, p.N, p.K, sa_bt, sa_m, 1), TN_ERR_UNSUPPORTED,
+           "shape not supported by the tensor-core GEMM");
+  const int bn = p.bn;
+  const uint64_t pitch = (uint64_t)((2 * p.K + BK - 1) / BK * BK);
+  CUtensorMap ma, mb;
+  const uint64_t a_row = (uint64_t)sa_m * 4, a_bt = p.nbt > 1 ? (uint64_t)sa_bt * 4 : a_row * (uint64_t)p.M;
+  make_map(&ma, A, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row,
+           (a_bt + 15) / 16 * 16, BM);
+  make_map(&mb, Bx, bf16, pitch, (uint64_t)(2 * p.N), (uint64_t)p.nbt, pitch * 2, pitch * 2 * 2 * p.N,
+           (uint32_t)bn);
+#define TN_TC_CASE(BNV)                                        \
+  case BNV:                                                    \
+    if (bf16)                                                  \
+      launch_bn<BNV, true>(ma, mb, p, s);                      \
+    else                                                       \
+      launch_bn<BNV, false>(ma, mb, p, s);                     \
+    break;
+  switch (bn) {
+    TN_TC_CASE(32)
+    TN_TC_CASE(64)
+    TN_TC_CASE(128)
+    TN_TC_CASE(256)
+    default:
+      fail(TN_ERR_UNSUPPORTED, "bad tensor-core tile");
+  }
+#undef TN_TC_CASE
+}
+
+// ------------------------------------------------------------ B expansion
+namespace {
+template <class T>
+__device__ __forceinline__ T neg16(T x);
+template <>
+__device__ __forceinline__ __half neg16(__half x) {
+  return __hneg(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 neg16(__nv_bfloat16 x) {
+  return __hneg(x);
+}
+
+// Bx[bt][2n+0][2k..2k+1] = (Re B, -Im B)[k][n], Bx[bt][2n+1][2k..2k+1] = (Im B, Re B)[k][n];
+// columns past 2K up to the pitch are zero
+template <class T2, class T>
+__global__ void expand_b_kernel(const T2* __restrict__ B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt,
+                                int64_t N, int64_t K, int64_t half_pitch, T2* __restrict__ Bx) {
+  const int64_t total = nbt * N * half_pitch;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = x % half_pitch;
+    const int64_t t = x / half_pitch;
+    const int64_t n = t % N, bt = t / N;
+    T2 r0, r1;
+    if (k < K) {
+      const T2 v = B[bt * sb_bt + k * sb_k + n * sb_n];
+      r0.x = v.x;
+      r0.y = neg16<T>(v.y);
+      r1.x = v.y;
+      r1.y = v.x;
+    } else {
+      r0.x = r0.y = r1.x = r1.y = T(0.0f);
+    }
+    const int64_t row0 = (bt * 2 * N + 2 * n) * half_pitch;
+    Bx[row0 + k] = r0;
+    Bx[row0 + half_pitch + k] = r1;
+  }
+}
+}  // namespace
+
+void launch_expand_b(const void* B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt, int64_t N, int64_t K,
+                     bool bf16, void* Bx, cudaStream_t s) {
+  const int64_t half_pitch = (2 * K + BK - 1) / BK * BK / 2;
+  const int64_t total = nbt * N * half_pitch;
+  if (total <= 0) return;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  if (bf16)
+    expand_b_kernel<__nv_bfloat162, __nv_bfloat16><<<blocks, 256, 0, s>>>(
+        (const __nv_bfloat162*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx);
+  else
+    expand_b_kernel<__half2, __half><<<blocks, 256, 0, s>>>((const __half2*)B, sb_bt, sb_k, sb_n, nbt, N, K,
+                                                           half_pitch, (__half2*)Bx);
+}
+
+int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K) {
+  return nbt * 2 * N * ((2 * K + BK - 1) / BK * BK) * 2;
+}
+
+// ------------------------------------------------------------ self-test
+namespace {
+__device__ __forceinline__ float hash_unit(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return (float)((x >> 40) * (1.0 / 16777216.0)) * 2.0f - 1.0f;
+}
+template <class T2>
+__global__ void fill_kernel(T2* p, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float re = hash_unit(seed * 0x9E3779B97F4A7C15ULL + 2 * i);
+    float im = hash_unit(seed * 0x9E3779B97F4A7C15ULL + 2 * i + 1);
+    T2 v;
+    v.x = re;
+    v.y = im;
+    p[i] = v;
+  }
+}
+// reference: plain FP32 complex GEMM from the same 16-bit inputs
+template <class T2>
+__global__ void ref_kernel(const T2* A, const T2* B, float2* C, int64_t nbt, int64_t M, int64_t N, int64_t K) {
+  const int64_t total = nbt * M * N;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = x % N, m = (x / N) % M, bt = x / (N * M);
+    float re = 0.f, im = 0.f;
+    for (int64_t k = 0; k < K; ++k) {
+      const T2 a = A[(bt * M + m) * K + k];
+      const T2 b = B[(bt * K + k) * N + n];
+      const float ar = (float)a.x, ai = (float)a.y, br = (float)b.x, bi = (float)b.y;
+      re = fmaf(ar, br, re);
+      re = fmaf(-ai, bi, re);
+      im = fmaf(ar, bi, im);
+      im = fmaf(ai, br, im);
+    }
+    C[x] = make_float2(re, im);
+  }
+}
+__global__ void diff_kernel(const float2* a, const float2* b, int64_t n, unsigned* max_diff, unsigned* max_ref) {
+  float md = 0.f, mr = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float dx = a[i].x - b[i].x, dy = a[i].y - b[i].y;
+    md = fmaxf(md, sqrtf(dx * dx + dy * dy));
+    mr = fmaxf(mr, sqrtf(b[i].x * b[i].x + b[i].y * b[i].y));
+    if (!(a[i].x == a[i].x) || !(a[i].y == a[i].y)) md = 3.0e38f;
+  }
+  atomicMax(max_diff, __float_as_uint(md));
+  atomicMax(max_ref, __float_as_uint(mr));
+}
+}  // namespace
+
+double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
+                        int* d_err) {
+  void *A = nullptr, *B = nullptr, *Bx = nullptr, *C = nullptr, *R = nullptr;
+  unsigned* mx = nullptr;
+  auto cleanup = [&] {
+    for (void* q : {A, B, Bx, C, R, (void*)mx})
+      if (q) cudaFree(q);
+  };
+  try {
+    TN_CUDA(cudaMalloc(&A, nbt * M * K * 4));
+    TN_CUDA(cudaMalloc(&B, nbt * K * N * 4));
+    TN_CUDA(cudaMalloc(&Bx, expanded_b_bytes(nbt, N, K)));
+    TN_CUDA(cudaMalloc(&C, nbt * M * N * 8));
+    TN_CUDA(cudaMalloc(&R, nbt * M * N * 8));
+    TN_CUDA(cudaMalloc(&mx, 8));
+    TN_CUDA(cudaMemsetAsync(mx, 0, 8, s));
+    TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));  // NaN pattern: unwritten outputs fail
+    if (bf16) {
+      fill_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>((__nv_bfloat162*)A, nbt * M * K, seed);
+      fill_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>((__nv_bfloat162*)B, nbt * K * N, seed + 1);
+    } else {
+      fill_kernel<__half2><<<1024, 256, 0, s>>>((__half2*)A, nbt * M * K, seed);
+      fill_kernel<__half2><<<1024, 256, 0, s>>>((__half2*)B, nbt * K * N, seed + 1);
+    }
+    // B stored [bt][k][n] (n contiguous): the expansion reads it strided
+    launch_expand_b(B, K * N, N, 1, nbt, N, K, bf16, Bx, s);
+    TcGemmParams p{};
+    p.nbt = nbt;
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.sc_bt = M * N;
+    p.sc_m = N;
+    p.sc_n = 1;
+    p.C = C;
+    p.out_kind = 2;
+    p.scale = 1.0f;
+    p.err = d_err;
+    p.bn = tc_gemm_bn(N);
+    launch_gemm_tc(A, M * K, K, Bx, p, bf16, s);
+    if (bf16)
+      ref_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>((const __nv_bfloat162*)A, (const __nv_bfloat162*)B,
+                                                     (float2*)R, nbt, M, N, K);
+    else
+      ref_kernel<__half2><<<1024, 256, 0, s>>>((const __half2*)A, (const __half2*)B, (float2*)R, nbt, M, N, K);
+    diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
+    unsigned h[2] = {0, 0};
+    TN_CUDA(cudaMemcpyAsync(h, mx, 8, cudaMemcpyDeviceToHost, s));
+    TN_CUDA(cudaStreamSynchronize(s));
+    cleanup();
+    float md, mr;
+    std::memcpy(&md, &h[0], 4);
+    std::memcpy(&mr, &h[1], 4);
+    return mr > 0 ? (double)md / (double)mr : (double)md;
+  } catch (...) {
+    cudaStreamSynchronize(s);
+    cleanup();
+    throw;
+  }
+}
+
+}  // namespace tn

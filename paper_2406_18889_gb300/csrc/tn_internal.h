@@ -75,6 +75,18 @@ struct StridedCopy {
   int64_t in_stride[kMaxBits];
 };
 
+// Tensor-core GEMM on interleaved 16-bit complex data (stacked 4M lowering):
+// C[bt][m][n] = scale * sum_k A[bt][m][k] B[bt][k][n]; extents in complex elements.
+struct TcGemmParams {
+  int64_t nbt, M, N, K;
+  int64_t sc_bt, sc_m, sc_n;  // output strides (complex elements)
+  void* C;
+  int out_kind;               // 0 = fp16 complex, 1 = bf16 complex, 2 = fp32 complex
+  float scale;                // power of two applied to the FP32 accumulators
+  int* err;                   // device flag raised when a bounded wait times out
+  int bn;                     // real-column tile (32, 64, 128 or 256)
+};
+
 // ------------------------------------------------------------ launchers
 void launch_gemm_c64(const GemmParams& p, int accumulate, cudaStream_t s);
 void launch_bit_permute_c64(const void* in, void* out, const BitPermute& bp, cudaStream_t s);
@@ -96,5 +108,14 @@ struct TopkParams {
 void launch_topk(const double2* amps, const TopkParams& tp, const int64_t* block_base,
                  int64_t* out_idx, double* out_p, int* d_flag, cudaStream_t s);
 void launch_xeb(const double* q, int64_t n, int n_qubits, double* d_out, cudaStream_t s);
+bool tc_gemm_supported(int64_t nbt, int64_t M, int64_t N, int64_t K, int64_t sa_bt, int64_t sa_m, int64_t sa_k);
+int tc_gemm_bn(int64_t N);
+void launch_gemm_tc(const void* A, int64_t sa_bt, int64_t sa_m, const void* Bx, const TcGemmParams& p, bool bf16,
+                    cudaStream_t s);
+void launch_expand_b(const void* B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt, int64_t N, int64_t K,
+                     bool bf16, void* Bx, cudaStream_t s);
+int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K);
+double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
+                        int* d_err);
 
 }  // namespace tn
