@@ -127,7 +127,15 @@ typedef struct {
  * Build a plan: validates the network and tree, assigns every intermediate a
  * memory layout (contracted dimensions of both operands in one order, free
  * dimensions in the output's order, so most steps need no transpose), plans
- * workspace offsets, and copies the leaves to the device in complex64.
+ * workspace offsets, and copies the leaves to the device.
+ * Reduced precision (TN_PREC_BF16 / TN_PREC_FP16): intermediates are stored
+ * as 16-bit complex pairs scaled by a per-tensor power of two 2^-e (so that
+ * amplitudes far below the 16-bit normal range do not underflow); e is fixed
+ * at creation by one complex64 calibration batch (slice ids 0..B-1) as the
+ * exponent of the tensor's largest component.  The root (final amplitudes of
+ * each slice) is kept in complex64.  Large steps run on the tensor cores as a
+ * real GEMM with FP32 accumulation, small ones on CUDA cores in FP32.
+ * Creation temporarily needs a complex64 workspace for the calibration.
  * Synchronises `stream`.  *out is set only on success; destroy with
  * tn_plan_destroy.
  */
@@ -152,9 +160,18 @@ tn_status tn_plan_query(tn_plan_t plan, int64_t* useful_flops_per_slice,
 
 /* Per-step description for profiling and tests: the step's GEMM shape and
  * whether it runs once per slice batch (variant) or once per plan.  kinds[t]
- * bit 0 = variant, bit 1 = needs an operand/output transpose. */
+ * bit 0 = variant, bit 1 = needs an output transpose, bit 2 = hoisted (runs
+ * at plan creation), bit 3 = tensor-core GEMM (reduced precision). */
 tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64_t* m,
                         int64_t* n, int64_t* k, int32_t* kinds, int32_t* n_steps_out);
+
+/*
+ * Synchronise `stream` and report whether a bounded device-side wait of an
+ * earlier call on this plan timed out (TN_ERR_TIMEOUT; the flag is then
+ * cleared).  The contraction calls are asynchronous and cannot report it
+ * themselves.
+ */
+tn_status tn_plan_status(tn_plan_t plan, void* stream);
 
 /*
  * Contract the sub-networks `slice_ids[0..n_slices)` (host array; each id in

@@ -25,8 +25,8 @@ TN_FLAG_PLAN_ONLY = 0x4
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
-           "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_last_error",
-           "tn_version")
+           "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_plan_status",
+           "tn_last_error", "tn_version")
 
 
 class TNError(RuntimeError):
@@ -85,6 +85,7 @@ def load() -> ctypes.CDLL:
                                         i32, vp, vp, vp]
     lib.tn_xeb.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double), vp]
     lib.tn_contract_slices_noalloc.argtypes = [vp, p_i64, i64, vp, ctypes.c_int, vp]
+    lib.tn_plan_status.argtypes = [vp, vp]
     lib.tn_selftest_gemm_tc.argtypes = [i64, i64, i64, i64, i32, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_double), vp]
     for name in EXPORTS[:-2]:
@@ -221,6 +222,10 @@ def tn_selftest_gemm_tc(nbt: int, M: int, N: int, K: int, prec: int, seed: int =
     _check(load().tn_selftest_gemm_tc(int(nbt), int(M), int(N), int(K), int(prec), int(seed),
                                       ctypes.byref(out), ctypes.c_void_p(stream)))
     return out.value
+
+
+def tn_plan_status(plan: int, stream: int = 0) -> None:
+    _check(load().tn_plan_status(ctypes.c_void_p(plan), ctypes.c_void_p(stream)))
 
 
 def tn_last_error() -> str:

@@ -62,7 +62,7 @@ static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int
   if (n > 0) {
     TN_CHECK(ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & 255) == 0, TN_ERR_INVALID_ARG,
              "workspace must be non-null and 256-byte aligned");
-    TN_CHECK((int64_t)ws_bytes >= P.ws_bytes, TN_ERR_INVALID_ARG, "workspace too small");
+    TN_CHECK((int64_t)ws_bytes >= P.mem.ws_bytes, TN_ERR_INVALID_ARG, "workspace too small");
   }
   if (n == 0) {
     if (!accumulate) launch_zero(amps, (size_t)(P.G * P.J * 16), s);
@@ -111,7 +111,7 @@ tn_status tn_plan_query(tn_plan_t plan, int64_t* flops, int64_t* bytes, int64_t*
     if (flops) *flops = (int64_t)P.useful_flops_per_slice;
     if (bytes) *bytes = (int64_t)P.algo_bytes_per_slice;
     if (peak) *peak = (int64_t)P.peak_intermediate_bytes;
-    if (ws) *ws = P.ws_bytes;
+    if (ws) *ws = P.mem.ws_bytes;
   });
 }
 
@@ -129,7 +129,7 @@ tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64
       if (m) m[t] = S.gp.M;
       if (n) n[t] = S.gp.N;
       if (k) k[t] = S.gp.K;
-      if (kinds) kinds[t] = (S.variant ? 1 : 0) | (S.post_perm ? 2 : 0) | (S.hoisted ? 4 : 0);
+      if (kinds) kinds[t] = (S.variant ? 1 : 0) | (S.post_perm ? 2 : 0) | (S.hoisted ? 4 : 0) | (S.tc ? 8 : 0);
     }
   });
 }
@@ -158,7 +158,7 @@ tn_status tn_contract_slices_batched(const tn_plan_t* plans, int32_t n_plans, co
       for (int64_t j = 0; j < n_slices[i]; ++j)
         TN_CHECK(slice_ids[i][j] >= 0 && slice_ids[i][j] < S, TN_ERR_INVALID_ARG, "slice id out of range");
       if (n_slices[i] > 0)
-        TN_CHECK((int64_t)ws_bytes >= P.ws_bytes && workspace, TN_ERR_INVALID_ARG, "workspace too small");
+        TN_CHECK((int64_t)ws_bytes >= P.mem.ws_bytes && workspace, TN_ERR_INVALID_ARG, "workspace too small");
     }
     for (int32_t i = 0; i < n_plans; ++i)
       contract_one(*plans[i]->p, slice_ids[i], n_slices[i], amps[i], accumulate, workspace, ws_bytes,
@@ -229,6 +229,9 @@ tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, i
     cudaStream_t s = (cudaStream_t)stream;
     contract_one(*plan->p, slice_ids, n_slices, amps, accumulate, workspace, ws_bytes, s, &rec);
     TN_CUDA(cudaStreamSynchronize(s));
+    int h_err = 0;
+    TN_CUDA(cudaMemcpy(&h_err, plan->p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    TN_CHECK(h_err == 0, TN_ERR_TIMEOUT, "a bounded device wait timed out");
     if (n_records) *n_records = (int32_t)rec.size();
     for (int32_t i = 0; i < (int32_t)rec.size() && i < max_records; ++i) {
       kind[i] = rec[i].kind;
@@ -271,6 +274,21 @@ tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int3
     cudaFree(d_err);
     TN_CHECK(h_err == 0, TN_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait timed out");
     *max_rel_err = r;
+  });
+}
+
+tn_status tn_plan_status(tn_plan_t plan, void* stream) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    Plan& P = *plan->p;
+    if (P.flags & TN_FLAG_PLAN_ONLY) return;
+    TN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int h_err = 0;
+    TN_CUDA(cudaMemcpy(&h_err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_err) {
+      TN_CUDA(cudaMemset(P.d_err, 0, sizeof(int)));
+      fail(TN_ERR_TIMEOUT, "a bounded device wait timed out in an earlier call on this plan");
+    }
   });
 }
 

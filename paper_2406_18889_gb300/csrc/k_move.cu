@@ -5,6 +5,9 @@
 // of two), so a change of dimension order is a permutation of the r index
 // bits.  These kernels are HBM-bound: each element is read once and written
 // once.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "tn_internal.h"
 
 namespace tn {
@@ -27,9 +30,10 @@ struct PermTile {
   int gout[kMaxBits];
 };
 
-__global__ void __launch_bounds__(256) bit_permute_kernel(const float2* __restrict__ in,
-                                                          float2* __restrict__ out, PermTile pt) {
-  __shared__ float2 tile[(1 << kTileMaxBits) + (1 << kTileMaxBits) / 16];
+template <class W>
+__global__ void __launch_bounds__(256) bit_permute_kernel(const W* __restrict__ in, W* __restrict__ out,
+                                                          PermTile pt) {
+  __shared__ W tile[(1 << kTileMaxBits) + (1 << kTileMaxBits) / 16];
   const int64_t blk = blockIdx.x;
   int64_t base_in = 0, base_out = 0;
   for (int j = 0; j < pt.ng; ++j) {
@@ -58,7 +62,8 @@ __global__ void __launch_bounds__(256) bit_permute_kernel(const float2* __restri
   }
 }
 
-__global__ void copy_kernel(const float2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+template <class W>
+__global__ void copy_kernel(const W* __restrict__ in, W* __restrict__ out, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < n; i += stride) out[i] = in[i];
@@ -66,14 +71,17 @@ __global__ void copy_kernel(const float2* __restrict__ in, float2* __restrict__ 
 
 }  // namespace
 
-void launch_bit_permute_c64(const void* in, void* out, const BitPermute& bp, cudaStream_t s) {
+void launch_bit_permute(const void* in, void* out, const BitPermute& bp, int elem_bytes, cudaStream_t s) {
   const int R = bp.nbits;
   bool identity = true;
   for (int i = 0; i < R; ++i) identity &= bp.out_bit[i] == i;
   if (identity) {
     int64_t n = int64_t(1) << R;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-    copy_kernel<<<blocks, 256, 0, s>>>((const float2*)in, (float2*)out, n);
+    if (elem_bytes == 8)
+      copy_kernel<uint2><<<blocks, 256, 0, s>>>((const uint2*)in, (uint2*)out, n);
+    else
+      copy_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, n);
     return;
   }
   const int a = std::min(5, R);
@@ -118,13 +126,22 @@ void launch_bit_permute_c64(const void* in, void* out, const BitPermute& bp, cud
     }
   int64_t blocks = int64_t(1) << pt.ng;
   TN_CHECK(blocks < (int64_t(1) << 31), TN_ERR_UNSUPPORTED, "transpose grid too large");
-  bit_permute_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float2*)in, (float2*)out, pt);
+  if (elem_bytes == 8)
+    bit_permute_kernel<uint2><<<(unsigned)blocks, 256, 0, s>>>((const uint2*)in, (uint2*)out, pt);
+  else
+    bit_permute_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, pt);
+}
+
+void launch_bit_permute_c64(const void* in, void* out, const BitPermute& bp, cudaStream_t s) {
+  launch_bit_permute(in, out, bp, 8, s);
 }
 
 // ------------------------------------------------------------ leaf upload
 namespace {
-__global__ void strided_copy_c128_kernel(const double2* __restrict__ in, float2* __restrict__ out,
-                                         StridedCopy sc, int64_t n) {
+// out_kind: 0 = fp16 complex, 1 = bf16 complex, 2 = fp32 complex; values are
+// multiplied by `scale` (a power of two) in FP64 before rounding
+__global__ void strided_copy_c128_kernel(const double2* __restrict__ in, void* __restrict__ out,
+                                         StridedCopy sc, int64_t n, int out_kind, double scale) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (o >= n) return;
   int64_t rem = o, off = 0;
@@ -134,25 +151,37 @@ __global__ void strided_copy_c128_kernel(const double2* __restrict__ in, float2*
     off += c * sc.in_stride[d];
   }
   double2 v = in[off];
-  out[o] = make_float2((float)v.x, (float)v.y);
+  const double re = v.x * scale, im = v.y * scale;
+  if (out_kind == 2)
+    ((float2*)out)[o] = make_float2((float)re, (float)im);
+  else if (out_kind == 1)
+    ((__nv_bfloat162*)out)[o] = __nv_bfloat162(__double2bfloat16(re), __double2bfloat16(im));
+  else
+    ((__half2*)out)[o] = __halves2half2(__double2half(re), __double2half(im));
 }
 }  // namespace
 
-void launch_strided_copy_c128_to_c64(const void* in, void* out, const StridedCopy& sc, int64_t n_out,
-                                     cudaStream_t s) {
+void launch_strided_copy_c128(const void* in, void* out, const StridedCopy& sc, int64_t n_out, int out_kind,
+                              double scale, cudaStream_t s) {
   if (n_out <= 0) return;
   int64_t blocks = (n_out + 255) / 256;
-  strided_copy_c128_kernel<<<(unsigned)blocks, 256, 0, s>>>((const double2*)in, (float2*)out, sc, n_out);
+  strided_copy_c128_kernel<<<(unsigned)blocks, 256, 0, s>>>((const double2*)in, out, sc, n_out, out_kind, scale);
+}
+
+void launch_strided_copy_c128_to_c64(const void* in, void* out, const StridedCopy& sc, int64_t n_out,
+                                     cudaStream_t s) {
+  launch_strided_copy_c128(in, out, sc, n_out, 2, 1.0, s);
 }
 
 // ------------------------------------------------------------ slice gather
 namespace {
+template <class W>
 __global__ void gather_kernel(const GatherLeaf* __restrict__ tab, const int64_t* __restrict__ ids, int B,
                               const char* __restrict__ pbase, char* __restrict__ wbase) {
   const GatherLeaf& g = tab[blockIdx.y];
   const int64_t total = g.rest * B;
-  const float2* src = (const float2*)(pbase + g.src_off);
-  float2* dst = (float2*)(wbase + g.dst_off);
+  const W* src = (const W*)(pbase + g.src_off);
+  W* dst = (W*)(wbase + g.dst_off);
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x) {
     int64_t b = x / g.rest, r = x % g.rest;
@@ -167,12 +196,15 @@ __global__ void gather_kernel(const GatherLeaf* __restrict__ tab, const int64_t*
 
 void launch_gather_leaves(const GatherLeaf* d_table, int n_leaves, int64_t max_rest,
                           const int64_t* d_slice_ids, int B, const char* plan_base, char* ws_base,
-                          cudaStream_t s) {
+                          cudaStream_t s, int elem_bytes) {
   if (n_leaves == 0) return;
   int64_t per = max_rest * B;
   unsigned bx = (unsigned)std::min<int64_t>((per + 255) / 256, 64);
   TN_CHECK(n_leaves <= 65535, TN_ERR_UNSUPPORTED, "too many sliced leaves");
-  gather_kernel<<<dim3(bx, n_leaves), 256, 0, s>>>(d_table, d_slice_ids, B, plan_base, ws_base);
+  if (elem_bytes == 8)
+    gather_kernel<uint2><<<dim3(bx, n_leaves), 256, 0, s>>>(d_table, d_slice_ids, B, plan_base, ws_base);
+  else
+    gather_kernel<uint32_t><<<dim3(bx, n_leaves), 256, 0, s>>>(d_table, d_slice_ids, B, plan_base, ws_base);
 }
 
 // ------------------------------------------------------------ accumulate
@@ -181,7 +213,7 @@ void launch_gather_leaves(const GatherLeaf* d_table, int n_leaves, int64_t max_r
 namespace {
 __global__ void accumulate_kernel(const float2* __restrict__ root, int64_t sb, int64_t sg, int64_t sj,
                                   int64_t G, int64_t J, const int32_t* __restrict__ n_valid,
-                                  double2* __restrict__ amps, int accumulate) {
+                                  double2* __restrict__ amps, int accumulate, double scale) {
   int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (x >= G * J) return;
   int64_t g = x / J, j = x % J;
@@ -193,6 +225,8 @@ __global__ void accumulate_kernel(const float2* __restrict__ root, int64_t sb, i
     re += (double)v.x;
     im += (double)v.y;
   }
+  re *= scale;  // power of two: exact
+  im *= scale;
   if (accumulate) {
     double2 a = amps[x];
     re = a.x + re;
@@ -207,11 +241,30 @@ __global__ void zero_kernel(uint4* p, int64_t n16) {
 }  // namespace
 
 void launch_accumulate_c64(const void* root, int64_t sb, int64_t sg, int64_t sj, int64_t G, int64_t J,
-                           const int32_t* d_n_valid, int B, void* amps, int accumulate, cudaStream_t s) {
+                           const int32_t* d_n_valid, int B, void* amps, int accumulate, cudaStream_t s,
+                           double scale) {
   (void)B;
   int64_t n = G * J;
   accumulate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)root, sb, sg, sj, G, J,
-                                                                 d_n_valid, (double2*)amps, accumulate);
+                                                                 d_n_valid, (double2*)amps, accumulate, scale);
+}
+
+// ------------------------------------------------------------ amax
+// out[slot] = max(out[slot], max |re|, |im| over a complex64 tensor)  (calibration)
+namespace {
+__global__ void amax_kernel(const float2* __restrict__ x, int64_t n, unsigned* out) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+}  // namespace
+
+void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s) {
+  if (n <= 0) return;
+  unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  amax_kernel<<<blocks, 256, 0, s>>>((const float2*)x, n, out);
 }
 
 void launch_zero(void* p, size_t bytes, cudaStream_t s) {

@@ -63,8 +63,8 @@ extern "C" tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* s
     TN_CHECK(amps != nullptr, TN_ERR_INVALID_ARG, "amps is null");
     TN_CHECK(n_slices >= 0 && (n_slices == 0 || slice_ids), TN_ERR_INVALID_ARG, "bad slice list");
     TN_CHECK(accumulate == 0 || accumulate == 1, TN_ERR_INVALID_ARG, "accumulate must be 0 or 1");
-    TN_CHECK(P.ws_bytes <= (int64_t)TN_STATIC_WORKSPACE_BYTES, TN_ERR_INVALID_ARG,
-             "plan needs " + std::to_string(P.ws_bytes) + " bytes of workspace; the static workspace holds " +
+    TN_CHECK(P.mem.ws_bytes <= (int64_t)TN_STATIC_WORKSPACE_BYTES, TN_ERR_INVALID_ARG,
+             "plan needs " + std::to_string(P.mem.ws_bytes) + " bytes of workspace; the static workspace holds " +
                  std::to_string((long long)TN_STATIC_WORKSPACE_BYTES) +
                  " (use tn_contract_slices or a smaller max_slice_batch)");
     const int64_t S = int64_t(1) << P.sliced.size();

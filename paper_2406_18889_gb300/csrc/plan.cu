@@ -17,6 +17,7 @@
 //    directly, and inserts a transpose only where no choice allows it.
 #include <algorithm>
 #include <array>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -110,6 +111,7 @@ Plan::~Plan() {
   if (d_slice_ids) cudaFree(d_slice_ids);
   if (d_n_valid) cudaFree(d_n_valid);
   if (d_gather) cudaFree(d_gather);
+  if (d_err) cudaFree(d_err);
 }
 
 // ---------------------------------------------------------------- layouts
@@ -151,7 +153,7 @@ struct Builder {
   // small preference terms: the operand's innermost block should be long
   // (coalesced loads) and preferably the contracted block
   double inner_penalty(const std::vector<std::vector<int>>& blocks, const std::vector<int>& kblock,
-                       double elems) const {
+                       double elems, bool larger) const {
     const std::vector<int>* inner = nullptr;
     for (auto it = blocks.rbegin(); it != blocks.rend(); ++it)
       if (dims_prod(*it) > 1) {
@@ -162,8 +164,8 @@ struct Builder {
     double sz = (double)dims_prod(*inner);
     double pen = 0.0;
     if (sz < 16) pen += elems * 0.25 * (16.0 - sz) / 16.0;
-    if (inner != &kblock && (inner->empty() || inner->front() != (kblock.empty() ? -2 : kblock.front())))
-      pen += elems * 0.01;
+    if (inner->empty() || kblock.empty() || inner->front() != kblock.front())
+      pen += elems * ((larger && P.skind != KIND_C64) ? 1.0 : 0.01);
     return pen;
   }
 
@@ -228,7 +230,7 @@ struct Builder {
             ablocks.push_back(*A3[i]);
             la.insert(la.end(), A3[i]->begin(), A3[i]->end());
           }
-          double ca = placement_cost(S.a, la) + inner_penalty(ablocks, k_o, ea);
+          double ca = placement_cost(S.a, la) + inner_penalty(ablocks, k_o, ea, ea >= eb);
           if (ca >= best) continue;
           std::array<int, 3> pb = {0, 1, 2};
           do {
@@ -238,7 +240,7 @@ struct Builder {
               bblocks.push_back(*B3[i]);
               lb.insert(lb.end(), B3[i]->begin(), B3[i]->end());
             }
-            double cb = placement_cost(S.b, lb) + inner_penalty(bblocks, k_o, eb);
+            double cb = placement_cost(S.b, lb) + inner_penalty(bblocks, k_o, eb, eb > ea);
             if (ca + cb < best) {
               best = ca + cb;
               best_a = la;
@@ -310,6 +312,249 @@ struct Builder {
 
 }  // namespace
 
+// ---------------------------------------------------------------- memory plans
+namespace {
+
+int64_t node_bytes(const Plan& P, int x, bool c64) {
+  return P.nodes[x].elems * ((c64 || x == P.root) ? 8 : 4);
+}
+
+// tensor-core operand roles of a step: (A node, a strides) and (B node, b strides)
+struct TcRoles {
+  int a_node, b_node;
+  int64_t M, N, K;
+  int64_t a_bt, a_m;               // A strides (k contiguous)
+  int64_t b_bt, b_k, b_n;          // B strides
+  int64_t c_bt, c_m, c_n;          // output strides
+};
+TcRoles tc_roles(const Step& S) {
+  const GemmParams& g = S.gp;
+  TcRoles r{};
+  if (!S.tc_swap) {
+    r = {S.a, S.b, g.M, g.N, g.K, g.sa_bt, g.sa_m, g.sb_bt, g.sb_k, g.sb_n, g.sc_bt, g.sc_m, g.sc_n};
+  } else {
+    r = {S.b, S.a, g.N, g.M, g.K, g.sb_bt, g.sb_n, g.sa_bt, g.sa_k, g.sa_m, g.sc_bt, g.sc_n, g.sc_m};
+  }
+  return r;
+}
+
+MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>& leaf_src_layout) {
+  MemPlan M;
+  M.c64 = c64;
+  const int nn = (int)P.nodes.size();
+  M.off.assign(nn, -1);
+  M.in_plan.assign(nn, 0);
+  M.tmp_off.assign(P.steps.size(), -1);
+  M.bx_off.assign(P.steps.size(), -1);
+  const int eb = c64 ? 8 : 4;
+  int64_t poff = 0;
+  std::vector<int64_t> src_off(P.n_leaves, -1);
+  for (int i = 0; i < P.n_leaves; ++i) {
+    int64_t el = 1;
+    for (int e : leaf_src_layout[i]) el *= P.dim[e];
+    src_off[i] = poff;
+    poff += round_up(el * eb, 256);
+    if (!P.nodes[i].variant) {
+      M.off[i] = src_off[i];
+      M.in_plan[i] = 1;
+    }
+  }
+  // hoisted steps run once at creation; their transposes and expanded operands
+  // use a creation-time scratch buffer: [transpose temp | expanded operand]
+  int64_t tmax = 0, bmax = 0;
+  for (size_t t = 0; t < P.steps.size(); ++t)
+    if (P.steps[t].hoisted) {
+      const Step& S = P.steps[t];
+      M.off[S.c] = poff;
+      M.in_plan[S.c] = 1;
+      poff += round_up(node_bytes(P, S.c, c64), 256);
+      if (S.post_perm) tmax = std::max(tmax, node_bytes(P, S.c, c64));
+      if (!c64 && S.tc) {
+        TcRoles r = tc_roles(S);
+        bmax = std::max(bmax, expanded_b_bytes(S.gp.nbt, r.N, r.K));
+      }
+    }
+  for (size_t t = 0; t < P.steps.size(); ++t)
+    if (P.steps[t].hoisted) {
+      if (P.steps[t].post_perm) M.tmp_off[t] = 0;
+      if (!c64 && P.steps[t].tc) M.bx_off[t] = round_up(tmax, 256);
+    }
+  M.create_scratch = (tmax || bmax) ? round_up(tmax, 256) + bmax : 0;
+  M.plan_bytes = poff;
+  Arena ws;
+  for (int i = 0; i < P.n_leaves; ++i)
+    if (P.nodes[i].variant) {
+      M.gather_node.push_back(i);
+      M.off[i] = ws.alloc(node_bytes(P, i, c64));
+    }
+  for (size_t t = 0; t < P.steps.size(); ++t) {
+    const Step& S = P.steps[t];
+    if (S.hoisted) continue;
+    M.off[S.c] = ws.alloc(node_bytes(P, S.c, c64));
+    int64_t tmp = -1, bx = -1;
+    if (S.post_perm) tmp = M.tmp_off[t] = ws.alloc(node_bytes(P, S.c, c64));
+    if (!c64 && S.tc) {
+      TcRoles r = tc_roles(S);
+      bx = M.bx_off[t] = ws.alloc(expanded_b_bytes(S.gp.nbt, r.N, r.K));
+    }
+    if (tmp >= 0) ws.release(tmp);
+    if (bx >= 0) ws.release(bx);
+    for (int x : {S.a, S.b})
+      if (!M.in_plan[x]) ws.release(M.off[x]);
+  }
+  M.ws_bytes = round_up(std::max<int64_t>(ws.peak, 256), 256);
+  // gather table (offsets relative to the plan-memory and workspace bases)
+  for (int i : M.gather_node) {
+    const Node& N = P.nodes[i];
+    GatherLeaf g{};
+    g.src_off = src_off[i];
+    g.dst_off = M.off[i];
+    g.rest = N.elems / P.B;
+    int64_t acc = 1, inner = 1;
+    for (int d = (int)N.layout.size() - 1; d >= 0; --d) {
+      if (N.layout[d] == P.batch_edge) inner = acc;
+      acc *= P.dim[N.layout[d]];
+    }
+    g.inner = inner;
+    std::vector<int> sl_here;
+    for (int e : leaf_src_layout[i])
+      if (std::find(P.sliced.begin(), P.sliced.end(), e) != P.sliced.end()) sl_here.push_back(e);
+    TN_CHECK(sl_here.size() <= 8, TN_ERR_UNSUPPORTED, "a leaf holds more than 8 sliced edges");
+    g.n_sel = (int)sl_here.size();
+    for (int j = 0; j < g.n_sel; ++j) {
+      g.slice_bit[j] = (int)(std::find(P.sliced.begin(), P.sliced.end(), sl_here[j]) - P.sliced.begin());
+      g.sel_stride[j] = g.rest << (g.n_sel - 1 - j);
+    }
+    M.gather.push_back(g);
+    M.gather_max_rest = std::max(M.gather_max_rest, g.rest);
+  }
+  return M;
+}
+
+// where a leaf's source lives in plan memory (variant leaves: the gather source)
+int64_t leaf_src_offset(const MemPlan& M, const Plan& P, int i) {
+  if (!P.nodes[i].variant) return M.off[i];
+  for (size_t j = 0; j < M.gather_node.size(); ++j)
+    if (M.gather_node[j] == i) return M.gather[j].src_off;
+  fail(TN_ERR_INVALID_ARG, "internal: sliced leaf without a gather entry");
+}
+
+struct Exec {
+  const Plan& P;
+  const MemPlan& M;
+  char* pb;  // plan memory base
+  char* wb;  // workspace base
+  char* base(int node) const { return (M.in_plan[node] ? pb : wb) + M.off[node]; }
+};
+
+struct Recorder {
+  std::vector<LaunchRecord>* rec;
+  cudaStream_t s;
+  void begin(int kind, double flops, double bytes) {
+    if (!rec) return;
+    LaunchRecord r{kind, flops, bytes, nullptr, nullptr};
+    TN_CUDA(cudaEventCreate(&r.start));
+    TN_CUDA(cudaEventCreate(&r.stop));
+    TN_CUDA(cudaEventRecord(r.start, s));
+    rec->push_back(r);
+  }
+  void end() {
+    if (rec) TN_CUDA(cudaEventRecord(rec->back().stop, s));
+  }
+};
+
+// One contraction step: GEMM (tensor-core or CUDA-core) + transpose if needed.
+// `amax` (calibration, complex64 only): per-node maxima of |re|, |im|.
+void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned* amax) {
+  const Plan& P = X.P;
+  const MemPlan& M = X.M;
+  const Step& S = P.steps[t];
+  char* dst = X.base(S.c);
+  char* out = S.post_perm ? X.wb + M.tmp_off[t] : dst;
+  const int out_kind = (M.c64 || S.c == P.root) ? KIND_C64 : P.skind;
+  const double flops = 8.0 * S.cost;
+  const double ebytes = M.c64 ? 8.0 : 4.0;
+  const double bytes = ebytes * ((double)P.nodes[S.a].elems + (double)P.nodes[S.b].elems) +
+                       (out_kind == KIND_C64 ? 8.0 : 4.0) * (double)P.nodes[S.c].elems;
+  const float scale =
+      M.c64 ? 1.0f : ldexpf(1.0f, P.nodes[S.a].exp2 + P.nodes[S.b].exp2 - P.nodes[S.c].exp2);
+  if (M.c64) {
+    GemmParams g = S.gp;
+    g.A = X.base(S.a);
+    g.B = X.base(S.b);
+    g.C = out;
+    R.begin(0, flops, bytes);
+    launch_gemm_c64(g, 0, s);
+    R.end();
+  } else if (S.tc) {
+    TcRoles r = tc_roles(S);
+    char* bx = X.wb + M.bx_off[t];
+    R.begin(4, 0, ebytes * (double)P.nodes[r.b_node].elems + (double)expanded_b_bytes(S.gp.nbt, r.N, r.K));
+    launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s);
+    R.end();
+    TcGemmParams tp{};
+    tp.nbt = S.gp.nbt;
+    tp.M = r.M;
+    tp.N = r.N;
+    tp.K = r.K;
+    tp.sc_bt = r.c_bt;
+    tp.sc_m = r.c_m;
+    tp.sc_n = r.c_n;
+    tp.C = out;
+    tp.out_kind = out_kind;
+    tp.scale = scale;
+    tp.err = P.d_err;
+    tp.bn = tc_gemm_bn(r.N);
+    R.begin(0, flops, bytes);
+    launch_gemm_tc(X.base(r.a_node), r.a_bt, r.a_m, bx, tp, P.skind == KIND_BF16, s);
+    R.end();
+  } else {
+    GemmParams g = S.gp;
+    g.A = X.base(S.a);
+    g.B = X.base(S.b);
+    g.C = out;
+    R.begin(0, flops, bytes);
+    launch_gemm_simt(g, P.skind, out_kind, scale, s);
+    R.end();
+  }
+  if (S.post_perm) {
+    const int pe = out_kind == KIND_C64 ? 8 : 4;
+    R.begin(1, 0, 2.0 * pe * (double)P.nodes[S.c].elems);
+    launch_bit_permute(out, dst, S.perm, pe, s);
+    R.end();
+  }
+  if (amax) launch_amax_c64(dst, P.nodes[S.c].elems, amax + S.c, s);
+}
+
+void enqueue_batch_mem(const Plan& P, const MemPlan& M, char* pb, void* ws, void* amps, int accumulate,
+                       cudaStream_t s, std::vector<LaunchRecord>* rec, unsigned* amax, bool hoisted_too) {
+  Exec X{P, M, pb, (char*)ws};
+  Recorder R{rec, s};
+  const double eb = M.c64 ? 8.0 : 4.0;
+  if (!M.gather.empty()) {
+    double bytes = 0;
+    for (auto& g : M.gather) bytes += 2.0 * g.rest * P.B * eb;
+    R.begin(2, 0, bytes);
+    launch_gather_leaves(P.d_gather, (int)M.gather.size(), M.gather_max_rest, P.d_slice_ids, P.B, pb,
+                         (char*)ws, s, M.c64 ? 8 : 4);
+    R.end();
+  }
+  if (amax)
+    for (int i = 0; i < P.n_leaves; ++i) launch_amax_c64(X.base(i), P.nodes[i].elems, amax + i, s);
+  for (size_t t = 0; t < P.steps.size(); ++t) {
+    if (P.steps[t].hoisted && !hoisted_too) continue;
+    enqueue_step(X, t, s, R, amax);
+  }
+  if (amps) {
+    R.begin(3, 0, 8.0 * (double)P.nodes[P.root].elems + 16.0 * P.G * P.J * (accumulate ? 2 : 1));
+    launch_accumulate_c64(X.base(P.root), P.root_sb, P.root_sg, P.root_sj, P.G, P.J, P.d_n_valid, P.B, amps,
+                          accumulate, s, ldexp(1.0, P.nodes[P.root].exp2));
+    R.end();
+  }
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------- build
 std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc* tree,
                                  const tn_plan_options* opt, cudaStream_t stream) {
@@ -319,13 +564,13 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
   TN_CHECK(net->n_leaves >= 1 && net->n_edges >= 1, TN_ERR_INVALID_ARG, "empty network");
   TN_CHECK(net->leaf_rank && net->leaf_edges && net->edge_dim && net->leaf_data, TN_ERR_INVALID_ARG,
            "null network array");
-  TN_CHECK(opt->prec == TN_PREC_C64, TN_ERR_UNSUPPORTED,
-           "this build contracts in complex64 only (bf16/fp16 not available)");
+  TN_CHECK(opt->prec == TN_PREC_C64 || opt->prec == TN_PREC_BF16 || opt->prec == TN_PREC_FP16,
+           TN_ERR_INVALID_ARG, "unknown precision");
   TN_CHECK(opt->max_slice_batch >= 1 && opt->max_slice_batch <= 65536 && is_pow2(opt->max_slice_batch),
            TN_ERR_INVALID_ARG, "max_slice_batch must be a power of two in [1, 65536]");
   P.prec = opt->prec;
+  P.skind = opt->prec == TN_PREC_C64 ? KIND_C64 : opt->prec == TN_PREC_BF16 ? KIND_BF16 : KIND_F16;
   P.flags = opt->flags;
-  P.elem_bytes = 8;
   P.n_leaves = net->n_leaves;
   P.n_edges = net->n_edges;
   P.dim.assign(net->edge_dim, net->edge_dim + net->n_edges);
@@ -403,7 +648,6 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     Node& N = P.nodes[i];
     N.leaf = true;
     N.leaf_id = i;
-    N.plan_mem = true;
     for (int e : P.leaf_edges[i]) {
       if (sliced_mark[e])
         N.variant = true;
@@ -429,12 +673,12 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     S.a = a;
     S.b = b;
     S.c = c;
-    const auto& X = P.nodes[a].edges;
-    const auto& Y = P.nodes[b].edges;
-    std::vector<int> shared = set_inter(X, Y);
+    const auto& Xe = P.nodes[a].edges;
+    const auto& Ye = P.nodes[b].edges;
+    std::vector<int> shared = set_inter(Xe, Ye);
     std::vector<int> C;
     std::vector<int> uni;
-    std::set_union(X.begin(), X.end(), Y.begin(), Y.end(), std::back_inserter(uni));
+    std::set_union(Xe.begin(), Xe.end(), Ye.begin(), Ye.end(), std::back_inserter(uni));
     for (int e : uni) {
       bool drop = false;
       if (contains(shared, e) && !keep.count(e)) {
@@ -444,8 +688,8 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       }
       if (!drop) C.push_back(e);
     }
-    for (int e : X) occ[e].erase(a);
-    for (int e : Y) occ[e].erase(b);
+    for (int e : Xe) occ[e].erase(a);
+    for (int e : Ye) occ[e].erase(b);
     for (int e : C) occ[e].insert(c);
     Node& N = P.nodes[c];
     N.edges = C;
@@ -457,8 +701,8 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     P.nodes[b].consumer = t;
     S.bt = set_inter(shared, C);
     S.k = set_minus(shared, C);
-    S.m = set_minus(X, Y);
-    S.n = set_minus(Y, X);
+    S.m = set_minus(Xe, Ye);
+    S.n = set_minus(Ye, Xe);
     S.variant = N.variant;
     P.steps.push_back(S);
   }
@@ -475,248 +719,187 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
 
   Builder bld(P);
   bld.assign_layouts();
-  // per-sub-network statistics (slice-batch edge at size 1)
   for (auto& S : P.steps) {
     bld.fill_gemm(S);
     double bscale = P.nodes[S.c].variant ? (double)P.B : 1.0;
     S.cost_one = S.cost / bscale;
+    const double eb = P.skind == KIND_C64 ? 8.0 : 4.0;
     double bytes = ((double)P.nodes[S.a].elems / (P.nodes[S.a].variant ? P.B : 1) +
                     (double)P.nodes[S.b].elems / (P.nodes[S.b].variant ? P.B : 1) +
                     (double)P.nodes[S.c].elems / (P.nodes[S.c].variant ? P.B : 1)) *
-                   P.elem_bytes;
+                   eb;
     P.useful_flops_per_slice += 8.0 * S.cost_one;
     P.algo_bytes_per_slice += bytes;
     P.peak_intermediate_bytes =
-        std::max(P.peak_intermediate_bytes,
-                 (double)P.nodes[S.c].elems / (P.nodes[S.c].variant ? P.B : 1) * P.elem_bytes);
+        std::max(P.peak_intermediate_bytes, (double)P.nodes[S.c].elems / (P.nodes[S.c].variant ? P.B : 1) * eb);
     if (S.post_perm) S.perm = bld.bit_perm(S.lc_nat, P.nodes[S.c].layout);
+    // tensor cores: the larger K-contiguous operand is A (used as stored), the
+    // other is expanded to its real 2x2 form
+    if (P.skind != KIND_C64) {
+      const GemmParams& g = S.gp;
+      const bool a_ok = tc_gemm_supported(g.nbt, g.M, g.N, g.K, g.sa_bt, g.sa_m, g.sa_k) && g.M >= 64;
+      const bool b_ok = tc_gemm_supported(g.nbt, g.N, g.M, g.K, g.sb_bt, g.sb_n, g.sb_k) && g.N >= 64;
+      const bool big = g.K >= 8 && (double)g.nbt * g.M * g.N * g.K >= double(1 << 18);
+      if (big && (a_ok || b_ok)) {
+        S.tc = true;
+        if (a_ok && b_ok)
+          S.tc_swap = P.nodes[S.b].elems > P.nodes[S.a].elems;
+        else
+          S.tc_swap = b_ok;
+      }
+    }
   }
-  if (P.steps.empty()) {
-    // single leaf network: the leaf is the root
-  }
-
-  // ------------------------------------------------------------ memory plan
-  // plan memory: leaves (invariant in their layout; variant as full source
-  // with sliced edges outermost) and hoisted step results
-  int64_t poff = 0;
-  std::vector<int64_t> leaf_src_elems(P.n_leaves);
+  // leaf storage layouts (variant leaves: sliced edges outermost, then the batch copy's order)
   std::vector<std::vector<int>> leaf_src_layout(P.n_leaves);
   for (int i = 0; i < P.n_leaves; ++i) {
-    Node& N = P.nodes[i];
-    std::vector<int> L;
+    const Node& N = P.nodes[i];
     if (N.variant) {
       for (int e : P.sliced)
-        if (contains(P.leaf_edges[i], e)) L.push_back(e);
+        if (contains(P.leaf_edges[i], e)) leaf_src_layout[i].push_back(e);
       for (int e : N.layout)
-        if (e != P.batch_edge) L.push_back(e);
+        if (e != P.batch_edge) leaf_src_layout[i].push_back(e);
     } else {
-      L = N.layout;
+      leaf_src_layout[i] = N.layout;
     }
-    leaf_src_layout[i] = L;
-    int64_t el = 1;
-    for (int e : L) el *= P.dim[e];
-    leaf_src_elems[i] = el;
-    N.off = poff;
-    poff += round_up(el * P.elem_bytes, 256);
   }
-  for (auto& S : P.steps)
-    if (S.hoisted) {
-      Node& N = P.nodes[S.c];
-      N.plan_mem = true;
-      N.off = poff;
-      poff += round_up(N.elems * P.elem_bytes, 256);
-    }
-  P.plan_bytes = poff;
-  // workspace: gathered variant leaves, per-call step results, transpose temps
-  Arena ws;
-  for (int i = 0; i < P.n_leaves; ++i)
-    if (P.nodes[i].variant) {
-      // the gathered copy lives in the workspace; remember the source offset
-      P.gather_node.push_back(i);
-      P.gather_src_off.push_back(P.nodes[i].off);
-    }
-  for (size_t gi = 0; gi < P.gather_node.size(); ++gi) {
-    Node& N = P.nodes[P.gather_node[gi]];
-    N.plan_mem = false;
-    N.off = ws.alloc(N.elems * P.elem_bytes);
-  }
-  // hoisted-step transposes need scratch at creation time only
-  int64_t create_scratch = 0;
-  for (auto& S : P.steps) {
-    if (S.hoisted) {
-      if (S.post_perm) create_scratch = std::max(create_scratch, P.nodes[S.c].elems * P.elem_bytes);
-      continue;
-    }
-    Node& N = P.nodes[S.c];
-    N.plan_mem = false;
-    N.off = ws.alloc(N.elems * P.elem_bytes);
-    if (S.post_perm) {
-      S.tmp_off = ws.alloc(N.elems * P.elem_bytes);
-      ws.release(S.tmp_off);
-    }
-    for (int x : {S.a, S.b})
-      if (!P.nodes[x].plan_mem) ws.release(P.nodes[x].off);
-  }
-  P.ws_bytes = round_up(std::max<int64_t>(ws.peak, 256), 256);
+  P.mem = plan_memory(P, P.skind == KIND_C64, leaf_src_layout);
   if (opt->mem_cap_bytes > 0)
-    TN_CHECK(P.ws_bytes <= opt->mem_cap_bytes, TN_ERR_OOM, "workspace exceeds mem_cap_bytes");
-  // root readout
+    TN_CHECK(P.mem.ws_bytes <= opt->mem_cap_bytes, TN_ERR_OOM, "workspace exceeds mem_cap_bytes");
   {
-    Node& R = P.nodes[P.root];
+    const Node& R = P.nodes[P.root];
     auto st = bld.strides(R.layout);
     P.root_sb = R.variant ? st.at(P.batch_edge) : 0;
     P.root_sg = P.block_edge >= 0 ? st.at(P.block_edge) : 0;
     P.root_sj = P.open_edges.empty() ? 0 : st.at(P.open_edges.back());
   }
-  // gather table
-  for (size_t gi = 0; gi < P.gather_node.size(); ++gi) {
-    int i = P.gather_node[gi];
-    Node& N = P.nodes[i];
-    GatherLeaf g{};
-    g.src_off = P.gather_src_off[gi];
-    g.dst_off = N.off;
-    g.rest = N.elems / P.B;
-    auto st = bld.strides(N.layout);
-    g.inner = st.at(P.batch_edge);
-    std::vector<int> sl_here;
-    for (int e : leaf_src_layout[i])
-      if (sliced_mark[e]) sl_here.push_back(e);
-    TN_CHECK(sl_here.size() <= 8, TN_ERR_UNSUPPORTED, "a leaf holds more than 8 sliced edges");
-    g.n_sel = (int)sl_here.size();
-    for (int j = 0; j < g.n_sel; ++j) {
-      int e = sl_here[j];
-      g.slice_bit[j] = (int)(std::find(P.sliced.begin(), P.sliced.end(), e) - P.sliced.begin());
-      g.sel_stride[j] = g.rest << (g.n_sel - 1 - j);
-    }
-    P.gather.push_back(g);
-    P.gather_max_rest = std::max(P.gather_max_rest, g.rest);
-  }
-
   if (P.flags & TN_FLAG_PLAN_ONLY) return Pp;
+
   // ------------------------------------------------------------ device setup
-  TN_CUDA(cudaMalloc(&P.d_plan, std::max<int64_t>(P.plan_bytes, 256)));
   TN_CUDA(cudaMalloc(&P.d_slice_ids, sizeof(int64_t) * P.B));
   TN_CUDA(cudaMalloc(&P.d_n_valid, sizeof(int32_t)));
-  if (!P.gather.empty()) {
-    TN_CUDA(cudaMalloc(&P.d_gather, sizeof(GatherLeaf) * P.gather.size()));
-    TN_CUDA(cudaMemcpyAsync(P.d_gather, P.gather.data(), sizeof(GatherLeaf) * P.gather.size(),
-                            cudaMemcpyHostToDevice, stream));
+  TN_CUDA(cudaMalloc(&P.d_err, sizeof(int)));
+  TN_CUDA(cudaMemsetAsync(P.d_err, 0, sizeof(int), stream));
+  {
+    std::vector<int64_t> ids(P.B);
+    const int64_t S = int64_t(1) << P.sliced.size();
+    for (int b = 0; b < P.B; ++b) ids[b] = b % S;
+    int32_t nv = P.B;
+    TN_CUDA(cudaMemcpyAsync(P.d_slice_ids, ids.data(), sizeof(int64_t) * P.B, cudaMemcpyHostToDevice, stream));
+    TN_CUDA(cudaMemcpyAsync(P.d_n_valid, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    TN_CUDA(cudaStreamSynchronize(stream));
   }
-  // upload leaves: complex128 host -> device staging -> complex64 in plan layout
   void* d_stage = nullptr;
   TN_CUDA(cudaMalloc(&d_stage, std::max<int64_t>(total_leaf_elems * 16, 256)));
   TN_CUDA(cudaMemcpyAsync(d_stage, net->leaf_data, total_leaf_elems * 16, cudaMemcpyHostToDevice, stream));
-  for (int i = 0; i < P.n_leaves; ++i) {
-    // host strides of leaf i (row-major in leaf_edges order)
-    std::map<int, int64_t> hs;
-    int64_t acc = 1;
-    for (int j = (int)P.leaf_edges[i].size() - 1; j >= 0; --j) {
-      hs[P.leaf_edges[i][j]] = acc;
-      acc *= P.dim[P.leaf_edges[i][j]];
+  // upload every leaf into plan memory `pbase` laid out by `M` in storage kind `kind`
+  auto upload_leaves = [&](const MemPlan& M, char* pbase, int kind) {
+    for (int i = 0; i < P.n_leaves; ++i) {
+      std::map<int, int64_t> hs;
+      int64_t acc = 1;
+      for (int j = (int)P.leaf_edges[i].size() - 1; j >= 0; --j) {
+        hs[P.leaf_edges[i][j]] = acc;
+        acc *= P.dim[P.leaf_edges[i][j]];
+      }
+      StridedCopy sc{};
+      sc.nd = (int)leaf_src_layout[i].size();
+      int64_t el = 1;
+      for (int d = 0; d < sc.nd; ++d) {
+        int e = leaf_src_layout[i][d];
+        sc.dims[d] = P.dim[e];
+        sc.in_stride[d] = hs.at(e);
+        el *= P.dim[e];
+      }
+      const char* src = (const char*)d_stage + P.leaf_off[i] * 16;
+      launch_strided_copy_c128(src, pbase + leaf_src_offset(M, P, i), sc, el, kind,
+                               ldexp(1.0, -P.nodes[i].exp2), stream);
     }
-    StridedCopy sc{};
-    sc.nd = (int)leaf_src_layout[i].size();
-    TN_CHECK(sc.nd <= kMaxBits, TN_ERR_UNSUPPORTED, "leaf rank too large");
-    for (int d = 0; d < sc.nd; ++d) {
-      int e = leaf_src_layout[i][d];
-      sc.dims[d] = P.dim[e];
-      sc.in_stride[d] = hs.at(e);
+  };
+  auto upload_gather = [&](const MemPlan& M, GatherLeaf** dtab) {
+    if (M.gather.empty()) return;
+    TN_CUDA(cudaMalloc(dtab, sizeof(GatherLeaf) * M.gather.size()));
+    TN_CUDA(cudaMemcpyAsync(*dtab, M.gather.data(), sizeof(GatherLeaf) * M.gather.size(), cudaMemcpyHostToDevice,
+                            stream));
+  };
+  auto run_hoisted = [&](const MemPlan& M, char* pbase, unsigned* amax) {
+    void* scratch = nullptr;
+    if (M.create_scratch) TN_CUDA(cudaMalloc(&scratch, M.create_scratch));
+    Exec X{P, M, pbase, (char*)scratch};
+    Recorder R{nullptr, stream};
+    for (size_t t = 0; t < P.steps.size(); ++t)
+      if (P.steps[t].hoisted) enqueue_step(X, t, stream, R, amax);
+    TN_CUDA(cudaStreamSynchronize(stream));
+    if (scratch) cudaFree(scratch);
+  };
+
+  if (P.skind != KIND_C64) {
+    // calibration: one complex64 batch (slice ids 0..B-1) records every tensor's
+    // largest component; exponents make the stored maxima lie in [1/2, 1)
+    MemPlan Mc = plan_memory(P, true, leaf_src_layout);
+    char *cplan = nullptr, *cws = nullptr;
+    unsigned* d_amax = nullptr;
+    GatherLeaf* cgather = nullptr;
+    auto cleanup = [&] {
+      if (cplan) cudaFree(cplan);
+      if (cws) cudaFree(cws);
+      if (d_amax) cudaFree(d_amax);
+      if (cgather) cudaFree(cgather);
+    };
+    try {
+      TN_CUDA(cudaMalloc(&cplan, std::max<int64_t>(Mc.plan_bytes, 256)));
+      TN_CUDA(cudaMalloc(&cws, std::max<int64_t>(Mc.ws_bytes, 256)));
+      TN_CUDA(cudaMalloc(&d_amax, sizeof(unsigned) * P.nodes.size()));
+      TN_CUDA(cudaMemsetAsync(d_amax, 0, sizeof(unsigned) * P.nodes.size(), stream));
+      upload_leaves(Mc, cplan, KIND_C64);
+      upload_gather(Mc, &cgather);
+      std::swap(P.d_gather, cgather);
+      run_hoisted(Mc, cplan, d_amax);
+      enqueue_batch_mem(P, Mc, cplan, cws, nullptr, 0, stream, nullptr, d_amax, false);
+      std::swap(P.d_gather, cgather);
+      std::vector<unsigned> h(P.nodes.size());
+      TN_CUDA(cudaMemcpyAsync(h.data(), d_amax, sizeof(unsigned) * h.size(), cudaMemcpyDeviceToHost, stream));
+      TN_CUDA(cudaStreamSynchronize(stream));
+      TN_CUDA(cudaGetLastError());
+      for (size_t x = 0; x < P.nodes.size(); ++x) {
+        float a;
+        std::memcpy(&a, &h[x], 4);
+        TN_CHECK(std::isfinite(a), TN_ERR_NUMERIC, "calibration found a non-finite value");
+        int e = 0;
+        if (a > 0) std::frexp(a, &e);
+        P.nodes[x].exp2 = ((int)x == P.root) ? 0 : e;
+      }
+    } catch (...) {
+      cudaStreamSynchronize(stream);
+      cleanup();
+      cudaFree(d_stage);
+      throw;
     }
-    const char* src = (const char*)d_stage + P.leaf_off[i] * 16;
-    void* dst = (char*)P.d_plan + (P.nodes[i].variant ? P.gather_src_off[std::find(P.gather_node.begin(),
-                                                                                      P.gather_node.end(), i) -
-                                                                            P.gather_node.begin()]
-                                                       : P.nodes[i].off);
-    launch_strided_copy_c128_to_c64(src, dst, sc, leaf_src_elems[i], stream);
+    cleanup();
   }
-  // hoisted steps
-  void* d_scratch = nullptr;
-  if (create_scratch) TN_CUDA(cudaMalloc(&d_scratch, create_scratch));
-  for (auto& S : P.steps) {
-    if (!S.hoisted) continue;
-    GemmParams g = S.gp;
-    g.A = (char*)P.d_plan + P.nodes[S.a].off;
-    g.B = (char*)P.d_plan + P.nodes[S.b].off;
-    void* dst = (char*)P.d_plan + P.nodes[S.c].off;
-    g.C = S.post_perm ? d_scratch : dst;
-    launch_gemm_c64(g, 0, stream);
-    if (S.post_perm) launch_bit_permute_c64(d_scratch, dst, S.perm, stream);
-  }
+  TN_CUDA(cudaMalloc(&P.d_plan, std::max<int64_t>(P.mem.plan_bytes, 256)));
+  upload_leaves(P.mem, (char*)P.d_plan, P.skind);
+  upload_gather(P.mem, &P.d_gather);
+  run_hoisted(P.mem, (char*)P.d_plan, nullptr);
   TN_CUDA(cudaStreamSynchronize(stream));
   TN_CUDA(cudaGetLastError());
   cudaFree(d_stage);
-  if (d_scratch) cudaFree(d_scratch);
+  int h_err = 0;
+  TN_CUDA(cudaMemcpy(&h_err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  TN_CHECK(h_err == 0, TN_ERR_TIMEOUT, "a bounded device wait timed out during plan creation");
   TN_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
   return Pp;
 }
 
 // ---------------------------------------------------------------- execute
-namespace {
-struct Recorder {
-  std::vector<LaunchRecord>* rec;
-  cudaStream_t s;
-  void begin(int kind, double flops, double bytes) {
-    if (!rec) return;
-    LaunchRecord r{kind, flops, bytes, nullptr, nullptr};
-    TN_CUDA(cudaEventCreate(&r.start));
-    TN_CUDA(cudaEventCreate(&r.stop));
-    TN_CUDA(cudaEventRecord(r.start, s));
-    rec->push_back(r);
-  }
-  void end() {
-    if (rec) TN_CUDA(cudaEventRecord(rec->back().stop, s));
-  }
-};
-}  // namespace
-
-static void enqueue_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t s,
-                          std::vector<LaunchRecord>* rec) {
-  char* wb = (char*)ws;
-  char* pb = (char*)P.d_plan;
-  Recorder R{rec, s};
-  const double eb = P.elem_bytes;
-  auto base = [&](int node) -> char* { return (P.nodes[node].plan_mem ? pb : wb) + P.nodes[node].off; };
-  if (!P.gather.empty()) {
-    double bytes = 0;
-    for (auto& g : P.gather) bytes += 2.0 * g.rest * P.B * eb;
-    R.begin(2, 0, bytes);
-    launch_gather_leaves(P.d_gather, (int)P.gather.size(), P.gather_max_rest, P.d_slice_ids, P.B, pb, wb,
-                         s);
-    R.end();
-  }
-  for (auto& S : P.steps) {
-    if (S.hoisted) continue;
-    GemmParams g = S.gp;
-    g.A = base(S.a);
-    g.B = base(S.b);
-    char* dst = base(S.c);
-    g.C = S.post_perm ? wb + S.tmp_off : dst;
-    R.begin(0, 8.0 * S.cost,
-            eb * ((double)P.nodes[S.a].elems + (double)P.nodes[S.b].elems + (double)P.nodes[S.c].elems));
-    launch_gemm_c64(g, 0, s);
-    R.end();
-    if (S.post_perm) {
-      R.begin(1, 0, 2.0 * eb * (double)P.nodes[S.c].elems);
-      launch_bit_permute_c64(wb + S.tmp_off, dst, S.perm, s);
-      R.end();
-    }
-  }
-  R.begin(3, 0, eb * (double)P.nodes[P.root].elems + 16.0 * P.G * P.J * (accumulate ? 2 : 1));
-  launch_accumulate_c64(base(P.root), P.root_sb, P.root_sg, P.root_sj, P.G, P.J, P.d_n_valid, P.B, amps,
-                        accumulate, s);
-  R.end();
-}
-
 // Direct launches only (no graph is built or replayed).
 void run_batch_direct(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream) {
-  enqueue_batch(P, ws, amps, accumulate, stream, nullptr);
+  enqueue_batch_mem(P, P.mem, (char*)P.d_plan, ws, amps, accumulate, stream, nullptr, nullptr, false);
   TN_CUDA(cudaGetLastError());
 }
 
 void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream,
                std::vector<LaunchRecord>* rec) {
   if ((P.flags & TN_FLAG_NO_GRAPH) || rec) {
-    enqueue_batch(P, ws, amps, accumulate, stream, rec);
+    enqueue_batch_mem(P, P.mem, (char*)P.d_plan, ws, amps, accumulate, stream, rec, nullptr, false);
     TN_CUDA(cudaGetLastError());
     return;
   }
@@ -728,7 +911,8 @@ void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t strea
     cudaGraph_t g = nullptr;
     TN_CUDA(cudaStreamBeginCapture(P.capture_stream, cudaStreamCaptureModeThreadLocal));
     try {
-      enqueue_batch(P, ws, amps, accumulate, P.capture_stream, nullptr);
+      enqueue_batch_mem(P, P.mem, (char*)P.d_plan, ws, amps, accumulate, P.capture_stream, nullptr, nullptr,
+                        false);
     } catch (...) {
       cudaStreamEndCapture(P.capture_stream, &g);
       if (g) cudaGraphDestroy(g);

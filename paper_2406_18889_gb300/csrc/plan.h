@@ -10,6 +10,9 @@
 
 namespace tn {
 
+// storage kinds (also the kernels' in/out kinds)
+enum : int { KIND_F16 = 0, KIND_BF16 = 1, KIND_C64 = 2 };
+
 struct Node {
   std::vector<int> edges;   // edge set of this tensor in one sub-network (+ batch edge if variant)
   std::vector<int> layout;  // storage order, slowest first
@@ -18,8 +21,7 @@ struct Node {
   bool leaf = false;
   int leaf_id = -1;
   int consumer = -1;        // step consuming this node; -1 for the root
-  bool plan_mem = false;    // stored in plan-owned memory (leaves, hoisted results)
-  int64_t off = -1;         // byte offset in plan memory or workspace
+  int exp2 = 0;             // stored value = true value * 2^-exp2 (reduced precision)
 };
 
 struct Step {
@@ -29,11 +31,26 @@ struct Step {
   bool post_perm = false;              // lc_nat differs from node c's layout
   bool variant = false;
   bool hoisted = false;                // runs once at plan creation
-  int64_t tmp_off = -1;                // workspace offset of the natural-layout result
   GemmParams gp{};                     // sizes and strides (pointers filled at launch)
   BitPermute perm{};                   // lc_nat -> node c layout
+  bool tc = false;                     // tensor-core GEMM in reduced precision
+  bool tc_swap = false;                // tensor-core A operand is node b (else node a)
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network
+};
+
+// Where every tensor lives for one storage precision.
+struct MemPlan {
+  bool c64 = true;                      // complex64 everywhere (else 16-bit, root in complex64)
+  std::vector<int64_t> off;             // per node: byte offset
+  std::vector<char> in_plan;            // per node: plan memory (1) or workspace (0)
+  std::vector<int64_t> tmp_off;         // per step: natural-layout result before the transpose
+  std::vector<int64_t> bx_off;          // per step: expanded operand of a tensor-core GEMM
+  std::vector<GatherLeaf> gather;       // per sliced leaf
+  std::vector<int> gather_node;
+  int64_t gather_max_rest = 0;
+  int64_t plan_bytes = 0, ws_bytes = 0;
+  int64_t create_scratch = 0;           // transposes of hoisted steps (creation only)
 };
 
 struct Plan {
@@ -54,19 +71,15 @@ struct Plan {
   int root = -1;
   // options
   int prec = TN_PREC_C64;
+  int skind = KIND_C64;                 // storage kind of intermediates
   uint32_t flags = 0;
-  int elem_bytes = 8;
   // memory
+  MemPlan mem;                          // execution
   void* d_plan = nullptr;               // leaves + hoisted results
-  int64_t plan_bytes = 0;
-  int64_t ws_bytes = 0;
   int64_t* d_slice_ids = nullptr;       // [B]
   int32_t* d_n_valid = nullptr;
   GatherLeaf* d_gather = nullptr;       // gather table (device)
-  std::vector<GatherLeaf> gather;       // host copy, pointers relative (filled per call)
-  std::vector<int> gather_node;         // node id of each gather entry
-  std::vector<int64_t> gather_src_off;  // plan-memory offset of each variant leaf's source
-  int64_t gather_max_rest = 0;
+  int* d_err = nullptr;                 // raised by a timed-out device wait
   // root readout strides (elements)
   int64_t root_sb = 0, root_sg = 0, root_sj = 1;
   // statistics

@@ -94,10 +94,15 @@ void launch_strided_copy_c128_to_c64(const void* in, void* out, const StridedCop
                                      int64_t n_out, cudaStream_t s);
 void launch_gather_leaves(const GatherLeaf* d_table, int n_leaves, int64_t max_rest,
                           const int64_t* d_slice_ids, int B, const char* plan_base, char* ws_base,
-                          cudaStream_t s);
+                          cudaStream_t s, int elem_bytes = 8);
 void launch_accumulate_c64(const void* root, int64_t sb, int64_t sg, int64_t sj, int64_t G,
                            int64_t J, const int32_t* d_n_valid, int B, void* amps, int accumulate,
-                           cudaStream_t s);
+                           cudaStream_t s, double scale = 1.0);
+void launch_bit_permute(const void* in, void* out, const BitPermute& bp, int elem_bytes, cudaStream_t s);
+void launch_strided_copy_c128(const void* in, void* out, const StridedCopy& sc, int64_t n_out, int out_kind,
+                              double scale, cudaStream_t s);
+void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s);
+void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
 struct TopkParams {
   int64_t G, Bsz;   // blocks and entries per block

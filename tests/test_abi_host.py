@@ -79,7 +79,7 @@ def test_hoist_flag_marks_invariant_steps(lib, prep):
 
 @pytest.mark.parametrize("mutate,status", [
     ("bad_pair", 1), ("repeat_pair", 1), ("sliced_open", 1), ("sliced_twice", 1),
-    ("batch_not_pow2", 1), ("short_tree", 1), ("bf16_not_built", 5)])
+    ("batch_not_pow2", 1), ("short_tree", 1), ("unknown_precision", 1)])
 def test_plan_validation(lib, prep, mutate, status):
     rank, edges, data = _flat(prep)
     tn, tree = prep.tn, prep.tree
@@ -100,8 +100,8 @@ def test_plan_validation(lib, prep, mutate, status):
         kw["max_slice_batch"] = 6
     elif mutate == "short_tree":
         kw["pairs"] = pairs[:-2]
-    elif mutate == "bf16_not_built":
-        kw["prec"] = 1
+    elif mutate == "unknown_precision":
+        kw["prec"] = 7
     with pytest.raises(lib.TNError) as ei:
         _create(lib, prep, **kw)
     assert ei.value.status == status
