@@ -58,6 +58,8 @@ typedef enum {
 #define TN_FLAG_NO_GRAPH 0x2u        /* launch kernels directly instead of replaying a CUDA graph */
 #define TN_FLAG_PLAN_ONLY 0x4u       /* host-side planning only: no device memory is touched and
                                         contraction calls on the plan fail (for inspection) */
+#define TN_FLAG_HILO 0x8u            /* reduced precision: every tensor-core step multiplies
+                                        split-precision operands (hi + lo, three passes) */
 
 typedef struct tn_plan_s* tn_plan_t;
 
@@ -128,13 +130,15 @@ typedef struct {
  * memory layout (contracted dimensions of both operands in one order, free
  * dimensions in the output's order, so most steps need no transpose), plans
  * workspace offsets, and copies the leaves to the device.
- * Reduced precision (TN_PREC_BF16 / TN_PREC_FP16): intermediates are stored
- * as 16-bit complex pairs scaled by a per-tensor power of two 2^-e (so that
- * amplitudes far below the 16-bit normal range do not underflow); e is fixed
- * at creation by one complex64 calibration batch (slice ids 0..B-1) as the
- * exponent of the tensor's largest component.  The root (final amplitudes of
- * each slice) is kept in complex64.  Large steps run on the tensor cores as a
- * real GEMM with FP32 accumulation, small ones on CUDA cores in FP32.
+ * Reduced precision (TN_PREC_BF16 / TN_PREC_FP16): large steps run on the
+ * tensor cores as one real GEMM with FP32 accumulation; the operand read by
+ * the tensor cores as stored is kept as 16-bit complex pairs scaled by a
+ * per-tensor power of two 2^-e (so that amplitudes far below the 16-bit normal
+ * range do not underflow), the other operand is rounded to 16 bits when it is
+ * expanded; with TN_FLAG_HILO both are split into hi + lo 16-bit parts.  Every
+ * other tensor, the small steps (CUDA cores, FP32) and the root stay in
+ * complex64.  e is fixed at creation by one complex64 calibration batch
+ * (slice ids 0..B-1) as the exponent of the tensor's largest component.
  * Creation temporarily needs a complex64 workspace for the calibration.
  * Synchronises `stream`.  *out is set only on success; destroy with
  * tn_plan_destroy.
@@ -161,7 +165,8 @@ tn_status tn_plan_query(tn_plan_t plan, int64_t* useful_flops_per_slice,
 /* Per-step description for profiling and tests: the step's GEMM shape and
  * whether it runs once per slice batch (variant) or once per plan.  kinds[t]
  * bit 0 = variant, bit 1 = needs an output transpose, bit 2 = hoisted (runs
- * at plan creation), bit 3 = tensor-core GEMM (reduced precision). */
+ * at plan creation), bit 3 = tensor-core GEMM (reduced precision), bit 4 =
+ * split-precision (hi + lo) tensor-core GEMM. */
 tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64_t* m,
                         int64_t* n, int64_t* k, int32_t* kinds, int32_t* n_steps_out);
 

@@ -22,6 +22,7 @@ TN_PREC_C64, TN_PREC_BF16, TN_PREC_FP16 = 0, 1, 2
 TN_FLAG_HOIST_INVARIANT = 0x1
 TN_FLAG_NO_GRAPH = 0x2
 TN_FLAG_PLAN_ONLY = 0x4
+TN_FLAG_HILO = 0x8
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",

@@ -39,6 +39,20 @@ struct BF16 {
   static __device__ __forceinline__ float2 ld(const T& v) { return __bfloat1622float2(v); }
   static __device__ __forceinline__ T st(float2 v) { return __floats2bfloat162_rn(v.x, v.y); }
 };
+// store v as a 16-bit pair plus its rounding residual (hi + lo)
+template <class H>
+__device__ __forceinline__ void store_out(typename H::T* C, typename H::T* C2, int64_t o, float2 v, bool hilo) {
+  const typename H::T hi = H::st(v);
+  C[o] = hi;
+  if (hilo) {
+    const float2 h = H::ld(hi);
+    C2[o] = H::st(make_float2(v.x - h.x, v.y - h.y));
+  }
+}
+template <>
+__device__ __forceinline__ void store_out<C64>(float2* C, float2*, int64_t o, float2 v, bool) {
+  C[o] = v;
+}
 
 __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -48,7 +62,7 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
 }
 
 template <int TM, int TN, int TK, int TY, int TX, class In, class Out>
-__global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale) {
+__global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, bool hilo) {
   static_assert(TY * TX == 256, "256 threads");
   constexpr int RM = TM / TY, RN = TN / TX;
   __shared__ float2 As[TK][TM + 1];
@@ -128,7 +142,8 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale) {
       for (int j = 0; j < RN; ++j) {
         int64_t gn = n0 + tx + j * TX;
         if (gn < p.N)
-          Cb[gm * p.sc_m + gn * p.sc_n] = Out::st(make_float2(acc[i][j].x * scale, acc[i][j].y * scale));
+          store_out<Out>(Cb, (TO*)p.C2 + bt * p.sc_bt, gm * p.sc_m + gn * p.sc_n,
+                         make_float2(acc[i][j].x * scale, acc[i][j].y * scale), hilo);
       }
     }
   }
@@ -136,7 +151,7 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale) {
 
 // one thread per output element (bt, m, n), n fastest
 template <class In, class Out>
-__global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale) {
+__global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bool hilo) {
   using TI = typename In::T;
   using TO = typename Out::T;
   const TI* __restrict__ A = (const TI*)p.A;
@@ -153,34 +168,35 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale) {
     const TI* b = Bm + bt * p.sb_bt + n * p.sb_n;
     float2 acc = make_float2(0.f, 0.f);
     for (int64_t k = 0; k < p.K; ++k) cmac(acc, In::ld(a[k * p.sa_k]), In::ld(b[k * p.sb_k]));
-    C[bt * p.sc_bt + m * p.sc_m + n * p.sc_n] = Out::st(make_float2(acc.x * scale, acc.y * scale));
+    store_out<Out>(C, (TO*)p.C2, bt * p.sc_bt + m * p.sc_m + n * p.sc_n,
+                   make_float2(acc.x * scale, acc.y * scale), hilo);
   }
 }
 
 template <int TM, int TN, int TK, int TY, int TX, class In, class Out>
-void launch_tiled(const GemmParams& p, float scale, cudaStream_t s) {
+void launch_tiled(const GemmParams& p, float scale, bool hilo, cudaStream_t s) {
   int64_t gx = (p.N + TN - 1) / TN, gy = (p.M + TM - 1) / TM;
   TN_CHECK(gx < (1LL << 31) && gy < 65536, TN_ERR_UNSUPPORTED, "GEMM grid too large");
   unsigned gz = (unsigned)std::min<int64_t>(p.nbt, 65535);
-  gemm_tiled<TM, TN, TK, TY, TX, In, Out><<<dim3((unsigned)gx, (unsigned)gy, gz), 256, 0, s>>>(p, scale);
+  gemm_tiled<TM, TN, TK, TY, TX, In, Out><<<dim3((unsigned)gx, (unsigned)gy, gz), 256, 0, s>>>(p, scale, hilo);
 }
 
 template <class In, class Out>
-void launch_typed(const GemmParams& p, float scale, cudaStream_t s) {
+void launch_typed(const GemmParams& p, float scale, cudaStream_t s, bool hilo = false) {
   const int64_t outputs = p.nbt * p.M * p.N;
   if (p.K <= 4 || (p.M < 16 && p.N < 16) || outputs * p.K < (1 << 16)) {
     int64_t blocks = std::min<int64_t>((outputs + 255) / 256, 152 * 64);
-    gemm_direct<In, Out><<<(unsigned)blocks, 256, 0, s>>>(p, scale);
+    gemm_direct<In, Out><<<(unsigned)blocks, 256, 0, s>>>(p, scale, hilo);
     return;
   }
   if (p.M >= 64 && p.N >= 64)
-    launch_tiled<64, 64, 16, 16, 16, In, Out>(p, scale, s);
+    launch_tiled<64, 64, 16, 16, 16, In, Out>(p, scale, hilo, s);
   else if (p.M < 32 && p.N >= 128)
-    launch_tiled<16, 128, 16, 8, 32, In, Out>(p, scale, s);
+    launch_tiled<16, 128, 16, 8, 32, In, Out>(p, scale, hilo, s);
   else if (p.N < 32 && p.M >= 128)
-    launch_tiled<128, 16, 16, 32, 8, In, Out>(p, scale, s);
+    launch_tiled<128, 16, 16, 32, 8, In, Out>(p, scale, hilo, s);
   else
-    launch_tiled<32, 32, 16, 16, 16, In, Out>(p, scale, s);
+    launch_tiled<32, 32, 16, 16, 16, In, Out>(p, scale, hilo, s);
 }
 
 }  // namespace
@@ -191,13 +207,16 @@ void launch_gemm_c64(const GemmParams& p, int accumulate, cudaStream_t s) {
   launch_typed<C64, C64>(p, 1.0f, s);
 }
 
-// in_kind / out_kind: 0 = fp16 complex, 1 = bf16 complex, 2 = fp32 complex
-void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s) {
+// in_kind / out_kind: 0 = fp16 complex, 1 = bf16 complex, 2 = fp32 complex;
+// out_hilo: a 16-bit output also stores its rounding residual in p.C2
+void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s, bool out_hilo) {
   if (p.nbt <= 0 || p.M <= 0 || p.N <= 0) return;
   if (in_kind == 2 && out_kind == 2) return launch_typed<C64, C64>(p, scale, s);
-  if (in_kind == 0 && out_kind == 0) return launch_typed<F16, F16>(p, scale, s);
+  if (in_kind == 2 && out_kind == 0) return launch_typed<C64, F16>(p, scale, s, out_hilo);
+  if (in_kind == 2 && out_kind == 1) return launch_typed<C64, BF16>(p, scale, s, out_hilo);
+  if (in_kind == 0 && out_kind == 0) return launch_typed<F16, F16>(p, scale, s, out_hilo);
   if (in_kind == 0 && out_kind == 2) return launch_typed<F16, C64>(p, scale, s);
-  if (in_kind == 1 && out_kind == 1) return launch_typed<BF16, BF16>(p, scale, s);
+  if (in_kind == 1 && out_kind == 1) return launch_typed<BF16, BF16>(p, scale, s, out_hilo);
   if (in_kind == 1 && out_kind == 2) return launch_typed<BF16, C64>(p, scale, s);
   fail(TN_ERR_UNSUPPORTED, "GEMM storage combination");
 }

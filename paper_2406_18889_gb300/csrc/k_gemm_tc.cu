@@ -108,9 +108,12 @@ constexpr size_t smem_bytes() {
   return 1024 + (size_t)STAGES * (BM + BN) * BK * 2 + 256;
 }
 
-template <int BN, bool BF16>
+// HILO: three accumulating passes over K -- (A, B), (A, B_lo), (A_lo, B) -- the
+// split-precision product that drops only the lo*lo term
+template <int BN, bool BF16, bool HILO>
 __global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
                    TcGemmParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -124,7 +127,8 @@ __global__ void __launch_bounds__(192, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tile = blockIdx.x, m_tile = blockIdx.y;
   const int bt = blockIdx.z;
-  const int k_tiles = (int)((2 * p.K + BK - 1) / BK);
+  const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
+  const int k_tiles = HILO ? 3 * k_tiles1 : k_tiles1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -153,9 +157,11 @@ __global__ void __launch_bounds__(192, 1)
         const int s = kt % STAGES;
         const uint32_t use = kt / STAGES;
         if (kt >= STAGES && !wait_bounded(&empty[s], (use & 1) ^ 1, p.err)) break;
+        const int pass = HILO ? kt / k_tiles1 : 0;
+        const int kx = (kt - pass * k_tiles1) * BK;
         mbar_expect_tx(&full[s], (uint32_t)((BM + BN) * BK * 2));
-        tma_load_3d(&tmA, &full[s], sA + s * BM * BK * 2, kt * BK, m_tile * BM, bt);
-        tma_load_3d(&tmB, &full[s], sB + s * BN * BK * 2, kt * BK, n_tile * BN, bt);
+        tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + s * BM * BK * 2, kx, m_tile * BM, bt);
+        tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
         ++issued;
       }
       // drain: every issued load must have landed before the CTA can exit
@@ -231,9 +237,19 @@ __global__ void __launch_bounds__(192, 1)
             if (p.out_kind == 2) {
               reinterpret_cast<float2*>(p.C)[o] = make_float2(re, im);
             } else if (p.out_kind == 1) {
-              reinterpret_cast<__nv_bfloat162*>(p.C)[o] = __floats2bfloat162_rn(re, im);
+              const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+              reinterpret_cast<__nv_bfloat162*>(p.C)[o] = h;
+              if (p.out_hilo) {
+                const float2 hf = __bfloat1622float2(h);
+                reinterpret_cast<__nv_bfloat162*>(p.C2)[o] = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+              }
             } else {
-              reinterpret_cast<__half2*>(p.C)[o] = __floats2half2_rn(re, im);
+              const __half2 h = __floats2half2_rn(re, im);
+              reinterpret_cast<__half2*>(p.C)[o] = h;
+              if (p.out_hilo) {
+                const float2 hf = __half22float2(h);
+                reinterpret_cast<__half2*>(p.C2)[o] = __floats2half2_rn(re - hf.x, im - hf.y);
+              }
             }
           }
         }
@@ -284,16 +300,18 @@ void make_map(CUtensorMap* map, const void* base, bool bf16, uint64_t inner, uin
   TN_CHECK(r == CUDA_SUCCESS, TN_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
-template <int BN, bool BF16>
-void launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const TcGemmParams& p, cudaStream_t s) {
+template <int BN, bool BF16, bool HILO>
+void launch_bn(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+               const TcGemmParams& p, cudaStream_t s) {
   const size_t sm = smem_bytes<BN>();
   static bool attr = false;
   if (!attr) {
-    TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, BF16, HILO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm));
     attr = true;
   }
   dim3 grid((unsigned)((2 * p.N + BN - 1) / BN), (unsigned)((p.M + BM - 1) / BM), (unsigned)p.nbt);
-  tc_gemm_kernel<BN, BF16><<<grid, 192, sm, s>>>(ma, mb, p);
+  tc_gemm_kernel<BN, BF16, HILO><<<grid, 192, sm, s>>>(ma, ma2, mb, mb2, p);
 }
 
 }  // namespace
@@ -310,25 +328,41 @@ int tc_gemm_bn(int64_t N) {
 
 // A: complex 16-bit [bt][M][K] with k contiguous (strides sa_bt, sa_m in complex
 // elements); Bx: expanded real [bt][2N][pitch] (pitch = round_up(2K, 64)).
-void launch_gemm_tc(const void* A, int64_t sa_bt, int64_t sa_m, const void* Bx, const TcGemmParams& p, bool bf16,
-                    cudaStream_t s) {
+void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m, const void* Bx,
+                    const void* Bx_lo, const TcGemmParams& p, bool bf16, cudaStream_t s) {
   if (p.nbt <= 0 || p.M <= 0 || p.N <= 0) return;
   TN_CHECK(tc_gemm_supported(p.nbt, p.M, p.N, p.K, sa_bt, sa_m, 1), TN_ERR_UNSUPPORTED,
            "shape not supported by the tensor-core GEMM");
+  const bool hilo = A_lo != nullptr && Bx_lo != nullptr;
   const int bn = p.bn;
   const uint64_t pitch = (uint64_t)((2 * p.K + BK - 1) / BK * BK);
-  CUtensorMap ma, mb;
+  CUtensorMap ma, ma2, mb, mb2;
   const uint64_t a_row = (uint64_t)sa_m * 4, a_bt = p.nbt > 1 ? (uint64_t)sa_bt * 4 : a_row * (uint64_t)p.M;
-  make_map(&ma, A, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row,
-           (a_bt + 15) / 16 * 16, BM);
+  make_map(&ma, A, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row, (a_bt + 15) / 16 * 16, BM);
   make_map(&mb, Bx, bf16, pitch, (uint64_t)(2 * p.N), (uint64_t)p.nbt, pitch * 2, pitch * 2 * 2 * p.N,
            (uint32_t)bn);
-#define TN_TC_CASE(BNV)                                        \
-  case BNV:                                                    \
-    if (bf16)                                                  \
-      launch_bn<BNV, true>(ma, mb, p, s);                      \
-    else                                                       \
-      launch_bn<BNV, false>(ma, mb, p, s);                     \
+  if (hilo) {
+    make_map(&ma2, A_lo, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row, (a_bt + 15) / 16 * 16,
+             BM);
+    make_map(&mb2, Bx_lo, bf16, pitch, (uint64_t)(2 * p.N), (uint64_t)p.nbt, pitch * 2, pitch * 2 * 2 * p.N,
+             (uint32_t)bn);
+  } else {
+    ma2 = ma;
+    mb2 = mb;
+  }
+#define TN_TC_CASE(BNV)                                                       \
+  case BNV:                                                                   \
+    if (bf16) {                                                               \
+      if (hilo)                                                               \
+        launch_bn<BNV, true, true>(ma, ma2, mb, mb2, p, s);                   \
+      else                                                                    \
+        launch_bn<BNV, true, false>(ma, ma2, mb, mb2, p, s);                  \
+    } else {                                                                  \
+      if (hilo)                                                               \
+        launch_bn<BNV, false, true>(ma, ma2, mb, mb2, p, s);                  \
+      else                                                                    \
+        launch_bn<BNV, false, false>(ma, ma2, mb, mb2, p, s);                 \
+    }                                                                         \
     break;
   switch (bn) {
     TN_TC_CASE(32)
@@ -355,44 +389,68 @@ __device__ __forceinline__ __nv_bfloat16 neg16(__nv_bfloat16 x) {
 }
 
 // Bx[bt][2n+0][2k..2k+1] = (Re B, -Im B)[k][n], Bx[bt][2n+1][2k..2k+1] = (Im B, Re B)[k][n];
-// columns past 2K up to the pitch are zero
-template <class T2, class T>
-__global__ void expand_b_kernel(const T2* __restrict__ B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt,
-                                int64_t N, int64_t K, int64_t half_pitch, T2* __restrict__ Bx) {
+// columns past 2K up to the pitch are zero.  With Bx_lo, every entry's
+// rounding residual (exact value - 16-bit value) goes to Bx_lo.
+template <class T2, class T, class TIN>
+__global__ void expand_b_kernel(const TIN* __restrict__ B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt,
+                                int64_t N, int64_t K, int64_t half_pitch, T2* __restrict__ Bx,
+                                T2* __restrict__ Bx_lo) {
   const int64_t total = nbt * N * half_pitch;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = x % half_pitch;
     const int64_t t = x / half_pitch;
     const int64_t n = t % N, bt = t / N;
-    T2 r0, r1;
+    float re = 0.f, im = 0.f;
     if (k < K) {
-      const T2 v = B[bt * sb_bt + k * sb_k + n * sb_n];
-      r0.x = v.x;
-      r0.y = neg16<T>(v.y);
-      r1.x = v.y;
-      r1.y = v.x;
-    } else {
-      r0.x = r0.y = r1.x = r1.y = T(0.0f);
+      const TIN v = B[bt * sb_bt + k * sb_k + n * sb_n];
+      re = (float)v.x;
+      im = (float)v.y;
     }
+    const T hre = T(re), him = T(im);
+    T2 r0, r1;
+    r0.x = hre;
+    r0.y = neg16<T>(him);
+    r1.x = him;
+    r1.y = hre;
     const int64_t row0 = (bt * 2 * N + 2 * n) * half_pitch;
     Bx[row0 + k] = r0;
     Bx[row0 + half_pitch + k] = r1;
+    if (Bx_lo) {
+      const T lre = T(re - (float)hre), lim = T(im - (float)him);
+      T2 l0, l1;
+      l0.x = lre;
+      l0.y = neg16<T>(lim);
+      l1.x = lim;
+      l1.y = lre;
+      Bx_lo[row0 + k] = l0;
+      Bx_lo[row0 + half_pitch + k] = l1;
+    }
   }
 }
 }  // namespace
 
 void launch_expand_b(const void* B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt, int64_t N, int64_t K,
-                     bool bf16, void* Bx, cudaStream_t s) {
+                     bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo) {
   const int64_t half_pitch = (2 * K + BK - 1) / BK * BK / 2;
   const int64_t total = nbt * N * half_pitch;
   if (total <= 0) return;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  if (bf16)
-    expand_b_kernel<__nv_bfloat162, __nv_bfloat16><<<blocks, 256, 0, s>>>(
-        (const __nv_bfloat162*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx);
-  else
-    expand_b_kernel<__half2, __half><<<blocks, 256, 0, s>>>((const __half2*)B, sb_bt, sb_k, sb_n, nbt, N, K,
-                                                           half_pitch, (__half2*)Bx);
+  if (bf16) {
+    if (in_c64)
+      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2><<<blocks, 256, 0, s>>>(
+          (const float2*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo);
+    else
+      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162><<<blocks, 256, 0, s>>>(
+          (const __nv_bfloat162*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
+          (__nv_bfloat162*)Bx_lo);
+  } else {
+    if (in_c64)
+      expand_b_kernel<__half2, __half, float2><<<blocks, 256, 0, s>>>(
+          (const float2*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
+    else
+      expand_b_kernel<__half2, __half, __half2><<<blocks, 256, 0, s>>>(
+          (const __half2*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
+  }
 }
 
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K) {
@@ -491,7 +549,7 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
     p.scale = 1.0f;
     p.err = d_err;
     p.bn = tc_gemm_bn(N);
-    launch_gemm_tc(A, M * K, K, Bx, p, bf16, s);
+    launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
     if (bf16)
       ref_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>((const __nv_bfloat162*)A, (const __nv_bfloat162*)B,
                                                      (float2*)R, nbt, M, N, K);

@@ -13,52 +13,70 @@
 namespace tn {
 
 // ------------------------------------------------------------ bit permute
-// A CTA moves one tile: the input's 5 fastest bits (coalesced 256-byte reads)
-// together with the bits that become the output's 5 fastest (coalesced
-// writes), staged through shared memory; the remaining bits index the grid.
+// A tile is 2^nt elements (nt <= 12): the input's fastest bits (coalesced
+// reads) together with the input bits that become the output's fastest bits
+// (coalesced writes), staged through shared memory.  The remaining bits index
+// the tiles; each CTA walks tiles with a grid stride.  Per-element offsets come
+// from two 64-entry tables per direction (low and high 6 bits of the tile
+// index), so the inner loops are two shared-memory loads and an add.
 namespace {
 
-constexpr int kTileMaxBits = 10;
+constexpr int kTileMaxBits = 12;
 
 struct PermTile {
   int nt;                   // tile bits
   int tin[kTileMaxBits];    // input bit position of tile bit i (read order)
   int tpos_w[kTileMaxBits]; // tile bit index of the i-th write-order bit
   int tout_w[kTileMaxBits]; // output bit position of the i-th write-order bit
-  int ng;                   // grid bits
+  int ng;                   // tile-index bits
   int gin[kMaxBits];
   int gout[kMaxBits];
 };
 
+__device__ __forceinline__ int pad(int t) { return t + (t >> 6); }
+
 template <class W>
 __global__ void __launch_bounds__(256) bit_permute_kernel(const W* __restrict__ in, W* __restrict__ out,
                                                           PermTile pt) {
-  __shared__ W tile[(1 << kTileMaxBits) + (1 << kTileMaxBits) / 16];
-  const int64_t blk = blockIdx.x;
-  int64_t base_in = 0, base_out = 0;
-  for (int j = 0; j < pt.ng; ++j) {
-    int64_t bit = (blk >> j) & 1;
-    base_in |= bit << pt.gin[j];
-    base_out |= bit << pt.gout[j];
-  }
-  const int n = 1 << pt.nt;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    int64_t off = base_in;
-#pragma unroll 4
-    for (int i = 0; i < pt.nt; ++i) off |= (int64_t)((t >> i) & 1) << pt.tin[i];
-    tile[t + (t >> 4)] = in[off];
+  __shared__ W tile[(1 << kTileMaxBits) + (1 << kTileMaxBits) / 64];
+  __shared__ int64_t in_lo[64], in_hi[64], out_lo[64], out_hi[64];
+  __shared__ int t_lo[64], t_hi[64];
+  const int tid = threadIdx.x;
+  if (tid < 64) {
+    int64_t a = 0, b = 0, c = 0, d = 0;
+    int e = 0, f = 0;
+    for (int i = 0; i < pt.nt; ++i) {
+      const int bit_lo = i < 6 ? (tid >> i) & 1 : 0;
+      const int bit_hi = i >= 6 ? (tid >> (i - 6)) & 1 : 0;
+      a |= (int64_t)bit_lo << pt.tin[i];
+      b |= (int64_t)bit_hi << pt.tin[i];
+      c |= (int64_t)bit_lo << pt.tout_w[i];
+      d |= (int64_t)bit_hi << pt.tout_w[i];
+      e |= bit_lo << pt.tpos_w[i];
+      f |= bit_hi << pt.tpos_w[i];
+    }
+    in_lo[tid] = a;
+    in_hi[tid] = b;
+    out_lo[tid] = c;
+    out_hi[tid] = d;
+    t_lo[tid] = e;
+    t_hi[tid] = f;
   }
   __syncthreads();
-  for (int u = threadIdx.x; u < n; u += blockDim.x) {
-    int64_t off = base_out;
-    int t = 0;
-#pragma unroll 4
-    for (int i = 0; i < pt.nt; ++i) {
-      int bit = (u >> i) & 1;
-      off |= (int64_t)bit << pt.tout_w[i];
-      t |= bit << pt.tpos_w[i];
+  const int n = 1 << pt.nt;
+  const int64_t n_tiles = int64_t(1) << pt.ng;
+  for (int64_t blk = blockIdx.x; blk < n_tiles; blk += gridDim.x) {
+    int64_t base_in = 0, base_out = 0;
+    for (int j = 0; j < pt.ng; ++j) {
+      const int64_t bit = (blk >> j) & 1;
+      base_in |= bit << pt.gin[j];
+      base_out |= bit << pt.gout[j];
     }
-    out[off] = tile[t + (t >> 4)];
+    for (int t = tid; t < n; t += 256) tile[pad(t)] = in[base_in + in_lo[t & 63] + in_hi[t >> 6]];
+    __syncthreads();
+    for (int u = tid; u < n; u += 256)
+      out[base_out + out_lo[u & 63] + out_hi[u >> 6]] = tile[pad(t_lo[u & 63] | t_hi[u >> 6])];
+    __syncthreads();
   }
 }
 
@@ -84,7 +102,7 @@ void launch_bit_permute(const void* in, void* out, const BitPermute& bp, int ele
       copy_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, n);
     return;
   }
-  const int a = std::min(5, R);
+  const int a = std::min(6, R);
   int in_of_out[kMaxBits];
   for (int i = 0; i < R; ++i) in_of_out[bp.out_bit[i]] = i;
   bool in_tile[kMaxBits] = {};
@@ -101,8 +119,8 @@ void launch_bit_permute(const void* in, void* out, const BitPermute& bp, int ele
       pt.tin[pt.nt++] = i;
     }
   }
-  // widen the tile while it stays within kTileMaxBits (more work per CTA)
-  for (int i = a; i < R && pt.nt < 8; ++i)
+  // widen the tile to 2^12 elements with the next input bits (more work per tile)
+  for (int i = a; i < R && pt.nt < kTileMaxBits; ++i)
     if (!in_tile[i]) {
       in_tile[i] = true;
       pt.tin[pt.nt++] = i;
@@ -124,12 +142,12 @@ void launch_bit_permute(const void* in, void* out, const BitPermute& bp, int ele
       pt.gout[pt.ng] = bp.out_bit[i];
       ++pt.ng;
     }
-  int64_t blocks = int64_t(1) << pt.ng;
-  TN_CHECK(blocks < (int64_t(1) << 31), TN_ERR_UNSUPPORTED, "transpose grid too large");
+  const int64_t tiles = int64_t(1) << pt.ng;
+  const unsigned blocks = (unsigned)std::min<int64_t>(tiles, 152 * 8);
   if (elem_bytes == 8)
-    bit_permute_kernel<uint2><<<(unsigned)blocks, 256, 0, s>>>((const uint2*)in, (uint2*)out, pt);
+    bit_permute_kernel<uint2><<<blocks, 256, 0, s>>>((const uint2*)in, (uint2*)out, pt);
   else
-    bit_permute_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, pt);
+    bit_permute_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, pt);
 }
 
 void launch_bit_permute_c64(const void* in, void* out, const BitPermute& bp, cudaStream_t s) {

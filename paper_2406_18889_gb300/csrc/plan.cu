@@ -315,9 +315,13 @@ struct Builder {
 // ---------------------------------------------------------------- memory plans
 namespace {
 
+// bytes of node x: complex64 (8), 16-bit complex (4), or hi + lo 16-bit (8)
 int64_t node_bytes(const Plan& P, int x, bool c64) {
-  return P.nodes[x].elems * ((c64 || x == P.root) ? 8 : 4);
+  const Node& N = P.nodes[x];
+  if (c64 || N.kind == KIND_C64 || N.hilo) return N.elems * 8;
+  return N.elems * 4;
 }
+int node_word(const Plan& P, int x, bool c64) { return (c64 || P.nodes[x].kind == KIND_C64) ? 8 : 4; }
 
 // tensor-core operand roles of a step: (A node, a strides) and (B node, b strides)
 struct TcRoles {
@@ -371,7 +375,7 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
       if (S.post_perm) tmax = std::max(tmax, node_bytes(P, S.c, c64));
       if (!c64 && S.tc) {
         TcRoles r = tc_roles(S);
-        bmax = std::max(bmax, expanded_b_bytes(S.gp.nbt, r.N, r.K));
+        bmax = std::max(bmax, expanded_b_bytes(S.gp.nbt, r.N, r.K) * (S.hilo ? 2 : 1));
       }
     }
   for (size_t t = 0; t < P.steps.size(); ++t)
@@ -395,7 +399,7 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
     if (S.post_perm) tmp = M.tmp_off[t] = ws.alloc(node_bytes(P, S.c, c64));
     if (!c64 && S.tc) {
       TcRoles r = tc_roles(S);
-      bx = M.bx_off[t] = ws.alloc(expanded_b_bytes(S.gp.nbt, r.N, r.K));
+      bx = M.bx_off[t] = ws.alloc(expanded_b_bytes(S.gp.nbt, r.N, r.K) * (S.hilo ? 2 : 1));
     }
     if (tmp >= 0) ws.release(tmp);
     if (bx >= 0) ws.release(bx);
@@ -469,13 +473,14 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
   const Plan& P = X.P;
   const MemPlan& M = X.M;
   const Step& S = P.steps[t];
+  const Node& NC = P.nodes[S.c];
   char* dst = X.base(S.c);
   char* out = S.post_perm ? X.wb + M.tmp_off[t] : dst;
-  const int out_kind = (M.c64 || S.c == P.root) ? KIND_C64 : P.skind;
+  const int out_kind = M.c64 ? KIND_C64 : NC.kind;
+  const bool out_hilo = !M.c64 && NC.hilo;
+  const int64_t lo_off = NC.elems * 4;  // hi + lo storage: lo follows hi
   const double flops = 8.0 * S.cost;
-  const double ebytes = M.c64 ? 8.0 : 4.0;
-  const double bytes = ebytes * ((double)P.nodes[S.a].elems + (double)P.nodes[S.b].elems) +
-                       (out_kind == KIND_C64 ? 8.0 : 4.0) * (double)P.nodes[S.c].elems;
+  const double bytes = (double)(node_bytes(P, S.a, M.c64) + node_bytes(P, S.b, M.c64) + node_bytes(P, S.c, M.c64));
   const float scale =
       M.c64 ? 1.0f : ldexpf(1.0f, P.nodes[S.a].exp2 + P.nodes[S.b].exp2 - P.nodes[S.c].exp2);
   if (M.c64) {
@@ -483,14 +488,21 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     g.A = X.base(S.a);
     g.B = X.base(S.b);
     g.C = out;
+    g.C2 = nullptr;
     R.begin(0, flops, bytes);
     launch_gemm_c64(g, 0, s);
     R.end();
   } else if (S.tc) {
     TcRoles r = tc_roles(S);
+    const Node& NA = P.nodes[r.a_node];
     char* bx = X.wb + M.bx_off[t];
-    R.begin(4, 0, ebytes * (double)P.nodes[r.b_node].elems + (double)expanded_b_bytes(S.gp.nbt, r.N, r.K));
-    launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s);
+    const int64_t bx_bytes = expanded_b_bytes(S.gp.nbt, r.N, r.K);
+    char* bx_lo = S.hilo ? bx + bx_bytes : nullptr;
+    const bool b_c64 = P.nodes[r.b_node].kind == KIND_C64;
+    TN_CHECK(NA.kind == P.skind && NA.hilo == S.hilo, TN_ERR_INVALID_ARG, "internal: tensor-core operand storage");
+    R.begin(4, 0, (double)node_bytes(P, r.b_node, false) + (double)bx_bytes * (S.hilo ? 2 : 1));
+    launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s, b_c64,
+                    bx_lo);
     R.end();
     TcGemmParams tp{};
     tp.nbt = S.gp.nbt;
@@ -501,26 +513,34 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     tp.sc_m = r.c_m;
     tp.sc_n = r.c_n;
     tp.C = out;
+    tp.C2 = out_hilo ? out + lo_off : nullptr;
     tp.out_kind = out_kind;
+    tp.out_hilo = out_hilo ? 1 : 0;
     tp.scale = scale;
     tp.err = P.d_err;
     tp.bn = tc_gemm_bn(r.N);
+    const char* a_hi = X.base(r.a_node);
     R.begin(0, flops, bytes);
-    launch_gemm_tc(X.base(r.a_node), r.a_bt, r.a_m, bx, tp, P.skind == KIND_BF16, s);
+    launch_gemm_tc(a_hi, S.hilo ? a_hi + NA.elems * 4 : nullptr, r.a_bt, r.a_m, bx, bx_lo, tp,
+                   P.skind == KIND_BF16, s);
     R.end();
   } else {
+    TN_CHECK(P.nodes[S.a].kind == KIND_C64 && P.nodes[S.b].kind == KIND_C64, TN_ERR_INVALID_ARG,
+             "internal: CUDA-core step operands must be complex64");
     GemmParams g = S.gp;
     g.A = X.base(S.a);
     g.B = X.base(S.b);
     g.C = out;
+    g.C2 = out_hilo ? out + lo_off : nullptr;
     R.begin(0, flops, bytes);
-    launch_gemm_simt(g, P.skind, out_kind, scale, s);
+    launch_gemm_simt(g, KIND_C64, out_kind, scale, s, out_hilo);
     R.end();
   }
   if (S.post_perm) {
     const int pe = out_kind == KIND_C64 ? 8 : 4;
-    R.begin(1, 0, 2.0 * pe * (double)P.nodes[S.c].elems);
+    R.begin(1, 0, 2.0 * (double)node_bytes(P, S.c, M.c64));
     launch_bit_permute(out, dst, S.perm, pe, s);
+    if (out_hilo) launch_bit_permute(out + lo_off, dst + lo_off, S.perm, pe, s);
     R.end();
   }
   if (amax) launch_amax_c64(dst, P.nodes[S.c].elems, amax + S.c, s);
@@ -530,13 +550,12 @@ void enqueue_batch_mem(const Plan& P, const MemPlan& M, char* pb, void* ws, void
                        cudaStream_t s, std::vector<LaunchRecord>* rec, unsigned* amax, bool hoisted_too) {
   Exec X{P, M, pb, (char*)ws};
   Recorder R{rec, s};
-  const double eb = M.c64 ? 8.0 : 4.0;
   if (!M.gather.empty()) {
     double bytes = 0;
-    for (auto& g : M.gather) bytes += 2.0 * g.rest * P.B * eb;
+    for (auto& g : M.gather) bytes += 2.0 * g.rest * P.B * 8.0;
     R.begin(2, 0, bytes);
     launch_gather_leaves(P.d_gather, (int)M.gather.size(), M.gather_max_rest, P.d_slice_ids, P.B, pb,
-                         (char*)ws, s, M.c64 ? 8 : 4);
+                         (char*)ws, s, 8);
     R.end();
   }
   if (amax)
@@ -723,15 +742,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     bld.fill_gemm(S);
     double bscale = P.nodes[S.c].variant ? (double)P.B : 1.0;
     S.cost_one = S.cost / bscale;
-    const double eb = P.skind == KIND_C64 ? 8.0 : 4.0;
-    double bytes = ((double)P.nodes[S.a].elems / (P.nodes[S.a].variant ? P.B : 1) +
-                    (double)P.nodes[S.b].elems / (P.nodes[S.b].variant ? P.B : 1) +
-                    (double)P.nodes[S.c].elems / (P.nodes[S.c].variant ? P.B : 1)) *
-                   eb;
     P.useful_flops_per_slice += 8.0 * S.cost_one;
-    P.algo_bytes_per_slice += bytes;
-    P.peak_intermediate_bytes =
-        std::max(P.peak_intermediate_bytes, (double)P.nodes[S.c].elems / (P.nodes[S.c].variant ? P.B : 1) * eb);
     if (S.post_perm) S.perm = bld.bit_perm(S.lc_nat, P.nodes[S.c].layout);
     // tensor cores: the larger K-contiguous operand is A (used as stored), the
     // other is expanded to its real 2x2 form
@@ -746,9 +757,20 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
           S.tc_swap = P.nodes[S.b].elems > P.nodes[S.a].elems;
         else
           S.tc_swap = b_ok;
+        // the operand read as stored must be an intermediate (leaves stay complex64)
+        const int an = S.tc_swap ? S.b : S.a;
+        if (P.nodes[an].leaf) S.tc = false;
+        S.hilo = S.tc && (P.flags & TN_FLAG_HILO);
       }
     }
   }
+  // storage: tensor-core A operands in 16 bits (hi + lo when split), all else complex64
+  for (auto& S : P.steps)
+    if (S.tc) {
+      Node& A = P.nodes[S.tc_swap ? S.b : S.a];
+      A.kind = P.skind;
+      A.hilo = S.hilo;
+    }
   // leaf storage layouts (variant leaves: sliced edges outermost, then the batch copy's order)
   std::vector<std::vector<int>> leaf_src_layout(P.n_leaves);
   for (int i = 0; i < P.n_leaves; ++i) {
@@ -761,6 +783,13 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     } else {
       leaf_src_layout[i] = N.layout;
     }
+  }
+  // algorithmic bytes of one sub-network: operands and result once each, at their storage size
+  for (auto& S : P.steps) {
+    const bool c64 = P.skind == KIND_C64;
+    auto per = [&](int x) { return (double)node_bytes(P, x, c64) / (P.nodes[x].variant ? P.B : 1); };
+    P.algo_bytes_per_slice += per(S.a) + per(S.b) + per(S.c);
+    P.peak_intermediate_bytes = std::max(P.peak_intermediate_bytes, per(S.c));
   }
   P.mem = plan_memory(P, P.skind == KIND_C64, leaf_src_layout);
   if (opt->mem_cap_bytes > 0)
@@ -865,7 +894,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
         TN_CHECK(std::isfinite(a), TN_ERR_NUMERIC, "calibration found a non-finite value");
         int e = 0;
         if (a > 0) std::frexp(a, &e);
-        P.nodes[x].exp2 = ((int)x == P.root) ? 0 : e;
+        P.nodes[x].exp2 = P.nodes[x].kind == KIND_C64 ? 0 : e;
       }
     } catch (...) {
       cudaStreamSynchronize(stream);
@@ -876,7 +905,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     cleanup();
   }
   TN_CUDA(cudaMalloc(&P.d_plan, std::max<int64_t>(P.mem.plan_bytes, 256)));
-  upload_leaves(P.mem, (char*)P.d_plan, P.skind);
+  upload_leaves(P.mem, (char*)P.d_plan, KIND_C64);
   upload_gather(P.mem, &P.d_gather);
   run_hoisted(P.mem, (char*)P.d_plan, nullptr);
   TN_CUDA(cudaStreamSynchronize(stream));

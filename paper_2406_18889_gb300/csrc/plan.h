@@ -22,6 +22,8 @@ struct Node {
   int leaf_id = -1;
   int consumer = -1;        // step consuming this node; -1 for the root
   int exp2 = 0;             // stored value = true value * 2^-exp2 (reduced precision)
+  int kind = 2;             // storage: KIND_C64, or KIND_F16 / KIND_BF16 (tensor-core operands)
+  bool hilo = false;        // 16-bit value followed by its 16-bit rounding residual
 };
 
 struct Step {
@@ -35,6 +37,7 @@ struct Step {
   BitPermute perm{};                   // lc_nat -> node c layout
   bool tc = false;                     // tensor-core GEMM in reduced precision
   bool tc_swap = false;                // tensor-core A operand is node b (else node a)
+  bool hilo = false;                   // split-precision product (A, B as hi + lo)
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network
 };

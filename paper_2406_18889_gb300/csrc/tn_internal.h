@@ -43,6 +43,7 @@ struct GemmParams {
   const void* A;
   const void* B;
   void* C;
+  void* C2;  // low part of a hi+lo output (reduced precision), else unused
 };
 
 // out[pi(x)] = in[x] for a tensor of 2^nbits elements; out_bit[i] is the
@@ -82,6 +83,8 @@ struct TcGemmParams {
   int64_t sc_bt, sc_m, sc_n;  // output strides (complex elements)
   void* C;
   int out_kind;               // 0 = fp16 complex, 1 = bf16 complex, 2 = fp32 complex
+  int out_hilo;               // 16-bit output also writes its rounding residual to C2
+  void* C2;
   float scale;                // power of two applied to the FP32 accumulators
   int* err;                   // device flag raised when a bounded wait times out
   int bn;                     // real-column tile (32, 64, 128 or 256)
@@ -101,7 +104,8 @@ void launch_accumulate_c64(const void* root, int64_t sb, int64_t sg, int64_t sj,
 void launch_bit_permute(const void* in, void* out, const BitPermute& bp, int elem_bytes, cudaStream_t s);
 void launch_strided_copy_c128(const void* in, void* out, const StridedCopy& sc, int64_t n_out, int out_kind,
                               double scale, cudaStream_t s);
-void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s);
+void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s,
+                      bool out_hilo = false);
 void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
 struct TopkParams {
@@ -115,10 +119,14 @@ void launch_topk(const double2* amps, const TopkParams& tp, const int64_t* block
 void launch_xeb(const double* q, int64_t n, int n_qubits, double* d_out, cudaStream_t s);
 bool tc_gemm_supported(int64_t nbt, int64_t M, int64_t N, int64_t K, int64_t sa_bt, int64_t sa_m, int64_t sa_k);
 int tc_gemm_bn(int64_t N);
-void launch_gemm_tc(const void* A, int64_t sa_bt, int64_t sa_m, const void* Bx, const TcGemmParams& p, bool bf16,
-                    cudaStream_t s);
+// A/A_lo: 16-bit complex [bt][M][K] (k contiguous); Bx/Bx_lo: expanded operand.
+// With A_lo and Bx_lo non-null the product is A*B + A*B_lo + A_lo*B (hi+lo split).
+void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m, const void* Bx,
+                    const void* Bx_lo, const TcGemmParams& p, bool bf16, cudaStream_t s);
+// expand a complex operand stored as fp32 (in_c64) or 16-bit complex into its real 2x2
+// form; with Bx_lo non-null also the rounding residual of every entry
 void launch_expand_b(const void* B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt, int64_t N, int64_t K,
-                     bool bf16, void* Bx, cudaStream_t s);
+                     bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr);
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K);
 double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
                         int* d_err);
