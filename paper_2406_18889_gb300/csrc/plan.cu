@@ -350,14 +350,13 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
   M.in_plan.assign(nn, 0);
   M.tmp_off.assign(P.steps.size(), -1);
   M.bx_off.assign(P.steps.size(), -1);
-  const int eb = c64 ? 8 : 4;
   int64_t poff = 0;
   std::vector<int64_t> src_off(P.n_leaves, -1);
   for (int i = 0; i < P.n_leaves; ++i) {
     int64_t el = 1;
     for (int e : leaf_src_layout[i]) el *= P.dim[e];
     src_off[i] = poff;
-    poff += round_up(el * eb, 256);
+    poff += round_up(el * 8, 256);  // leaves are always complex64
     if (!P.nodes[i].variant) {
       M.off[i] = src_off[i];
       M.in_plan[i] = 1;
