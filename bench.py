@@ -190,6 +190,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ roofline
+KIND_NAMES = {0: "gemm_cuda_core", 1: "bit_permute", 2: "gather", 3: "accumulate_fp64",
+              4: "expand_operand", 5: "gemm_tensor_core"}
+
+
+def roofline_from_profile(prof) -> tuple:
+    """Roofline of the kernel class with the largest share of one profiled step:
+    achieved = algorithmic FLOPs (or bytes) of its launches / their summed event time."""
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    src = "of measured" if peaks else "of fallback"
+    kinds, ms, flops, nbytes = prof["kind"], prof["ms"], prof["flops"], prof["bytes"]
+    per_kind = {}
+    for k in np.unique(kinds):
+        sel = kinds == k
+        t = float(ms[sel].sum())
+        entry = {"launches": int(sel.sum()), "ms": t}
+        if k in (0, 5):
+            entry["tflops"] = float(flops[sel].sum() / (t / 1e3) / 1e12) if t > 0 else None
+        entry["gbs"] = float(nbytes[sel].sum() / (t / 1e3) / 1e9) if t > 0 else None
+        per_kind[KIND_NAMES[int(k)]] = entry
+    dom = max(per_kind, key=lambda n: per_kind[n]["ms"])
+    e = per_kind[dom]
+    if dom == "gemm_tensor_core":
+        r = {"bound": "tensor", "achieved": e["tflops"], "peak": tc_peak, "unit": "TFLOP/s",
+             "peak_source": f"bf16_tflops burst {src} (fp16 dense rate is the same)"}
+    elif dom == "gemm_cuda_core":
+        p = fp32_alu_peak_tflops()
+        r = {"bound": "alu", "achieved": e["tflops"], "peak": p, "unit": "TFLOP/s",
+             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        r = {"bound": "hbm", "achieved": e["gbs"], "peak": hbm, "unit": "GB/s",
+             "peak_source": f"hbm_gbs {src}"}
+    r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
+    r["traffic"] = None
+    r["kernel"] = f"{dom} (all {e['launches']} launches of one step)"
+    r["per_kind"] = per_kind
+    return r, per_kind
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -203,7 +244,8 @@ def run_ours(args):
 
     w = rank_workload(rank)
     prep = E.prepare(w)
-    plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch)
+    plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch,
+                  flags=B.TN_FLAG_HILO if args.hilo else 0)
     S = plan.n_slices_total
     ids = np.arange(S, dtype=np.int64)
     base_np = w.block_base()
@@ -288,19 +330,22 @@ def run_ours(args):
     # per-kernel roofline: one profiled pass (events around every launch)
     prof = B.tn_contract_slices_profile(plan.handle, ids, amps.data_ptr(), 0, plan.workspace.data_ptr(),
                                         plan.workspace.numel(), stream.cuda_stream)
-    kinds = prof["kind"]
-    names = {0: "gemm_c64", 1: "bit_permute", 2: "gather", 3: "accumulate_fp64"}
-    per_kind = {names[k]: {"launches": int((kinds == k).sum()), "ms": float(prof["ms"][kinds == k].sum())}
-                for k in np.unique(kinds)}
-    g = kinds == 0
-    gemm_tflops = float(prof["flops"][g].sum() / (prof["ms"][g].sum() / 1e3) / 1e12)
-    peak = fp32_alu_peak_tflops()
+    roofline, per_kind = roofline_from_profile(prof)
     launches_per_step = prof["n_launches"] + 2  # + top-k + XEB
-    roofline = {"bound": "alu", "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": gemm_tflops / peak, "traffic": None,
-                "kernel": "gemm_c64 (all launches of one step)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "per_kind": per_kind}
+    c64_value = None
+    if args.prec != "c64" and not args.no_c64:
+        plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch)
+        for _ in range(3):
+            plan64.contract(ids, out=amps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            plan64.contract(ids, out=amps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c64_value = sum_over_ranks(5.0 * S, dist, "cuda") / (max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / 1e3)
+        plan64.close()
     if rank != 0:
         return
     cpu = None
@@ -312,12 +357,17 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "complex64" if args.prec == "c64" else args.prec,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "complex64" if args.prec == "c64" else
+                 f"{args.prec} tensor-core operands, fp32 accumulate, complex64 elsewhere",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec,
+        "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"{world} independent block sets (one per GPU)"},
         "useful_tflops": value * useful_per_slice / 1e12,
+        "complex64_path": None if c64_value is None else {
+            "value": c64_value, "unit": "slices/s", "speedup": value / c64_value,
+            "note": "same workload and batch through the complex64 CUDA-core path (contraction only)"},
         "useful_flops_per_slice": useful_per_slice,
         "wall_s": wall,
         "roofline": roofline,
@@ -337,7 +387,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="c64", choices=["c64", "bf16", "fp16"])
+    ap.add_argument("--prec", default="fp16", choices=["c64", "bf16", "fp16"])
+    ap.add_argument("--hilo", action="store_true", help="split-precision (hi + lo) tensor-core steps")
+    ap.add_argument("--no-c64", action="store_true", help="skip timing the complex64 path alongside")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",

@@ -234,8 +234,9 @@ tn_status tn_xeb(const double* q, int64_t n_sel, int32_t n_qubits, double* out_x
 /*
  * Profiling form of tn_contract_slices: the same work launched directly (no
  * graph) with a CUDA event pair around every kernel; synchronises `stream`
- * and reports, per kernel launch in launch order, its class (0 = GEMM,
- * 1 = transpose, 2 = slice gather, 3 = FP64 accumulate), its duration in
+ * and reports, per kernel launch in launch order, its class (0 = CUDA-core
+ * GEMM, 1 = transpose, 2 = slice gather, 3 = FP64 accumulate, 4 = operand
+ * expansion for the tensor cores, 5 = tensor-core GEMM), its duration in
  * milliseconds, and its algorithmic FLOPs (8 * batch*M*N*K for a GEMM, else 0)
  * and bytes (operands + result for a GEMM; bytes read + written otherwise).
  * Arrays hold max_records entries; *n_records is set to the number of
