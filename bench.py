@@ -244,8 +244,8 @@ def run_ours(args):
 
     w = rank_workload(rank)
     prep = E.prepare(w)
-    plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch,
-                  flags=B.TN_FLAG_HILO if args.hilo else 0)
+    flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
+    plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
     S = plan.n_slices_total
     ids = np.arange(S, dtype=np.int64)
     base_np = w.block_base()
@@ -334,7 +334,8 @@ def run_ours(args):
     launches_per_step = prof["n_launches"] + 2  # + top-k + XEB
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
-        plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch)
+        plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch,
+                        flags=0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
         for _ in range(3):
             plan64.contract(ids, out=amps)
         torch.cuda.synchronize()
@@ -362,6 +363,7 @@ def run_ours(args):
                  f"{args.prec} tensor-core operands, fp32 accumulate, complex64 elsewhere",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
+                   "hoist_invariant": not args.no_hoist,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"{world} independent block sets (one per GPU)"},
         "useful_tflops": value * useful_per_slice / 1e12,
@@ -390,6 +392,8 @@ def main(argv=None):
     ap.add_argument("--prec", default="fp16", choices=["c64", "bf16", "fp16"])
     ap.add_argument("--hilo", action="store_true", help="split-precision (hi + lo) tensor-core steps")
     ap.add_argument("--no-c64", action="store_true", help="skip timing the complex64 path alongside")
+    ap.add_argument("--no-hoist", action="store_true",
+                    help="recompute slice-independent subtrees in every batch instead of once per plan")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",

@@ -1,19 +1,21 @@
-// Complex strided batched GEMM on CUDA cores: the plain complex64 path, and
-// the small steps of the reduced-precision path (fp16/bf16 complex storage,
-// FP32 arithmetic).
+// Complex strided-gather GEMM on CUDA cores: the plain complex64 path, and
+// the small steps of the reduced-precision path (FP32 arithmetic; complex64
+// operands; complex64 or 16-bit complex results).
 //
 // One pairwise contraction of the tree (arXiv 2406.18889, Sec. III: the
 // per-step tensor contraction the paper runs through cuTensor or
 // transpose-transpose-GEMM-transpose) is C[bt][m][n] = sum_k A[bt][m][k] *
-// B[bt][k][n] once the plan has put each operand's batch, free and contracted
-// indices into contiguous blocks.  Each complex multiply-add is four FP32
-// fused multiply-adds.
+// B[bt][k][n].  Each index group of each tensor is addressed through its runs
+// (tn_internal.h), so operands are read and results written in whatever
+// layout the plan chose -- no separate transpose pass.  Each complex
+// multiply-add is four FP32 fused multiply-adds.
 //
 // Two kernels:
-//  * tiled: a CTA of 256 threads computes a TM x TN tile, staging TK-deep
-//    slices of A and B through shared memory (loads coalesced along whichever
-//    of the operand's two indices is contiguous); each thread keeps RM x RN
-//    complex accumulators.
+//  * tiled: a CTA of 256 threads computes a TM x TN tile; per CTA the row and
+//    column offsets of the tile are tabulated in shared memory once (and the k
+//    offsets once per TK-deep slice); operands are staged through shared
+//    memory with loads coalesced along whichever index is contiguous; each
+//    thread keeps RM x RN complex accumulators.
 //  * direct: one thread per output element, for shapes too small for a tile.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -61,32 +63,47 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
+// flags: bit 0 = A loads run along k (A's k is contiguous), bit 1 = B loads run along n
 template <int TM, int TN, int TK, int TY, int TX, class In, class Out>
-__global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, bool hilo) {
+__global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, bool hilo, int flags) {
   static_assert(TY * TX == 256, "256 threads");
   constexpr int RM = TM / TY, RN = TN / TX;
-  __shared__ float2 As[TK][TM + 1];
-  __shared__ float2 Bs[TK][TN + 1];
   using TI = typename In::T;
   using TO = typename Out::T;
+  __shared__ float2 As[TK][TM + 1];
+  __shared__ float2 Bs[TK][TN + 1];
+  __shared__ int64_t a_row[TM], b_col[TN], c_row[TM], c_col[TN];
+  __shared__ int64_t a_kof[TK], b_kof[TK];
   const TI* __restrict__ A = (const TI*)p.A;
   const TI* __restrict__ Bm = (const TI*)p.B;
   TO* __restrict__ C = (TO*)p.C;
+  TO* __restrict__ C2 = (TO*)p.C2;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TN;
-  const bool a_kc = p.sa_k == 1;  // A contiguous along k
-  const bool b_nc = p.sb_n == 1;  // B contiguous along n
+  const bool a_kc = flags & 1;
+  const bool b_nc = flags & 2;
+  for (int i = tid; i < TM; i += 256) {
+    a_row[i] = m0 + i < p.M ? run_offset(p.a_m, m0 + i) : 0;
+    c_row[i] = m0 + i < p.M ? run_offset(p.c_m, m0 + i) : 0;
+  }
+  for (int i = tid; i < TN; i += 256) {
+    b_col[i] = n0 + i < p.N ? run_offset(p.b_n, n0 + i) : 0;
+    c_col[i] = n0 + i < p.N ? run_offset(p.c_n, n0 + i) : 0;
+  }
   for (int64_t bt = blockIdx.z; bt < p.nbt; bt += gridDim.z) {
-    const TI* Ab = A + bt * p.sa_bt;
-    const TI* Bb = Bm + bt * p.sb_bt;
+    const TI* Ab = A + run_offset(p.a_bt, bt);
+    const TI* Bb = Bm + run_offset(p.b_bt, bt);
     float2 acc[RM][RN];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
       for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
     for (int64_t k0 = 0; k0 < p.K; k0 += TK) {
-      // stage A[m0 : m0+TM][k0 : k0+TK]
+      __syncthreads();  // previous slice consumed; offset tables written
+      if (tid < TK) a_kof[tid] = k0 + tid < p.K ? run_offset(p.a_k, k0 + tid) : 0;
+      if (tid >= 32 && tid < 32 + TK) b_kof[tid - 32] = k0 + tid - 32 < p.K ? run_offset(p.b_k, k0 + tid - 32) : 0;
+      __syncthreads();
 #pragma unroll
       for (int l = tid; l < TM * TK; l += 256) {
         int mm, kk;
@@ -97,12 +114,10 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
           kk = l / TM;
           mm = l % TM;
         }
-        int64_t gm = m0 + mm, gk = k0 + kk;
         float2 v = make_float2(0.f, 0.f);
-        if (gm < p.M && gk < p.K) v = In::ld(Ab[gm * p.sa_m + gk * p.sa_k]);
+        if (m0 + mm < p.M && k0 + kk < p.K) v = In::ld(Ab[a_row[mm] + a_kof[kk]]);
         As[kk][mm] = v;
       }
-      // stage B[k0 : k0+TK][n0 : n0+TN]
 #pragma unroll
       for (int l = tid; l < TN * TK; l += 256) {
         int nn, kk;
@@ -113,9 +128,8 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
           nn = l / TK;
           kk = l % TK;
         }
-        int64_t gn = n0 + nn, gk = k0 + kk;
         float2 v = make_float2(0.f, 0.f);
-        if (gn < p.N && gk < p.K) v = In::ld(Bb[gk * p.sb_k + gn * p.sb_n]);
+        if (n0 + nn < p.N && k0 + kk < p.K) v = In::ld(Bb[b_kof[kk] + b_col[nn]]);
         Bs[kk][nn] = v;
       }
       __syncthreads();
@@ -131,19 +145,18 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
 #pragma unroll
           for (int j = 0; j < RN; ++j) cmac(acc[i][j], a[i], b[j]);
       }
-      __syncthreads();
     }
-    TO* Cb = C + bt * p.sc_bt;
+    const int64_t cb = run_offset(p.c_bt, bt);
 #pragma unroll
     for (int i = 0; i < RM; ++i) {
-      int64_t gm = m0 + ty + i * TY;
-      if (gm >= p.M) continue;
+      const int mm = ty + i * TY;
+      if (m0 + mm >= p.M) continue;
 #pragma unroll
       for (int j = 0; j < RN; ++j) {
-        int64_t gn = n0 + tx + j * TX;
-        if (gn < p.N)
-          store_out<Out>(Cb, (TO*)p.C2 + bt * p.sc_bt, gm * p.sc_m + gn * p.sc_n,
-                         make_float2(acc[i][j].x * scale, acc[i][j].y * scale), hilo);
+        const int nn = tx + j * TX;
+        if (n0 + nn < p.N)
+          store_out<Out>(C, C2, cb + c_row[mm] + c_col[nn], make_float2(acc[i][j].x * scale, acc[i][j].y * scale),
+                         hilo);
       }
     }
   }
@@ -160,25 +173,29 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
   const int64_t total = p.nbt * p.M * p.N;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x) {
-    int64_t n = x % p.N;
-    int64_t t = x / p.N;
-    int64_t m = t % p.M;
-    int64_t bt = t / p.M;
-    const TI* a = A + bt * p.sa_bt + m * p.sa_m;
-    const TI* b = Bm + bt * p.sb_bt + n * p.sb_n;
+    const int64_t n = x % p.N;
+    const int64_t t = x / p.N;
+    const int64_t m = t % p.M;
+    const int64_t bt = t / p.M;
+    const TI* a = A + run_offset(p.a_bt, bt) + run_offset(p.a_m, m);
+    const TI* b = Bm + run_offset(p.b_bt, bt) + run_offset(p.b_n, n);
     float2 acc = make_float2(0.f, 0.f);
-    for (int64_t k = 0; k < p.K; ++k) cmac(acc, In::ld(a[k * p.sa_k]), In::ld(b[k * p.sb_k]));
-    store_out<Out>(C, (TO*)p.C2, bt * p.sc_bt + m * p.sc_m + n * p.sc_n,
+    for (int64_t k = 0; k < p.K; ++k) cmac(acc, In::ld(a[run_offset(p.a_k, k)]), In::ld(b[run_offset(p.b_k, k)]));
+    store_out<Out>(C, (TO*)p.C2, run_offset(p.c_bt, bt) + run_offset(p.c_m, m) + run_offset(p.c_n, n),
                    make_float2(acc.x * scale, acc.y * scale), hilo);
   }
 }
+
+bool fastest_unit(const Runs& r) { return r.n > 0 && r.st[0] == 1; }
 
 template <int TM, int TN, int TK, int TY, int TX, class In, class Out>
 void launch_tiled(const GemmParams& p, float scale, bool hilo, cudaStream_t s) {
   int64_t gx = (p.N + TN - 1) / TN, gy = (p.M + TM - 1) / TM;
   TN_CHECK(gx < (1LL << 31) && gy < 65536, TN_ERR_UNSUPPORTED, "GEMM grid too large");
   unsigned gz = (unsigned)std::min<int64_t>(p.nbt, 65535);
-  gemm_tiled<TM, TN, TK, TY, TX, In, Out><<<dim3((unsigned)gx, (unsigned)gy, gz), 256, 0, s>>>(p, scale, hilo);
+  const int flags = (fastest_unit(p.a_k) || !fastest_unit(p.a_m) ? 1 : 0) | (fastest_unit(p.b_n) ? 2 : 0);
+  gemm_tiled<TM, TN, TK, TY, TX, In, Out><<<dim3((unsigned)gx, (unsigned)gy, gz), 256, 0, s>>>(p, scale, hilo,
+                                                                                             flags);
 }
 
 template <class In, class Out>
@@ -214,11 +231,16 @@ void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scal
   if (in_kind == 2 && out_kind == 2) return launch_typed<C64, C64>(p, scale, s);
   if (in_kind == 2 && out_kind == 0) return launch_typed<C64, F16>(p, scale, s, out_hilo);
   if (in_kind == 2 && out_kind == 1) return launch_typed<C64, BF16>(p, scale, s, out_hilo);
-  if (in_kind == 0 && out_kind == 0) return launch_typed<F16, F16>(p, scale, s, out_hilo);
-  if (in_kind == 0 && out_kind == 2) return launch_typed<F16, C64>(p, scale, s);
-  if (in_kind == 1 && out_kind == 1) return launch_typed<BF16, BF16>(p, scale, s, out_hilo);
-  if (in_kind == 1 && out_kind == 2) return launch_typed<BF16, C64>(p, scale, s);
   fail(TN_ERR_UNSUPPORTED, "GEMM storage combination");
+}
+
+// one run covering any extent (the digit mask is wider than every index)
+Runs single_run(int64_t extent, int64_t stride) {
+  Runs r{};
+  r.n = extent > 1 ? 1 : 0;
+  r.lg[0] = 62;
+  r.st[0] = stride;
+  return r;
 }
 
 }  // namespace tn

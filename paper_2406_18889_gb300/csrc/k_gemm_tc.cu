@@ -105,7 +105,7 @@ __host__ __device__ constexpr uint32_t make_idesc(int n, bool bf16) {
 
 template <int BN>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM + BN) * BK * 2 + 256;
+  return 1024 + (size_t)STAGES * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8;
 }
 
 // HILO: three accumulating passes over K -- (A, B), (A, B_lo), (A_lo, B) -- the
@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int64_t* n_off = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 256);  // [BN / 2]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tile = blockIdx.x, m_tile = blockIdx.y;
@@ -202,11 +203,16 @@ __global__ void __launch_bounds__(192, 1)
                    : "memory");
     }
   } else {
-    // epilogue warps 2..5
+    // epilogue warps 2..5: output offsets of this tile's columns, then rows
+    const int et = threadIdx.x - 64;  // 0..127
+    const int64_t nbase = (int64_t)n_tile * BN / 2;
+    for (int j = et; j < BN / 2; j += 128) n_off[j] = nbase + j < p.N ? run_offset(p.c_n, nbase + j) : 0;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
     const bool ok = wait_bounded(done, 0, p.err);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int quarter = warp & 3;
     const int64_t m = (int64_t)m_tile * BM + quarter * 32 + lane;
+    const int64_t base = m < p.M ? run_offset(p.c_bt, bt) + run_offset(p.c_m, m) : 0;
     if (ok) {
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -225,15 +231,13 @@ __global__ void __launch_bounds__(192, 1)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (m < p.M) {
-          const int64_t n0 = ((int64_t)n_tile * BN + c0) / 2;
-          const int64_t base = (int64_t)bt * p.sc_bt + m * p.sc_m;
+          const int j0 = c0 / 2;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int64_t n = n0 + j;
-            if (n >= p.N) break;
+            if (nbase + j0 + j >= p.N) break;
             const float re = __uint_as_float(v[2 * j]) * p.scale;
             const float im = __uint_as_float(v[2 * j + 1]) * p.scale;
-            const int64_t o = base + n * p.sc_n;
+            const int64_t o = base + n_off[j0 + j];
             if (p.out_kind == 2) {
               reinterpret_cast<float2*>(p.C)[o] = make_float2(re, im);
             } else if (p.out_kind == 1) {
@@ -392,9 +396,8 @@ __device__ __forceinline__ __nv_bfloat16 neg16(__nv_bfloat16 x) {
 // columns past 2K up to the pitch are zero.  With Bx_lo, every entry's
 // rounding residual (exact value - 16-bit value) goes to Bx_lo.
 template <class T2, class T, class TIN>
-__global__ void expand_b_kernel(const TIN* __restrict__ B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt,
-                                int64_t N, int64_t K, int64_t half_pitch, T2* __restrict__ Bx,
-                                T2* __restrict__ Bx_lo) {
+__global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, Runs b_n, int64_t nbt, int64_t N,
+                                int64_t K, int64_t half_pitch, T2* __restrict__ Bx, T2* __restrict__ Bx_lo) {
   const int64_t total = nbt * N * half_pitch;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = x % half_pitch;
@@ -402,7 +405,7 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, int64_t sb_bt, int64_
     const int64_t n = t % N, bt = t / N;
     float re = 0.f, im = 0.f;
     if (k < K) {
-      const TIN v = B[bt * sb_bt + k * sb_k + n * sb_n];
+      const TIN v = B[run_offset(b_bt, bt) + run_offset(b_k, k) + run_offset(b_n, n)];
       re = (float)v.x;
       im = (float)v.y;
     }
@@ -429,8 +432,8 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, int64_t sb_bt, int64_
 }
 }  // namespace
 
-void launch_expand_b(const void* B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt, int64_t N, int64_t K,
-                     bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo) {
+void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
+                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo) {
   const int64_t half_pitch = (2 * K + BK - 1) / BK * BK / 2;
   const int64_t total = nbt * N * half_pitch;
   if (total <= 0) return;
@@ -438,18 +441,18 @@ void launch_expand_b(const void* B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, i
   if (bf16) {
     if (in_c64)
       expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2><<<blocks, 256, 0, s>>>(
-          (const float2*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo);
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo);
     else
       expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162><<<blocks, 256, 0, s>>>(
-          (const __nv_bfloat162*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
+          (const __nv_bfloat162*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
           (__nv_bfloat162*)Bx_lo);
   } else {
     if (in_c64)
       expand_b_kernel<__half2, __half, float2><<<blocks, 256, 0, s>>>(
-          (const float2*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
     else
       expand_b_kernel<__half2, __half, __half2><<<blocks, 256, 0, s>>>(
-          (const __half2*)B, sb_bt, sb_k, sb_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
+          (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
   }
 }
 
@@ -535,15 +538,15 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
       fill_kernel<__half2><<<1024, 256, 0, s>>>((__half2*)B, nbt * K * N, seed + 1);
     }
     // B stored [bt][k][n] (n contiguous): the expansion reads it strided
-    launch_expand_b(B, K * N, N, 1, nbt, N, K, bf16, Bx, s);
+    launch_expand_b(B, single_run(nbt, K * N), single_run(K, N), single_run(N, 1), nbt, N, K, bf16, Bx, s);
     TcGemmParams p{};
     p.nbt = nbt;
     p.M = M;
     p.N = N;
     p.K = K;
-    p.sc_bt = M * N;
-    p.sc_m = N;
-    p.sc_n = 1;
+    p.c_bt = single_run(nbt, M * N);
+    p.c_m = single_run(M, N);
+    p.c_n = single_run(N, 1);
     p.C = C;
     p.out_kind = 2;
     p.scale = 1.0f;

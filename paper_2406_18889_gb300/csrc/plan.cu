@@ -135,64 +135,15 @@ struct Builder {
     }
     return s;
   }
-  // stride of a contiguous block = stride of its fastest edge (0 if empty)
-  int64_t block_stride(const std::vector<int>& block, const std::map<int, int64_t>& st) const {
-    if (block.empty()) return 0;
-    return st.at(block.back());
-  }
   int producer(int node) const { return P.nodes[node].leaf ? -1 : node - P.n_leaves; }
 
-  // cost (elements moved) for node x to be stored in layout L
-  double placement_cost(int x, const std::vector<int>& L) const {
-    int q = producer(x);
-    if (q < 0) return 0.0;
-    const Step& Q = P.steps[q];
-    if (decomposes(L, {&Q.bt, &Q.m, &Q.n})) return 0.0;
-    return 2.0 * (double)P.nodes[x].elems;
-  }
-  // small preference terms: the operand's innermost block should be long
-  // (coalesced loads) and preferably the contracted block
-  double inner_penalty(const std::vector<std::vector<int>>& blocks, const std::vector<int>& kblock,
-                       double elems, bool larger) const {
-    const std::vector<int>* inner = nullptr;
-    for (auto it = blocks.rbegin(); it != blocks.rend(); ++it)
-      if (dims_prod(*it) > 1) {
-        inner = &*it;
-        break;
-      }
-    if (!inner) return 0.0;
-    double sz = (double)dims_prod(*inner);
-    double pen = 0.0;
-    if (sz < 16) pen += elems * 0.25 * (16.0 - sz) / 16.0;
-    if (inner->empty() || kblock.empty() || inner->front() != kblock.front())
-      pen += elems * ((larger && P.skind != KIND_C64) ? 1.0 : 0.01);
-    return pen;
-  }
-
-  std::vector<std::vector<int>> k_candidates(const Step& S) const {
-    std::vector<std::vector<int>> out;
-    out.push_back(S.k);  // ascending edge ids
-    for (int operand = 0; operand < 2; ++operand) {
-      int q = producer(operand == 0 ? S.a : S.b);
-      if (q < 0) continue;
-      const Step& Q = P.steps[q];
-      std::array<const std::vector<int>*, 3> gs = {&Q.bt, &Q.m, &Q.n};
-      std::array<int, 3> perm = {0, 1, 2};
-      do {
-        std::vector<int> kk;
-        for (int gi : perm)
-          for (int e : *gs[gi])
-            if (contains(S.k, e)) kk.push_back(e);
-        if (kk.size() == S.k.size()) out.push_back(kk);
-      } while (std::next_permutation(perm.begin(), perm.end()));
-    }
-    std::sort(out.begin(), out.end());
-    out.erase(std::unique(out.begin(), out.end()), out.end());
-    return out;
-  }
-
+  // Root-down (the paper's greedy dimension ordering from the root): the
+  // larger operand is stored [batch][free][contracted] (contracted fastest,
+  // the form the tensor cores read), the smaller [batch][contracted][free];
+  // batch and free indices keep the result's order; the contracted order
+  // groups the larger operand's producer's index groups so that producer
+  // writes long contiguous runs.
   void assign_layouts() {
-    // root: [slice batch][block][open edges]
     Node& R = P.nodes[P.root];
     std::vector<int> rl;
     if (R.variant) rl.push_back(P.batch_edge);
@@ -202,94 +153,80 @@ struct Builder {
     for (int t = (int)P.steps.size() - 1; t >= 0; --t) {
       Step& S = P.steps[t];
       const std::vector<int>& Lc = P.nodes[S.c].layout;
-      if (decomposes(Lc, {&S.bt, &S.m, &S.n})) {
-        S.lc_nat = Lc;
-        S.post_perm = false;
-      } else {
-        std::vector<int> nat;
-        for (auto* g : {&S.bt, &S.m, &S.n})
-          for (int e : order_by(*g, Lc)) nat.push_back(e);
-        S.lc_nat = nat;
-        S.post_perm = true;
+      S.lc_nat = Lc;
+      S.post_perm = false;
+      std::vector<int> bt_o = order_by(S.bt, Lc), m_o = order_by(S.m, Lc), n_o = order_by(S.n, Lc);
+      const bool a_big = P.nodes[S.a].elems >= P.nodes[S.b].elems;
+      std::vector<int> k_o = S.k;
+      const int q = producer(a_big ? S.a : S.b);
+      if (q >= 0) {
+        const Step& Q = P.steps[q];
+        std::vector<int> kk;
+        for (auto* g : {&Q.bt, &Q.m, &Q.n})
+          for (int e : *g)
+            if (contains(S.k, e)) kk.push_back(e);
+        if (kk.size() == S.k.size()) k_o = kk;
       }
-      std::vector<int> bt_o = order_by(S.bt, S.lc_nat);
-      std::vector<int> m_o = order_by(S.m, S.lc_nat);
-      std::vector<int> n_o = order_by(S.n, S.lc_nat);
-      double ea = (double)P.nodes[S.a].elems, eb = (double)P.nodes[S.b].elems;
-      double best = 1e300;
-      std::vector<int> best_a, best_b;
-      for (const auto& k_o : k_candidates(S)) {
-        // operand A blocks {bt, m, k}; operand B blocks {bt, k, n}
-        std::array<const std::vector<int>*, 3> A3 = {&bt_o, &m_o, &k_o};
-        std::array<const std::vector<int>*, 3> B3 = {&bt_o, &n_o, &k_o};
-        std::array<int, 3> pa = {0, 1, 2};
-        do {
-          std::vector<int> la;
-          std::vector<std::vector<int>> ablocks;
-          for (int i : pa) {
-            ablocks.push_back(*A3[i]);
-            la.insert(la.end(), A3[i]->begin(), A3[i]->end());
-          }
-          double ca = placement_cost(S.a, la) + inner_penalty(ablocks, k_o, ea, ea >= eb);
-          if (ca >= best) continue;
-          std::array<int, 3> pb = {0, 1, 2};
-          do {
-            std::vector<int> lb;
-            std::vector<std::vector<int>> bblocks;
-            for (int i : pb) {
-              bblocks.push_back(*B3[i]);
-              lb.insert(lb.end(), B3[i]->begin(), B3[i]->end());
-            }
-            double cb = placement_cost(S.b, lb) + inner_penalty(bblocks, k_o, eb, eb > ea);
-            if (ca + cb < best) {
-              best = ca + cb;
-              best_a = la;
-              best_b = lb;
-            }
-          } while (std::next_permutation(pb.begin(), pb.end()));
-        } while (std::next_permutation(pa.begin(), pa.end()));
-      }
-      P.nodes[S.a].layout = best_a;
-      P.nodes[S.b].layout = best_b;
+      std::vector<int> big, small;
+      const std::vector<int>& fb = a_big ? m_o : n_o;
+      const std::vector<int>& fs = a_big ? n_o : m_o;
+      big.insert(big.end(), bt_o.begin(), bt_o.end());
+      big.insert(big.end(), fb.begin(), fb.end());
+      big.insert(big.end(), k_o.begin(), k_o.end());
+      small.insert(small.end(), bt_o.begin(), bt_o.end());
+      small.insert(small.end(), k_o.begin(), k_o.end());
+      small.insert(small.end(), fs.begin(), fs.end());
+      P.nodes[S.a].layout = a_big ? big : small;
+      P.nodes[S.b].layout = a_big ? small : big;
     }
   }
 
+  // runs of `group` (canonical order `order`, slowest first) inside `layout`
+  Runs runs_of(const std::vector<int>& order, const std::vector<int>& layout) const {
+    auto st = strides(layout);
+    Runs r{};
+    r.n = 0;
+    for (int i = (int)order.size() - 1; i >= 0; --i) {
+      const int e = order[i];
+      const int lg = ilog2(P.dim[e]);
+      if (lg == 0) continue;
+      const int64_t s = st.at(e);
+      if (r.n > 0 && s == r.st[r.n - 1] << r.lg[r.n - 1] && r.lg[r.n - 1] + lg <= 62) {
+        r.lg[r.n - 1] = (int8_t)(r.lg[r.n - 1] + lg);
+      } else {
+        TN_CHECK(r.n < kMaxRuns, TN_ERR_UNSUPPORTED, "an index group is split into too many runs");
+        r.lg[r.n] = (int8_t)lg;
+        r.st[r.n] = s;
+        ++r.n;
+      }
+    }
+    return r;
+  }
+
   void fill_gemm(Step& S) {
-    auto sa = strides(P.nodes[S.a].layout);
-    auto sb = strides(P.nodes[S.b].layout);
-    auto sc = strides(S.lc_nat);
-    std::vector<int> bt_o = order_by(S.bt, S.lc_nat);
-    std::vector<int> m_o = order_by(S.m, S.lc_nat);
-    std::vector<int> n_o = order_by(S.n, S.lc_nat);
-    std::vector<int> k_o = order_by(S.k, P.nodes[S.a].layout);
+    const auto& La = P.nodes[S.a].layout;
+    const auto& Lb = P.nodes[S.b].layout;
+    const auto& Lc = P.nodes[S.c].layout;
+    std::vector<int> bt_o = order_by(S.bt, Lc), m_o = order_by(S.m, Lc), n_o = order_by(S.n, Lc);
+    std::vector<int> k_o = order_by(S.k, P.nodes[S.a].elems >= P.nodes[S.b].elems ? La : Lb);
     GemmParams& g = S.gp;
     g.nbt = dims_prod(bt_o);
     g.M = dims_prod(m_o);
     g.N = dims_prod(n_o);
     g.K = dims_prod(k_o);
-    g.sa_bt = block_stride(order_by(S.bt, P.nodes[S.a].layout), sa);
-    g.sa_m = block_stride(order_by(S.m, P.nodes[S.a].layout), sa);
-    g.sa_k = block_stride(k_o, sa);
-    g.sb_bt = block_stride(order_by(S.bt, P.nodes[S.b].layout), sb);
-    g.sb_k = block_stride(order_by(S.k, P.nodes[S.b].layout), sb);
-    g.sb_n = block_stride(order_by(S.n, P.nodes[S.b].layout), sb);
-    g.sc_bt = block_stride(bt_o, sc);
-    g.sc_m = block_stride(m_o, sc);
-    g.sc_n = block_stride(n_o, sc);
-    // consistency: group orders agree across operands (guaranteed by construction)
-    TN_CHECK(order_by(S.bt, P.nodes[S.a].layout) == bt_o && order_by(S.bt, P.nodes[S.b].layout) == bt_o &&
-                 order_by(S.m, P.nodes[S.a].layout) == m_o && order_by(S.n, P.nodes[S.b].layout) == n_o &&
-                 order_by(S.k, P.nodes[S.b].layout) == k_o,
-             TN_ERR_INVALID_ARG, "internal: inconsistent operand layouts");
-    TN_CHECK(decomposes(P.nodes[S.a].layout, {&S.bt, &S.m, &S.k}) &&
-                 decomposes(P.nodes[S.b].layout, {&S.bt, &S.k, &S.n}) &&
-                 decomposes(S.lc_nat, {&S.bt, &S.m, &S.n}),
-             TN_ERR_INVALID_ARG, "internal: operand not blockwise");
+    g.a_bt = runs_of(bt_o, La);
+    g.a_m = runs_of(m_o, La);
+    g.a_k = runs_of(k_o, La);
+    g.b_bt = runs_of(bt_o, Lb);
+    g.b_k = runs_of(k_o, Lb);
+    g.b_n = runs_of(n_o, Lb);
+    g.c_bt = runs_of(bt_o, Lc);
+    g.c_m = runs_of(m_o, Lc);
+    g.c_n = runs_of(n_o, Lc);
     S.cost = (double)g.nbt * g.M * g.N * g.K;
   }
 
   BitPermute bit_perm(const std::vector<int>& from, const std::vector<int>& to) const {
-    // bit position of (edge, sub-bit) in a layout; bit 0 = fastest
     auto positions = [&](const std::vector<int>& L) {
       std::map<int, int> base;
       int acc = 0;
@@ -323,22 +260,56 @@ int64_t node_bytes(const Plan& P, int x, bool c64) {
 }
 int node_word(const Plan& P, int x, bool c64) { return (c64 || P.nodes[x].kind == KIND_C64) ? 8 : 4; }
 
-// tensor-core operand roles of a step: (A node, a strides) and (B node, b strides)
+// tensor-core operand roles of a step: A is read as stored ([bt][m][k], k
+// contiguous: single runs), B is expanded through its runs
 struct TcRoles {
   int a_node, b_node;
   int64_t M, N, K;
-  int64_t a_bt, a_m;               // A strides (k contiguous)
-  int64_t b_bt, b_k, b_n;          // B strides
-  int64_t c_bt, c_m, c_n;          // output strides
+  int64_t a_bt, a_m;               // A strides (complex elements)
+  Runs b_bt, b_k, b_n;             // B index maps
+  Runs c_bt, c_m, c_n;             // output index maps
 };
-TcRoles tc_roles(const Step& S) {
+int64_t single_stride(const Runs& r, int64_t extent, bool* ok) {
+  if (extent <= 1) return 0;
+  if (r.n != 1) *ok = false;
+  return r.n > 0 ? r.st[0] : 0;
+}
+TcRoles tc_roles(const Step& S, bool* ok_out = nullptr) {
   const GemmParams& g = S.gp;
   TcRoles r{};
+  bool ok = true;
   if (!S.tc_swap) {
-    r = {S.a, S.b, g.M, g.N, g.K, g.sa_bt, g.sa_m, g.sb_bt, g.sb_k, g.sb_n, g.sc_bt, g.sc_m, g.sc_n};
+    r.a_node = S.a;
+    r.b_node = S.b;
+    r.M = g.M;
+    r.N = g.N;
+    r.K = g.K;
+    r.a_bt = single_stride(g.a_bt, g.nbt, &ok);
+    r.a_m = single_stride(g.a_m, g.M, &ok);
+    ok = ok && (g.K <= 1 || (g.a_k.n == 1 && g.a_k.st[0] == 1));
+    r.b_bt = g.b_bt;
+    r.b_k = g.b_k;
+    r.b_n = g.b_n;
+    r.c_bt = g.c_bt;
+    r.c_m = g.c_m;
+    r.c_n = g.c_n;
   } else {
-    r = {S.b, S.a, g.N, g.M, g.K, g.sb_bt, g.sb_n, g.sa_bt, g.sa_k, g.sa_m, g.sc_bt, g.sc_n, g.sc_m};
+    r.a_node = S.b;
+    r.b_node = S.a;
+    r.M = g.N;
+    r.N = g.M;
+    r.K = g.K;
+    r.a_bt = single_stride(g.b_bt, g.nbt, &ok);
+    r.a_m = single_stride(g.b_n, g.N, &ok);
+    ok = ok && (g.K <= 1 || (g.b_k.n == 1 && g.b_k.st[0] == 1));
+    r.b_bt = g.a_bt;
+    r.b_k = g.a_k;
+    r.b_n = g.a_m;
+    r.c_bt = g.c_bt;
+    r.c_m = g.c_n;
+    r.c_n = g.c_m;
   }
+  if (ok_out) *ok_out = ok;
   return r;
 }
 
@@ -500,17 +471,17 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     const bool b_c64 = P.nodes[r.b_node].kind == KIND_C64;
     TN_CHECK(NA.kind == P.skind && NA.hilo == S.hilo, TN_ERR_INVALID_ARG, "internal: tensor-core operand storage");
     R.begin(4, 0, (double)node_bytes(P, r.b_node, false) + (double)bx_bytes * (S.hilo ? 2 : 1));
-    launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s, b_c64,
-                    bx_lo);
+    launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s,
+                    b_c64, bx_lo);
     R.end();
     TcGemmParams tp{};
     tp.nbt = S.gp.nbt;
     tp.M = r.M;
     tp.N = r.N;
     tp.K = r.K;
-    tp.sc_bt = r.c_bt;
-    tp.sc_m = r.c_m;
-    tp.sc_n = r.c_n;
+    tp.c_bt = r.c_bt;
+    tp.c_m = r.c_m;
+    tp.c_n = r.c_n;
     tp.C = out;
     tp.C2 = out_hilo ? out + lo_off : nullptr;
     tp.out_kind = out_kind;
@@ -747,19 +718,16 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     // other is expanded to its real 2x2 form
     if (P.skind != KIND_C64) {
       const GemmParams& g = S.gp;
-      const bool a_ok = tc_gemm_supported(g.nbt, g.M, g.N, g.K, g.sa_bt, g.sa_m, g.sa_k) && g.M >= 64;
-      const bool b_ok = tc_gemm_supported(g.nbt, g.N, g.M, g.K, g.sb_bt, g.sb_n, g.sb_k) && g.N >= 64;
       const bool big = g.K >= 8 && (double)g.nbt * g.M * g.N * g.K >= double(1 << 18);
-      if (big && (a_ok || b_ok)) {
+      // the operand laid out [bt][free][contracted] is the one read as stored
+      S.tc_swap = P.nodes[S.b].elems > P.nodes[S.a].elems;
+      bool ok = false;
+      TcRoles r = tc_roles(S, &ok);
+      const int an = r.a_node;
+      if (big && ok && !P.nodes[an].leaf && r.M >= 64 &&
+          tc_gemm_supported(g.nbt, r.M, r.N, r.K, r.a_bt, r.a_m, 1)) {
         S.tc = true;
-        if (a_ok && b_ok)
-          S.tc_swap = P.nodes[S.b].elems > P.nodes[S.a].elems;
-        else
-          S.tc_swap = b_ok;
-        // the operand read as stored must be an intermediate (leaves stay complex64)
-        const int an = S.tc_swap ? S.b : S.a;
-        if (P.nodes[an].leaf) S.tc = false;
-        S.hilo = S.tc && (P.flags & TN_FLAG_HILO);
+        S.hilo = (P.flags & TN_FLAG_HILO) != 0;
       }
     }
   }

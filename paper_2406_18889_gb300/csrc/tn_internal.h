@@ -34,12 +34,34 @@ void set_error(const std::string& msg);
 // ------------------------------------------------------------ kernel params
 constexpr int kMaxBits = 48;
 
-// C[bt][m][n] (+)= sum_k A[bt][m][k] * B[bt][k][n]; element strides per index.
+// Index map of one index group of one tensor: the group's linear index i is
+// split into digits, run 0 the fastest; digit r has 2^lg[r] values and stride
+// st[r] (elements).  offset(i) = sum_r digit_r(i) * st[r].  The digit order is
+// the group's canonical order, shared by every tensor holding the group, so a
+// group may sit in memory as several separate runs in any order.
+constexpr int kMaxRuns = 16;
+struct Runs {
+  int n;
+  int8_t lg[kMaxRuns];
+  int64_t st[kMaxRuns];
+};
+
+__host__ __device__ inline int64_t run_offset(const Runs& R, int64_t i) {
+  int64_t o = 0;
+  for (int r = 0; r < R.n; ++r) {
+    o += (i & ((int64_t(1) << R.lg[r]) - 1)) * R.st[r];
+    i >>= R.lg[r];
+  }
+  return o;
+}
+
+// C[bt][m][n] = scale * sum_k A[bt][m][k] * B[bt][k][n] with every index group
+// addressed through its runs (any layout of A, B and C).
 struct GemmParams {
   int64_t nbt, M, N, K;
-  int64_t sa_bt, sa_m, sa_k;
-  int64_t sb_bt, sb_k, sb_n;
-  int64_t sc_bt, sc_m, sc_n;
+  Runs a_bt, a_m, a_k;
+  Runs b_bt, b_k, b_n;
+  Runs c_bt, c_m, c_n;
   const void* A;
   const void* B;
   void* C;
@@ -80,7 +102,7 @@ struct StridedCopy {
 // C[bt][m][n] = scale * sum_k A[bt][m][k] B[bt][k][n]; extents in complex elements.
 struct TcGemmParams {
   int64_t nbt, M, N, K;
-  int64_t sc_bt, sc_m, sc_n;  // output strides (complex elements)
+  Runs c_bt, c_m, c_n;        // output index maps
   void* C;
   int out_kind;               // 0 = fp16 complex, 1 = bf16 complex, 2 = fp32 complex
   int out_hilo;               // 16-bit output also writes its rounding residual to C2
@@ -123,10 +145,12 @@ int tc_gemm_bn(int64_t N);
 // With A_lo and Bx_lo non-null the product is A*B + A*B_lo + A_lo*B (hi+lo split).
 void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m, const void* Bx,
                     const void* Bx_lo, const TcGemmParams& p, bool bf16, cudaStream_t s);
-// expand a complex operand stored as fp32 (in_c64) or 16-bit complex into its real 2x2
-// form; with Bx_lo non-null also the rounding residual of every entry
-void launch_expand_b(const void* B, int64_t sb_bt, int64_t sb_k, int64_t sb_n, int64_t nbt, int64_t N, int64_t K,
-                     bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr);
+// expand a complex operand B[bt][k][n] (index maps b_bt, b_k, b_n) stored as fp32
+// (in_c64) or 16-bit complex into its real 2x2 form; with Bx_lo non-null also
+// the rounding residual of every entry
+void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
+                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr);
+Runs single_run(int64_t extent, int64_t stride);
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K);
 double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
                         int* d_err);

@@ -62,6 +62,20 @@ def test_grid4x6_all_slices(E, sv_grid4x6, batch):
     assert err <= C64_TOL, err
 
 
+@pytest.mark.parametrize("prec", ["c64", "fp16"])
+def test_hoisted_invariant_subtrees(E, sv_grid4x6, prec):
+    # slice-independent subtrees contracted once at plan creation give the same sum
+    from paper_2406_18889_gb300 import binding as B
+    w, psi = sv_grid4x6
+    prep = E.prepare(w)
+    plan = E.Plan(prep.tn, prep.tree, prec=prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=32)
+    kinds = plan.steps()["kinds"]
+    assert ((kinds & 4) > 0).sum() > 0
+    got = plan.contract().cpu().numpy()
+    ref, _ = _sv_blocks(w, psi)
+    assert pp.relative_l2(got, ref) <= (C64_TOL if prec == "c64" else 3e-3)
+
+
 @pytest.mark.parametrize("batch,n_run", [(8, 19), (4, 4), (16, 1)])
 def test_partial_fraction_ragged_batches(E, batch, n_run):
     # f < 1: the sum over a seeded subset of sub-networks, against the oracle's own
