@@ -37,7 +37,6 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;  // real k per stage: one 128-byte swizzle row of 16-bit values
-constexpr int STAGES = 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -104,45 +103,60 @@ __host__ __device__ constexpr uint32_t make_idesc(int n, bool bf16) {
 }
 
 template <int BN>
-constexpr size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8;
+__host__ __device__ constexpr int stages_for() {
+  return BN >= 256 ? 4 : BN >= 128 ? 6 : 8;
+}
+template <int BN>
+__host__ __device__ constexpr size_t smem_bytes() {
+  return 1024 + (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8;
 }
 
-// HILO: three accumulating passes over K -- (A, B), (A, B_lo), (A_lo, B) -- the
-// split-precision product that drops only the lo*lo term
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent: CTA c walks output tiles c, c + gridDim.x, ... (n tile fastest,
+// then m tile, then batch).  The TMEM accumulator is double-buffered (2 x BN
+// columns): the MMA thread fills buffer (i & 1) for the CTA's i-th tile while
+// the epilogue drains the other; tfull/tempty hand the buffers back and forth.
 template <int BN, bool BF16, bool HILO>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
                    TcGemmParams p) {
+  constexpr int S = stages_for<BN>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sB = sA + STAGES * BM * BK * 2;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * BN * BK * 2);
-  uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint8_t* sB = sA + S * BM * BK * 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * BN * BK * 2);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;   // [2] MMA -> epilogue
+  uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int64_t* n_off = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 256);  // [BN / 2]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y;
-  const int bt = blockIdx.z;
   const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
   const int k_tiles = HILO ? 3 * k_tiles1 : k_tiles1;
+  const int64_t n_n = (2 * p.N + BN - 1) / BN, n_m = (p.M + BM - 1) / BM;
+  const int64_t tiles = p.nbt * n_m * n_n;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -153,71 +167,104 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kt = 0; kt < k_tiles; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t use = kt / STAGES;
-        if (kt >= STAGES && !wait_bounded(&empty[s], (use & 1) ^ 1, p.err)) break;
-        const int pass = HILO ? kt / k_tiles1 : 0;
-        const int kx = (kt - pass * k_tiles1) * BK;
-        mbar_expect_tx(&full[s], (uint32_t)((BM + BN) * BK * 2));
-        tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + s * BM * BK * 2, kx, m_tile * BM, bt);
-        tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
-        ++issued;
+      int64_t g = 0;  // ring position over all of this CTA's k tiles
+      bool stop = false;
+      for (int64_t t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
+        const int n_tile = (int)(t % n_n), m_tile = (int)((t / n_n) % n_m), bt = (int)(t / (n_n * n_m));
+        for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+          const int s = (int)(g % S);
+          const uint32_t use = (uint32_t)(g / S);
+          if (g >= S && !wait_bounded(&empty[s], (use & 1) ^ 1, p.err)) {
+            stop = true;
+            break;
+          }
+          const int pass = HILO ? kt / k_tiles1 : 0;
+          const int kx = (kt - pass * k_tiles1) * BK;
+          mbar_expect_tx(&full[s], (uint32_t)((BM + BN) * BK * 2));
+          tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + s * BM * BK * 2, kx, m_tile * BM, bt);
+          tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
+        }
       }
       // drain: every issued load must have landed before the CTA can exit
-      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
+      for (int64_t q = (g > S ? g - S : 0); q < g; ++q) {
         const uint64_t t0 = gtimer();
-        while (!mbar_try_wait(&full[kt % STAGES], (kt / STAGES) & 1) && gtimer() - t0 < kWaitNs) {
+        while (!mbar_try_wait(&full[q % S], (uint32_t)((q / S) & 1)) && gtimer() - t0 < kWaitNs) {
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(BN, BF16);
-      for (int kt = 0; kt < k_tiles; ++kt) {
-        const int s = kt % STAGES;
-        if (!wait_bounded(&full[s], (kt / STAGES) & 1, p.err)) break;
+      int64_t g = 0;
+      int64_t local = 0;
+      bool stop = false;
+      for (int64_t t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++local) {
+        const int b = (int)(local & 1);
+        const uint32_t u = (uint32_t)(local >> 1);
+        if (local >= 2 && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
-        const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
+        const uint32_t acc_addr = tmem + (uint32_t)(b * BN);
+        for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+          const int s = (int)(g % S);
+          if (!wait_bounded(&full[s], (uint32_t)((g / S) & 1), p.err)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
+          const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint64_t ad = sw128_desc(a0 + kk * 32);
-          const uint64_t bd = sw128_desc(b0 + kk * 32);
-          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\t"
-              "setp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ad = sw128_desc(a0 + kk * 32);
+            const uint64_t bd = sw128_desc(b0 + kk * 32);
+            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty[s]))
+                       : "memory");
         }
+        // tfull[b] completes when this tile's MMAs (and all earlier ones) finish
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&empty[s]))
+                         smem_u32(&tfull[b]))
                      : "memory");
       }
-      // `done` completes when every MMA issued above has finished
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(done))
-                   : "memory");
+      // before TMEM is freed: wait (bounded) for the last committed tile's MMAs
+      if (local > 0) {
+        const int64_t last = local - 1;
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(&tfull[last & 1], (uint32_t)((last >> 1) & 1)) && gtimer() - t0 < kWaitNs) {
+        }
+      }
     }
   } else {
-    // epilogue warps 2..5: output offsets of this tile's columns, then rows
+    // epilogue warps 2..5
     const int et = threadIdx.x - 64;  // 0..127
-    const int64_t nbase = (int64_t)n_tile * BN / 2;
-    for (int j = et; j < BN / 2; j += 128) n_off[j] = nbase + j < p.N ? run_offset(p.c_n, nbase + j) : 0;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    const bool ok = wait_bounded(done, 0, p.err);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int quarter = warp & 3;
-    const int64_t m = (int64_t)m_tile * BM + quarter * 32 + lane;
-    const int64_t base = m < p.M ? run_offset(p.c_bt, bt) + run_offset(p.c_m, m) : 0;
-    if (ok) {
+    int64_t local = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
+      const int n_tile = (int)(t % n_n), m_tile = (int)((t / n_n) % n_m), bt = (int)(t / (n_n * n_m));
+      const int b = (int)(local & 1);
+      const uint32_t u = (uint32_t)(local >> 1);
+      const int64_t nbase = (int64_t)n_tile * BN / 2;
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // previous tile's table no longer read
+      for (int j = et; j < BN / 2; j += 128) n_off[j] = nbase + j < p.N ? run_offset(p.c_n, nbase + j) : 0;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // every epilogue thread runs every iteration (the named barriers above need all
+      // 128); after a timed-out wait (warp-uniform) the tile's reads and stores are skipped
+      const bool ok = __all_sync(0xffffffffu, wait_bounded(&tfull[b], u & 1, p.err));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t m = (int64_t)m_tile * BM + quarter * 32 + lane;
+      const int64_t base = m < p.M ? run_offset(p.c_bt, bt) + run_offset(p.c_m, m) : 0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < BN && ok; c0 += 32) {
         uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
             "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -258,20 +305,17 @@ __global__ void __launch_bounds__(192, 1)
           }
         }
       }
+      // hand the accumulator buffer back to the MMA thread
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // all MMAs must be complete before their accumulator is freed
-    if (lane == 0) {
-      const uint64_t t0 = gtimer();
-      while (!mbar_try_wait(done, 0) && gtimer() - t0 < kWaitNs) {
-      }
-    }
-    __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
                  : "memory");
   }
 }
@@ -314,7 +358,8 @@ void launch_bn(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap&
                                  (int)sm));
     attr = true;
   }
-  dim3 grid((unsigned)((2 * p.N + BN - 1) / BN), (unsigned)((p.M + BM - 1) / BM), (unsigned)p.nbt);
+  const int64_t tiles = ((2 * p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM) * p.nbt;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152);
   tc_gemm_kernel<BN, BF16, HILO><<<grid, 192, sm, s>>>(ma, ma2, mb, mb2, p);
 }
 
