@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
   }
 }
 
-// one thread per output element (bt, m, n), n fastest
+// one thread per output element, walking C in memory order (coalesced writes);
+// (bt, m, n) are decoded from the output offset's bits
 template <class In, class Out>
 __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bool hilo) {
   using TI = typename In::T;
@@ -173,16 +174,14 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
   const int64_t total = p.nbt * p.M * p.N;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = x % p.N;
-    const int64_t t = x / p.N;
-    const int64_t m = t % p.M;
-    const int64_t bt = t / p.M;
-    const TI* a = A + run_offset(p.a_bt, bt) + run_offset(p.a_m, m);
-    const TI* b = Bm + run_offset(p.b_bt, bt) + run_offset(p.b_n, n);
+    int64_t idx[3] = {0, 0, 0};
+    for (int e = 0; e < p.c_dec.n; ++e)
+      idx[p.c_dec.grp[e]] |= ((x >> p.c_dec.pos[e]) & ((int64_t(1) << p.c_dec.lg[e]) - 1)) << p.c_dec.shift[e];
+    const TI* a = A + run_offset(p.a_bt, idx[0]) + run_offset(p.a_m, idx[1]);
+    const TI* b = Bm + run_offset(p.b_bt, idx[0]) + run_offset(p.b_n, idx[2]);
     float2 acc = make_float2(0.f, 0.f);
     for (int64_t k = 0; k < p.K; ++k) cmac(acc, In::ld(a[run_offset(p.a_k, k)]), In::ld(b[run_offset(p.b_k, k)]));
-    store_out<Out>(C, (TO*)p.C2, run_offset(p.c_bt, bt) + run_offset(p.c_m, m) + run_offset(p.c_n, n),
-                   make_float2(acc.x * scale, acc.y * scale), hilo);
+    store_out<Out>(C, (TO*)p.C2, x, make_float2(acc.x * scale, acc.y * scale), hilo);
   }
 }
 
@@ -232,6 +231,28 @@ void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scal
   if (in_kind == 2 && out_kind == 0) return launch_typed<C64, F16>(p, scale, s, out_hilo);
   if (in_kind == 2 && out_kind == 1) return launch_typed<C64, BF16>(p, scale, s, out_hilo);
   fail(TN_ERR_UNSUPPORTED, "GEMM storage combination");
+}
+
+RunDecode decode_of(const Runs& bt, const Runs& m, const Runs& n) {
+  RunDecode d{};
+  d.n = 0;
+  const Runs* gs[3] = {&bt, &m, &n};
+  for (int g = 0; g < 3; ++g) {
+    int shift = 0;
+    for (int r = 0; r < gs[g]->n; ++r) {
+      int64_t st = gs[g]->st[r];
+      int pos = 0;
+      while ((int64_t(1) << pos) < st) ++pos;
+      TN_CHECK((int64_t(1) << pos) == st, TN_ERR_UNSUPPORTED, "output stride is not a power of two");
+      d.pos[d.n] = (int8_t)pos;
+      d.lg[d.n] = gs[g]->lg[r];
+      d.grp[d.n] = (int8_t)g;
+      d.shift[d.n] = (int8_t)shift;
+      shift += gs[g]->lg[r];
+      ++d.n;
+    }
+  }
+  return d;
 }
 
 // one run covering any extent (the digit mask is wider than every index)

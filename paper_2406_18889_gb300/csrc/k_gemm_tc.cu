@@ -102,13 +102,38 @@ __host__ __device__ constexpr uint32_t make_idesc(int n, bool bf16) {
          ((uint32_t)(BM >> 4) << 24);
 }
 
+// epilogue staging: per warp 32 rows x 16 complex (padded) + 32 row offsets
+constexpr int kStagePitch = 17;
+constexpr size_t kStageBytes = 4 * 32 * kStagePitch * 8 + 4 * 32 * 8;
+
 template <int BN>
 __host__ __device__ constexpr int stages_for() {
   return BN >= 256 ? 4 : BN >= 128 ? 6 : 8;
 }
 template <int BN>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8;
+  return 1024 + (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8 + kStageBytes;
+}
+
+// one complex output element, converted to the output kind (hi + lo when split)
+__device__ __forceinline__ void store_c(const TcGemmParams& p, int64_t o, float re, float im) {
+  if (p.out_kind == 2) {
+    reinterpret_cast<float2*>(p.C)[o] = make_float2(re, im);
+  } else if (p.out_kind == 1) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    reinterpret_cast<__nv_bfloat162*>(p.C)[o] = h;
+    if (p.out_hilo) {
+      const float2 hf = __bfloat1622float2(h);
+      reinterpret_cast<__nv_bfloat162*>(p.C2)[o] = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+    }
+  } else {
+    const __half2 h = __floats2half2_rn(re, im);
+    reinterpret_cast<__half2*>(p.C)[o] = h;
+    if (p.out_hilo) {
+      const float2 hf = __half22float2(h);
+      reinterpret_cast<__half2*>(p.C2)[o] = __floats2half2_rn(re - hf.x, im - hf.y);
+    }
+  }
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -135,6 +160,8 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int64_t* n_off = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 256);  // [BN / 2]
+  float2* stage_buf = reinterpret_cast<float2*>(n_off + BN / 2);                         // [4][32][pitch]
+  int64_t* row_base = reinterpret_cast<int64_t*>(stage_buf + 4 * 32 * kStagePitch);      // [4][32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
@@ -261,6 +288,10 @@ __global__ void __launch_bounds__(192, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t m = (int64_t)m_tile * BM + quarter * 32 + lane;
       const int64_t base = m < p.M ? run_offset(p.c_bt, bt) + run_offset(p.c_m, m) : 0;
+      float2* stg = stage_buf + quarter * 32 * kStagePitch;
+      int64_t* rb = row_base + quarter * 32;
+      rb[lane] = base;
+      __syncwarp();
 #pragma unroll 1
       for (int c0 = 0; c0 < BN && ok; c0 += 32) {
         uint32_t v[32];
@@ -277,31 +308,31 @@ __global__ void __launch_bounds__(192, 1)
             : "r"(taddr)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (m < p.M) {
-          const int j0 = c0 / 2;
+        const int j0 = c0 / 2;
+        if (p.stage_n) {
+          // transpose through shared memory: lanes then run along n (16 per row)
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            stg[lane * kStagePitch + j] =
+                make_float2(__uint_as_float(v[2 * j]) * p.scale, __uint_as_float(v[2 * j + 1]) * p.scale);
+          __syncwarp();
+#pragma unroll 4
+          for (int it = 0; it < 16; ++it) {
+            const int e = it * 32 + lane;
+            const int r = e >> 4, jj = e & 15;
+            const int64_t mr = (int64_t)m_tile * BM + quarter * 32 + r;
+            if (mr < p.M && nbase + j0 + jj < p.N) {
+              const float2 val = stg[r * kStagePitch + jj];
+              store_c(p, rb[r] + n_off[j0 + jj], val.x, val.y);
+            }
+          }
+          __syncwarp();
+        } else if (m < p.M) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             if (nbase + j0 + j >= p.N) break;
-            const float re = __uint_as_float(v[2 * j]) * p.scale;
-            const float im = __uint_as_float(v[2 * j + 1]) * p.scale;
-            const int64_t o = base + n_off[j0 + j];
-            if (p.out_kind == 2) {
-              reinterpret_cast<float2*>(p.C)[o] = make_float2(re, im);
-            } else if (p.out_kind == 1) {
-              const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
-              reinterpret_cast<__nv_bfloat162*>(p.C)[o] = h;
-              if (p.out_hilo) {
-                const float2 hf = __bfloat1622float2(h);
-                reinterpret_cast<__nv_bfloat162*>(p.C2)[o] = __floats2bfloat162_rn(re - hf.x, im - hf.y);
-              }
-            } else {
-              const __half2 h = __floats2half2_rn(re, im);
-              reinterpret_cast<__half2*>(p.C)[o] = h;
-              if (p.out_hilo) {
-                const float2 hf = __half22float2(h);
-                reinterpret_cast<__half2*>(p.C2)[o] = __floats2half2_rn(re - hf.x, im - hf.y);
-              }
-            }
+            store_c(p, base + n_off[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
+                    __uint_as_float(v[2 * j + 1]) * p.scale);
           }
         }
       }
@@ -378,12 +409,19 @@ int tc_gemm_bn(int64_t N) {
 // A: complex 16-bit [bt][M][K] with k contiguous (strides sa_bt, sa_m in complex
 // elements); Bx: expanded real [bt][2N][pitch] (pitch = round_up(2K, 64)).
 void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m, const void* Bx,
-                    const void* Bx_lo, const TcGemmParams& p, bool bf16, cudaStream_t s) {
+                    const void* Bx_lo, const TcGemmParams& p_in, bool bf16, cudaStream_t s) {
+  TcGemmParams p = p_in;
   if (p.nbt <= 0 || p.M <= 0 || p.N <= 0) return;
   TN_CHECK(tc_gemm_supported(p.nbt, p.M, p.N, p.K, sa_bt, sa_m, 1), TN_ERR_UNSUPPORTED,
            "shape not supported by the tensor-core GEMM");
   const bool hilo = A_lo != nullptr && Bx_lo != nullptr;
   const int bn = p.bn;
+  {
+    // stage the epilogue when n is the output's more contiguous index
+    const int64_t big = int64_t(1) << 62;
+    const int64_t sn = p.c_n.n > 0 ? p.c_n.st[0] : big, sm = p.c_m.n > 0 ? p.c_m.st[0] : big;
+    p.stage_n = sn < sm ? 1 : 0;
+  }
   const uint64_t pitch = (uint64_t)((2 * p.K + BK - 1) / BK * BK);
   CUtensorMap ma, ma2, mb, mb2;
   const uint64_t a_row = (uint64_t)sa_m * 4, a_bt = p.nbt > 1 ? (uint64_t)sa_bt * 4 : a_row * (uint64_t)p.M;

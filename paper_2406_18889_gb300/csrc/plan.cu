@@ -223,6 +223,7 @@ struct Builder {
     g.c_bt = runs_of(bt_o, Lc);
     g.c_m = runs_of(m_o, Lc);
     g.c_n = runs_of(n_o, Lc);
+    g.c_dec = decode_of(g.c_bt, g.c_m, g.c_n);
     S.cost = (double)g.nbt * g.M * g.N * g.K;
   }
 

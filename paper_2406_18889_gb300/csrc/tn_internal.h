@@ -55,6 +55,15 @@ __host__ __device__ inline int64_t run_offset(const Runs& R, int64_t i) {
   return o;
 }
 
+// Inverse of C's runs: output offset o -> (bt, m, n).  Entry e takes the
+// digit (o >> pos[e]) & (2^lg[e] - 1) into group grp[e] (0 bt, 1 m, 2 n) at
+// bit `shift[e]` of that group's index.  Valid when C is dense (it holds
+// exactly nbt * M * N elements), which every contraction result is.
+struct RunDecode {
+  int n;
+  int8_t pos[3 * kMaxRuns], lg[3 * kMaxRuns], grp[3 * kMaxRuns], shift[3 * kMaxRuns];
+};
+
 // C[bt][m][n] = scale * sum_k A[bt][m][k] * B[bt][k][n] with every index group
 // addressed through its runs (any layout of A, B and C).
 struct GemmParams {
@@ -62,6 +71,7 @@ struct GemmParams {
   Runs a_bt, a_m, a_k;
   Runs b_bt, b_k, b_n;
   Runs c_bt, c_m, c_n;
+  RunDecode c_dec;  // memory-order walk of C (small-K kernel)
   const void* A;
   const void* B;
   void* C;
@@ -110,6 +120,7 @@ struct TcGemmParams {
   float scale;                // power of two applied to the FP32 accumulators
   int* err;                   // device flag raised when a bounded wait times out
   int bn;                     // real-column tile (32, 64, 128 or 256)
+  int stage_n;                // write tiles out along n (n is the output's contiguous index)
 };
 
 // ------------------------------------------------------------ launchers
@@ -151,6 +162,7 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
 void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
                      int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr);
 Runs single_run(int64_t extent, int64_t stride);
+RunDecode decode_of(const Runs& bt, const Runs& m, const Runs& n);
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K);
 double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
                         int* d_err);
