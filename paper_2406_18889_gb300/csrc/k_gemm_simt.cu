@@ -163,25 +163,36 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
 }
 
 // one thread per output element, walking C in memory order (coalesced writes);
-// (bt, m, n) are decoded from the output offset's bits
-template <class In, class Out>
+// (bt, m, n) are decoded from the output offset's bits.  I is the index type:
+// 32-bit when every operand and the result hold fewer than 2^31 elements.
+template <class I>
+__device__ __forceinline__ I run_off(const Runs& R, I i) {
+  I o = 0;
+  for (int r = 0; r < R.n; ++r) {
+    o += (i & ((I(1) << R.lg[r]) - 1)) * (I)R.st[r];
+    i >>= R.lg[r];
+  }
+  return o;
+}
+
+template <class In, class Out, class I>
 __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bool hilo) {
   using TI = typename In::T;
   using TO = typename Out::T;
   const TI* __restrict__ A = (const TI*)p.A;
   const TI* __restrict__ Bm = (const TI*)p.B;
   TO* __restrict__ C = (TO*)p.C;
-  const int64_t total = p.nbt * p.M * p.N;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    int64_t idx[3] = {0, 0, 0};
+  const I total = (I)(p.nbt * p.M * p.N);
+  const I K = (I)p.K;
+  for (I x = blockIdx.x * (I)blockDim.x + threadIdx.x; x < total; x += (I)gridDim.x * blockDim.x) {
+    I idx[3] = {0, 0, 0};
     for (int e = 0; e < p.c_dec.n; ++e)
-      idx[p.c_dec.grp[e]] |= ((x >> p.c_dec.pos[e]) & ((int64_t(1) << p.c_dec.lg[e]) - 1)) << p.c_dec.shift[e];
-    const TI* a = A + run_offset(p.a_bt, idx[0]) + run_offset(p.a_m, idx[1]);
-    const TI* b = Bm + run_offset(p.b_bt, idx[0]) + run_offset(p.b_n, idx[2]);
+      idx[p.c_dec.grp[e]] |= ((x >> p.c_dec.pos[e]) & ((I(1) << p.c_dec.lg[e]) - 1)) << p.c_dec.shift[e];
+    const TI* a = A + run_off<I>(p.a_bt, idx[0]) + run_off<I>(p.a_m, idx[1]);
+    const TI* b = Bm + run_off<I>(p.b_bt, idx[0]) + run_off<I>(p.b_n, idx[2]);
     float2 acc = make_float2(0.f, 0.f);
-    for (int64_t k = 0; k < p.K; ++k) cmac(acc, In::ld(a[run_offset(p.a_k, k)]), In::ld(b[run_offset(p.b_k, k)]));
-    store_out<Out>(C, (TO*)p.C2, x, make_float2(acc.x * scale, acc.y * scale), hilo);
+    for (I k = 0; k < K; ++k) cmac(acc, In::ld(a[run_off<I>(p.a_k, k)]), In::ld(b[run_off<I>(p.b_k, k)]));
+    store_out<Out>(C, (TO*)p.C2, (int64_t)x, make_float2(acc.x * scale, acc.y * scale), hilo);
   }
 }
 
@@ -202,7 +213,10 @@ void launch_typed(const GemmParams& p, float scale, cudaStream_t s, bool hilo = 
   const int64_t outputs = p.nbt * p.M * p.N;
   if (p.K <= 4 || (p.M < 16 && p.N < 16) || outputs * p.K < (1 << 16)) {
     int64_t blocks = std::min<int64_t>((outputs + 255) / 256, 152 * 64);
-    gemm_direct<In, Out><<<(unsigned)blocks, 256, 0, s>>>(p, scale, hilo);
+    if (p.elems_max < (int64_t(1) << 31))
+      gemm_direct<In, Out, int32_t><<<(unsigned)blocks, 256, 0, s>>>(p, scale, hilo);
+    else
+      gemm_direct<In, Out, int64_t><<<(unsigned)blocks, 256, 0, s>>>(p, scale, hilo);
     return;
   }
   if (p.M >= 64 && p.N >= 64)

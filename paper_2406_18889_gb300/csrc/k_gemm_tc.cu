@@ -420,7 +420,8 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     // stage the epilogue when n is the output's more contiguous index
     const int64_t big = int64_t(1) << 62;
     const int64_t sn = p.c_n.n > 0 ? p.c_n.st[0] : big, sm = p.c_m.n > 0 ? p.c_m.st[0] : big;
-    p.stage_n = sn < sm ? 1 : 0;
+    // only for write-bound tiles (one or two k tiles); deeper tiles hide the per-row stores
+    p.stage_n = (sn < sm && 2 * p.K <= 2 * BK) ? 1 : 0;
   }
   const uint64_t pitch = (uint64_t)((2 * p.K + BK - 1) / BK * BK);
   CUtensorMap ma, ma2, mb, mb2;

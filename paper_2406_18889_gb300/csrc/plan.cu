@@ -224,6 +224,7 @@ struct Builder {
     g.c_m = runs_of(m_o, Lc);
     g.c_n = runs_of(n_o, Lc);
     g.c_dec = decode_of(g.c_bt, g.c_m, g.c_n);
+    g.elems_max = std::max({P.nodes[S.a].elems, P.nodes[S.b].elems, P.nodes[S.c].elems});
     S.cost = (double)g.nbt * g.M * g.N * g.K;
   }
 

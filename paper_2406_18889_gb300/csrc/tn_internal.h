@@ -72,6 +72,7 @@ struct GemmParams {
   Runs b_bt, b_k, b_n;
   Runs c_bt, c_m, c_n;
   RunDecode c_dec;  // memory-order walk of C (small-K kernel)
+  int64_t elems_max;  // largest of A, B, C in elements (index width selection)
   const void* A;
   const void* B;
   void* C;
