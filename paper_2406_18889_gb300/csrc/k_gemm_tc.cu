@@ -110,9 +110,9 @@ template <int BN>
 __host__ __device__ constexpr int stages_for() {
   return BN >= 256 ? 4 : BN >= 128 ? 6 : 8;
 }
-template <int BN>
+template <int BN, bool STAGE>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8 + kStageBytes;
+  return 1024 + (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8 + (STAGE ? kStageBytes : 0);
 }
 
 // one complex output element, converted to the output kind (hi + lo when split)
@@ -144,7 +144,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // then m tile, then batch).  The TMEM accumulator is double-buffered (2 x BN
 // columns): the MMA thread fills buffer (i & 1) for the CTA's i-th tile while
 // the epilogue drains the other; tfull/tempty hand the buffers back and forth.
-template <int BN, bool BF16, bool HILO>
+template <int BN, bool BF16, bool HILO, bool STAGE>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
@@ -290,8 +290,10 @@ __global__ void __launch_bounds__(192, 1)
       const int64_t base = m < p.M ? run_offset(p.c_bt, bt) + run_offset(p.c_m, m) : 0;
       float2* stg = stage_buf + quarter * 32 * kStagePitch;
       int64_t* rb = row_base + quarter * 32;
-      rb[lane] = base;
-      __syncwarp();
+      if (STAGE) {
+        rb[lane] = base;
+        __syncwarp();
+      }
 #pragma unroll 1
       for (int c0 = 0; c0 < BN && ok; c0 += 32) {
         uint32_t v[32];
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(192, 1)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int j0 = c0 / 2;
-        if (p.stage_n) {
+        if (STAGE) {
           // transpose through shared memory: lanes then run along n (16 per row)
 #pragma unroll
           for (int j = 0; j < 16; ++j)
@@ -379,19 +381,27 @@ void make_map(CUtensorMap* map, const void* base, bool bf16, uint64_t inner, uin
   TN_CHECK(r == CUDA_SUCCESS, TN_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
-template <int BN, bool BF16, bool HILO>
-void launch_bn(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
-               const TcGemmParams& p, cudaStream_t s) {
-  const size_t sm = smem_bytes<BN>();
+template <int BN, bool BF16, bool HILO, bool STAGE>
+void launch_bn4(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+                const TcGemmParams& p, cudaStream_t s) {
+  const size_t sm = smem_bytes<BN, STAGE>();
   static bool attr = false;
   if (!attr) {
-    TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, BF16, HILO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm));
+    TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, BF16, HILO, STAGE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
   const int64_t tiles = ((2 * p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM) * p.nbt;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152);
-  tc_gemm_kernel<BN, BF16, HILO><<<grid, 192, sm, s>>>(ma, ma2, mb, mb2, p);
+  tc_gemm_kernel<BN, BF16, HILO, STAGE><<<grid, 192, sm, s>>>(ma, ma2, mb, mb2, p);
+}
+template <int BN, bool BF16, bool HILO>
+void launch_bn(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+               const TcGemmParams& p, cudaStream_t s) {
+  if (p.stage_n)
+    launch_bn4<BN, BF16, HILO, true>(ma, ma2, mb, mb2, p, s);
+  else
+    launch_bn4<BN, BF16, HILO, false>(ma, ma2, mb, mb2, p, s);
 }
 
 }  // namespace
