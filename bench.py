@@ -231,6 +231,29 @@ def roofline_from_profile(prof) -> tuple:
     return r, per_kind
 
 
+def permute_bandwidth(B, torch, stream, bits: int = 28) -> dict:
+    """HBM bandwidth of tn_permute on a 2^28-element complex64 tensor whose two
+    14-bit halves swap places (a full transpose), events over 5 launches."""
+    peaks = measured_peaks()
+    x = torch.empty(1 << bits, dtype=torch.int64, device="cuda")
+    y = torch.empty_like(x)
+    half = bits // 2
+    out_bit = [(i + half) % bits for i in range(bits)]
+    B.tn_permute(x.data_ptr(), y.data_ptr(), out_bit, 8, stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        B.tn_permute(x.data_ptr(), y.data_ptr(), out_bit, 8, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    gbs = 2.0 * 8 * (1 << bits) / (ms / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    del x, y
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "case": "2^28 complex64 elements, 14-bit halves swapped (read + write bytes)", "ms": ms}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -331,6 +354,7 @@ def run_ours(args):
     prof = B.tn_contract_slices_profile(plan.handle, ids, amps.data_ptr(), 0, plan.workspace.data_ptr(),
                                         plan.workspace.numel(), stream.cuda_stream)
     roofline, per_kind = roofline_from_profile(prof)
+    permute = permute_bandwidth(B, torch, stream)
     launches_per_step = prof["n_launches"] + 2  # + top-k + XEB
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
@@ -373,6 +397,7 @@ def run_ours(args):
         "useful_flops_per_slice": useful_per_slice,
         "wall_s": wall,
         "roofline": roofline,
+        "permute": permute,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "slices/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

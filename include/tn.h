@@ -288,6 +288,19 @@ tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* slice_ids, i
 tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int32_t prec, uint64_t seed,
                               double* max_rel_err, void* stream);
 
+/*
+ * Index permutation of a tensor with power-of-two dimensions (paper Sec. III:
+ * the order of dimensions, and transposes between contraction steps).  The
+ * contraction path itself never calls it -- every GEMM reads and writes any
+ * layout in place -- but layouts fixed by a caller can be converted with it.
+ * in/out: device arrays of 2^nbits elements of elem_bytes (4 or 8) bytes,
+ * not overlapping; element x of `in` goes to the index whose bit out_bit[i]
+ * is bit i of x (out_bit a permutation of 0..nbits-1, host array).
+ * 1 <= nbits <= 40.
+ */
+tn_status tn_permute(const void* in, void* out, int32_t nbits, const int32_t* out_bit, int32_t elem_bytes,
+                     void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* tn_last_error(void);
 

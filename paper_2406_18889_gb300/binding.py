@@ -27,7 +27,7 @@ TN_FLAG_HILO = 0x8
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
            "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_plan_status",
-           "tn_last_error", "tn_version")
+           "tn_permute", "tn_last_error", "tn_version")
 
 
 class TNError(RuntimeError):
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
     lib.tn_xeb.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double), vp]
     lib.tn_contract_slices_noalloc.argtypes = [vp, p_i64, i64, vp, ctypes.c_int, vp]
     lib.tn_plan_status.argtypes = [vp, vp]
+    lib.tn_permute.argtypes = [vp, vp, i32, p_i32, i32, vp]
     lib.tn_selftest_gemm_tc.argtypes = [i64, i64, i64, i64, i32, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_double), vp]
     for name in EXPORTS[:-2]:
@@ -227,6 +228,12 @@ def tn_selftest_gemm_tc(nbt: int, M: int, N: int, K: int, prec: int, seed: int =
 
 def tn_plan_status(plan: int, stream: int = 0) -> None:
     _check(load().tn_plan_status(ctypes.c_void_p(plan), ctypes.c_void_p(stream)))
+
+
+def tn_permute(in_ptr: int, out_ptr: int, out_bit, elem_bytes: int, stream: int = 0) -> None:
+    ob = _i32(out_bit)
+    _check(load().tn_permute(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), len(ob), _p(ob, ctypes.c_int32),
+                             int(elem_bytes), ctypes.c_void_p(stream)))
 
 
 def tn_last_error() -> str:

@@ -293,6 +293,26 @@ tn_status tn_plan_status(tn_plan_t plan, void* stream) {
   });
 }
 
+tn_status tn_permute(const void* in, void* out, int32_t nbits, const int32_t* out_bit, int32_t elem_bytes,
+                     void* stream) {
+  return guarded([&] {
+    TN_CHECK(in && out && out_bit, TN_ERR_INVALID_ARG, "null pointer");
+    TN_CHECK(nbits >= 1 && nbits <= 40, TN_ERR_INVALID_ARG, "nbits out of range");
+    TN_CHECK(elem_bytes == 4 || elem_bytes == 8, TN_ERR_INVALID_ARG, "elem_bytes must be 4 or 8");
+    BitPermute bp{};
+    bp.nbits = nbits;
+    std::vector<char> seen(nbits, 0);
+    for (int i = 0; i < nbits; ++i) {
+      TN_CHECK(out_bit[i] >= 0 && out_bit[i] < nbits && !seen[out_bit[i]], TN_ERR_INVALID_ARG,
+               "out_bit is not a permutation");
+      seen[out_bit[i]] = 1;
+      bp.out_bit[i] = out_bit[i];
+    }
+    launch_bit_permute(in, out, bp, elem_bytes, (cudaStream_t)stream);
+    TN_CUDA(cudaGetLastError());
+  });
+}
+
 const char* tn_last_error(void) { return g_last_error.c_str(); }
 
 const char* tn_version(void) { return "tn-gb300 0.1 (sm_103a)"; }

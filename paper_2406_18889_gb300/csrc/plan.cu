@@ -137,12 +137,13 @@ struct Builder {
   }
   int producer(int node) const { return P.nodes[node].leaf ? -1 : node - P.n_leaves; }
 
-  // Root-down (the paper's greedy dimension ordering from the root): the
-  // larger operand is stored [batch][free][contracted] (contracted fastest,
-  // the form the tensor cores read), the smaller [batch][contracted][free];
-  // batch and free indices keep the result's order; the contracted order
-  // groups the larger operand's producer's index groups so that producer
-  // writes long contiguous runs.
+  // Root-down (the paper's greedy dimension ordering from the root): both
+  // operands are stored [batch][free][contracted] -- contracted dimensions
+  // last and in the same order in both inputs, free dimensions in the
+  // result's order; the larger operand is the one the tensor cores read as
+  // stored, the smaller is read along k when it is expanded.  The contracted
+  // order groups the larger operand's producer's index groups so that the
+  // producer writes long contiguous runs.
   void assign_layouts() {
     Node& R = P.nodes[P.root];
     std::vector<int> rl;
@@ -174,8 +175,8 @@ struct Builder {
       big.insert(big.end(), fb.begin(), fb.end());
       big.insert(big.end(), k_o.begin(), k_o.end());
       small.insert(small.end(), bt_o.begin(), bt_o.end());
-      small.insert(small.end(), k_o.begin(), k_o.end());
       small.insert(small.end(), fs.begin(), fs.end());
+      small.insert(small.end(), k_o.begin(), k_o.end());
       P.nodes[S.a].layout = a_big ? big : small;
       P.nodes[S.b].layout = a_big ? small : big;
     }
