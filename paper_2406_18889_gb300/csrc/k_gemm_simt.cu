@@ -184,15 +184,24 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
   TO* __restrict__ C = (TO*)p.C;
   const I total = (I)(p.nbt * p.M * p.N);
   const I K = (I)p.K;
-  for (I x = blockIdx.x * (I)blockDim.x + threadIdx.x; x < total; x += (I)gridDim.x * blockDim.x) {
+  // four consecutive outputs per thread when C's fastest run (pos 0) spans >= 4
+  // elements: they differ only in that run's digit, i.e. in one group's index
+  const bool vec = p.c_dec.n > 0 && p.c_dec.pos[0] == 0 && p.c_dec.lg[0] >= 2 && (total & 3) == 0;
+  const int g0 = p.c_dec.grp[0];
+  const I step0 = I(1) << p.c_dec.shift[0];
+  const I per = vec ? 4 : 1;
+  for (I x = (blockIdx.x * (I)blockDim.x + threadIdx.x) * per; x < total; x += (I)gridDim.x * blockDim.x * per) {
     I idx[3] = {0, 0, 0};
     for (int e = 0; e < p.c_dec.n; ++e)
       idx[p.c_dec.grp[e]] |= ((x >> p.c_dec.pos[e]) & ((I(1) << p.c_dec.lg[e]) - 1)) << p.c_dec.shift[e];
-    const TI* a = A + run_off<I>(p.a_bt, idx[0]) + run_off<I>(p.a_m, idx[1]);
-    const TI* b = Bm + run_off<I>(p.b_bt, idx[0]) + run_off<I>(p.b_n, idx[2]);
-    float2 acc = make_float2(0.f, 0.f);
-    for (I k = 0; k < K; ++k) cmac(acc, In::ld(a[run_off<I>(p.a_k, k)]), In::ld(b[run_off<I>(p.b_k, k)]));
-    store_out<Out>(C, (TO*)p.C2, (int64_t)x, make_float2(acc.x * scale, acc.y * scale), hilo);
+    for (I v = 0; v < per; ++v) {
+      const TI* a = A + run_off<I>(p.a_bt, idx[0]) + run_off<I>(p.a_m, idx[1]);
+      const TI* b = Bm + run_off<I>(p.b_bt, idx[0]) + run_off<I>(p.b_n, idx[2]);
+      float2 acc = make_float2(0.f, 0.f);
+      for (I k = 0; k < K; ++k) cmac(acc, In::ld(a[run_off<I>(p.a_k, k)]), In::ld(b[run_off<I>(p.b_k, k)]));
+      store_out<Out>(C, (TO*)p.C2, (int64_t)(x + v), make_float2(acc.x * scale, acc.y * scale), hilo);
+      idx[g0] += step0;
+    }
   }
 }
 
@@ -212,7 +221,7 @@ template <class In, class Out>
 void launch_typed(const GemmParams& p, float scale, cudaStream_t s, bool hilo = false) {
   const int64_t outputs = p.nbt * p.M * p.N;
   if (p.K <= 4 || (p.M < 16 && p.N < 16) || outputs * p.K < (1 << 16)) {
-    int64_t blocks = std::min<int64_t>((outputs + 255) / 256, 152 * 64);
+    int64_t blocks = std::min<int64_t>((outputs / 4 + 255) / 256 + 1, 152 * 64);
     if (p.elems_max < (int64_t(1) << 31))
       gemm_direct<In, Out, int32_t><<<(unsigned)blocks, 256, 0, s>>>(p, scale, hilo);
     else

@@ -1,0 +1,48 @@
+"""Sycamore-shaped circuit (53 qubits on the diagonal-coupler grid, 12 cycles,
+l = 8 open qubits, G = 4 blocks), sliced until the largest intermediate has
+2^26 elements (43 sliced bonds).  Four seeded sub-networks are contracted one
+by one on the GPU and each is compared with the oracle's own contraction of
+the same sub-network.  A sub-network's amplitudes are ~1e-14: far below the
+fp16 normal range, so the reduced-precision run exercises the per-tensor
+power-of-two exponents."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import einsum_tn as et
+from oracle import postprocess as pp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def case():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_18889_gb300 import engine as E
+    from paper_2406_18889_gb300 import network as N
+    from paper_2406_18889_gb300 import pathfind as P
+    w = W.workload("sycamore53_d20", cycles=12, l=8, G=4)
+    assert w.n_qubits == 53
+    tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    tree = P.plan_tree(tn, cap_log2=26, restarts=1)
+    assert tree.log2_max_intermediate <= 26
+    ids = W.draw_slice_subset(1 << min(len(tree.sliced_edges), 62), 4, seed=53)
+    wires = [tn.wire_of_edge[e] for e in tree.sliced_edges]
+    net = et.build_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    ref = et.contract_each_slice(net, wires, ids)
+    return E, E.Prepared(tn, tree), ids, ref
+
+
+@pytest.mark.parametrize("prec,tol", [("c64", 1e-5), ("fp16", 3e-3)])
+def test_sycamore_shaped_slices(case, prec, tol):
+    E, prep, ids, ref = case
+    plan = E.Plan(prep.tn, prep.tree, prec=prec, max_slice_batch=4)
+    for i, sid in enumerate(ids):
+        got = plan.contract([sid]).cpu().numpy()
+        assert np.abs(ref[i]).max() < 1e-10  # deep below the fp16 range
+        assert pp.relative_l2(got, ref[i]) <= tol, (prec, sid)
+    plan.close()
