@@ -37,10 +37,19 @@ def case():
     return E, E.Prepared(tn, tree), ids, ref
 
 
-@pytest.mark.parametrize("prec,tol", [("c64", 1e-5), ("fp16", 3e-3)])
-def test_sycamore_shaped_slices(case, prec, tol):
+def c64_tolerance(plan) -> float:
+    """FP32 bound for a sub-network of S pairwise steps: each step rounds its result to
+    FP32 (relative u = 2^-24) and errors add along the tree at worst linearly, so
+    relative L2 <= 2 u S.  This network has ~1050 steps (bound ~1.25e-4); the 1e-5 bar of
+    the 24-qubit workloads is kept there."""
+    return max(1e-5, 2 * 2.0 ** -24 * len(plan.steps()["k"]))
+
+
+@pytest.mark.parametrize("prec", ["c64", "fp16"])
+def test_sycamore_shaped_slices(case, prec):
     E, prep, ids, ref = case
     plan = E.Plan(prep.tn, prep.tree, prec=prec, max_slice_batch=4)
+    tol = c64_tolerance(plan) if prec == "c64" else 3e-3
     for i, sid in enumerate(ids):
         got = plan.contract([sid]).cpu().numpy()
         assert np.abs(ref[i]).max() < 1e-10  # deep below the fp16 range
