@@ -779,9 +779,19 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
   TN_CUDA(cudaMalloc(&P.d_err, sizeof(int)));
   TN_CUDA(cudaMemsetAsync(P.d_err, 0, sizeof(int), stream));
   {
+    // calibration slices: seeded pseudo-random ids (splitmix64) spread over all sliced
+    // edges, so no sliced edge is pinned to one value across the sample
     std::vector<int64_t> ids(P.B);
     const int64_t S = int64_t(1) << P.sliced.size();
-    for (int b = 0; b < P.B; ++b) ids[b] = b % S;
+    uint64_t z = 0x2406188890ull;
+    for (int b = 0; b < P.B; ++b) {
+      z += 0x9E3779B97F4A7C15ull;
+      uint64_t x = z;
+      x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+      x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+      x ^= x >> 31;
+      ids[b] = (int64_t)(x & (uint64_t)(S - 1));
+    }
     int32_t nv = P.B;
     TN_CUDA(cudaMemcpyAsync(P.d_slice_ids, ids.data(), sizeof(int64_t) * P.B, cudaMemcpyHostToDevice, stream));
     TN_CUDA(cudaMemcpyAsync(P.d_n_valid, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, stream));
@@ -858,12 +868,21 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       TN_CUDA(cudaMemcpyAsync(h.data(), d_amax, sizeof(unsigned) * h.size(), cudaMemcpyDeviceToHost, stream));
       TN_CUDA(cudaStreamSynchronize(stream));
       TN_CUDA(cudaGetLastError());
+      // magnitude exponent of every tensor; one that was exactly zero in the sample
+      // takes the bound of its product, e_a + e_b + log2(K) (steps are topological)
+      std::vector<int> mag(P.nodes.size(), 0);
       for (size_t x = 0; x < P.nodes.size(); ++x) {
         float a;
         std::memcpy(&a, &h[x], 4);
         TN_CHECK(std::isfinite(a), TN_ERR_NUMERIC, "calibration found a non-finite value");
         int e = 0;
-        if (a > 0) std::frexp(a, &e);
+        if (a > 0) {
+          std::frexp(a, &e);
+        } else if (!P.nodes[x].leaf) {
+          const Step& S = P.steps[x - P.n_leaves];
+          e = mag[S.a] + mag[S.b] + ilog2(std::max<int64_t>(S.gp.K, 1));
+        }
+        mag[x] = e;
         P.nodes[x].exp2 = P.nodes[x].kind == KIND_C64 ? 0 : e;
       }
     } catch (...) {
