@@ -491,7 +491,8 @@ __device__ __forceinline__ __nv_bfloat16 neg16(__nv_bfloat16 x) {
 // rounding residual (exact value - 16-bit value) goes to Bx_lo.
 template <class T2, class T, class TIN>
 __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, Runs b_n, int64_t nbt, int64_t N,
-                                int64_t K, int64_t half_pitch, T2* __restrict__ Bx, T2* __restrict__ Bx_lo) {
+                                int64_t K, int64_t half_pitch, T2* __restrict__ Bx, T2* __restrict__ Bx_lo,
+                                float bscale) {
   const int64_t total = nbt * N * half_pitch;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = x % half_pitch;
@@ -500,8 +501,8 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, 
     float re = 0.f, im = 0.f;
     if (k < K) {
       const TIN v = B[run_offset(b_bt, bt) + run_offset(b_k, k) + run_offset(b_n, n)];
-      re = (float)v.x;
-      im = (float)v.y;
+      re = (float)v.x * bscale;  // power of two: exact unless out of range
+      im = (float)v.y * bscale;
     }
     const T hre = T(re), him = T(im);
     T2 r0, r1;
@@ -527,7 +528,7 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, 
 }  // namespace
 
 void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
-                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo) {
+                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo, float bscale) {
   const int64_t half_pitch = (2 * K + BK - 1) / BK * BK / 2;
   const int64_t total = nbt * N * half_pitch;
   if (total <= 0) return;
@@ -535,18 +536,18 @@ void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Run
   if (bf16) {
     if (in_c64)
       expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2><<<blocks, 256, 0, s>>>(
-          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo);
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo, bscale);
     else
       expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162><<<blocks, 256, 0, s>>>(
           (const __nv_bfloat162*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
-          (__nv_bfloat162*)Bx_lo);
+          (__nv_bfloat162*)Bx_lo, bscale);
   } else {
     if (in_c64)
       expand_b_kernel<__half2, __half, float2><<<blocks, 256, 0, s>>>(
-          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
     else
       expand_b_kernel<__half2, __half, __half2><<<blocks, 256, 0, s>>>(
-          (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo);
+          (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
   }
 }
 

@@ -454,8 +454,9 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
   const int64_t lo_off = NC.elems * 4;  // hi + lo storage: lo follows hi
   const double flops = 8.0 * S.cost;
   const double bytes = (double)(node_bytes(P, S.a, M.c64) + node_bytes(P, S.b, M.c64) + node_bytes(P, S.c, M.c64));
-  const float scale =
-      M.c64 ? 1.0f : ldexpf(1.0f, P.nodes[S.a].exp2 + P.nodes[S.b].exp2 - P.nodes[S.c].exp2);
+  // stored = true * 2^-exp2; the tensor-core B operand is scaled by 2^-bexp as it is expanded
+  const int e_in = S.tc ? P.nodes[S.tc_swap ? S.b : S.a].exp2 + S.bexp : P.nodes[S.a].exp2 + P.nodes[S.b].exp2;
+  const float scale = M.c64 ? 1.0f : ldexpf(1.0f, e_in - P.nodes[S.c].exp2);
   if (M.c64) {
     GemmParams g = S.gp;
     g.A = X.base(S.a);
@@ -475,7 +476,7 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     TN_CHECK(NA.kind == P.skind && NA.hilo == S.hilo, TN_ERR_INVALID_ARG, "internal: tensor-core operand storage");
     R.begin(4, 0, (double)node_bytes(P, r.b_node, false) + (double)bx_bytes * (S.hilo ? 2 : 1));
     launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s,
-                    b_c64, bx_lo);
+                    b_c64, bx_lo, ldexpf(1.0f, -S.bexp));
     R.end();
     TcGemmParams tp{};
     tp.nbt = S.gp.nbt;
@@ -885,6 +886,8 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
         mag[x] = e;
         P.nodes[x].exp2 = P.nodes[x].kind == KIND_C64 ? 0 : e;
       }
+      for (auto& S : P.steps)
+        if (S.tc) S.bexp = mag[S.tc_swap ? S.a : S.b];
     } catch (...) {
       cudaStreamSynchronize(stream);
       cleanup();

@@ -38,6 +38,7 @@ struct Step {
   bool tc = false;                     // tensor-core GEMM in reduced precision
   bool tc_swap = false;                // tensor-core A operand is node b (else node a)
   bool hilo = false;                   // split-precision product (A, B as hi + lo)
+  int bexp = 0;                        // the expanded operand is scaled by 2^-bexp into 16 bits
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network
 };

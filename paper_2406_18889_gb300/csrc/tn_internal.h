@@ -161,7 +161,8 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
 // (in_c64) or 16-bit complex into its real 2x2 form; with Bx_lo non-null also
 // the rounding residual of every entry
 void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
-                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr);
+                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr,
+                     float bscale = 1.0f);
 Runs single_run(int64_t extent, int64_t stride);
 RunDecode decode_of(const Runs& bt, const Runs& m, const Runs& n);
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K);
