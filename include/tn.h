@@ -280,9 +280,10 @@ tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* slice_ids, i
  * Self-test of the tensor-core GEMM on this device: random complex operands
  * in fp16 (prec = TN_PREC_FP16) or bf16 (TN_PREC_BF16), A [nbt][M][K] and
  * B [nbt][K][N] (complex extents), multiplied by the tcgen05 kernel (after
- * expanding B to its real 2x2 form) and by a plain FP32 CUDA-core reference
- * from the same 16-bit inputs.  *max_rel_err = max |C_tc - C_ref| /
- * max |C_ref|.  Allocates and frees its own buffers; synchronises `stream`.
+ * expanding B to its real 2x2 form) in both of its forms -- one CTA per tile,
+ * and two-CTA clusters sharing B tiles by TMA multicast -- and by a plain FP32
+ * CUDA-core reference from the same 16-bit inputs.  *max_rel_err = max over
+ * both forms of max |C_tc - C_ref| / max |C_ref|.  Allocates and frees its own buffers; synchronises `stream`.
  * Returns TN_ERR_TIMEOUT if a bounded device wait gave up.
  */
 tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int32_t prec, uint64_t seed,

@@ -85,6 +85,26 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* ba
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+// the same load delivered to every CTA of the cluster in `mask` (same smem
+// offset, each CTA's own mbarrier at the same offset)
+__device__ __forceinline__ void tma_load_3d_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (SBO), descriptor version 1 (tcgen05)
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -144,7 +164,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // then m tile, then batch).  The TMEM accumulator is double-buffered (2 x BN
 // columns): the MMA thread fills buffer (i & 1) for the CTA's i-th tile while
 // the epilogue drains the other; tfull/tempty hand the buffers back and forth.
-template <int BN, bool BF16, bool HILO, bool STAGE>
+// C2: a cluster of two CTAs takes two adjacent m tiles of one n tile; each CTA
+// loads its own A tile and one half of the shared B tile, multicast to both,
+// so every SM reads a third less from L2 per k step.  A stage is refilled only
+// after both CTAs' MMAs released it (their commits arrive on both CTAs'
+// `empty` barriers).
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
@@ -167,12 +192,17 @@ __global__ void __launch_bounds__(192, 1)
   const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
   const int k_tiles = HILO ? 3 * k_tiles1 : k_tiles1;
   const int64_t n_n = (2 * p.N + BN - 1) / BN, n_m = (p.M + BM - 1) / BM;
-  const int64_t tiles = p.nbt * n_m * n_n;
+  // work units: single tiles, or (C2) pairs of m tiles sharing an n tile
+  const int64_t n_mu = C2 ? (n_m + 1) / 2 : n_m;
+  const int64_t tiles = p.nbt * n_mu * n_n;
+  const int rank = C2 ? (int)cluster_rank() : 0;
+  const int64_t unit0 = C2 ? blockIdx.x / 2 : blockIdx.x;
+  const int64_t ustride = C2 ? gridDim.x / 2 : gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], C2 ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -189,6 +219,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (C2) cluster_sync_all();  // the peer's barriers are initialised before any multicast
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -196,8 +227,9 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       int64_t g = 0;  // ring position over all of this CTA's k tiles
       bool stop = false;
-      for (int64_t t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
-        const int n_tile = (int)(t % n_n), m_tile = (int)((t / n_n) % n_m), bt = (int)(t / (n_n * n_m));
+      for (int64_t t = unit0; t < tiles && !stop; t += ustride) {
+        const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
+        const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
         for (int kt = 0; kt < k_tiles; ++kt, ++g) {
           const int s = (int)(g % S);
           const uint32_t use = (uint32_t)(g / S);
@@ -209,7 +241,11 @@ __global__ void __launch_bounds__(192, 1)
           const int kx = (kt - pass * k_tiles1) * BK;
           mbar_expect_tx(&full[s], (uint32_t)((BM + BN) * BK * 2));
           tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + s * BM * BK * 2, kx, m_tile * BM, bt);
-          tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
+          if (C2)
+            tma_load_3d_mc(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2 + rank * (BN / 2) * BK * 2, kx,
+                           n_tile * BN + rank * (BN / 2), bt, (uint16_t)0x3);
+          else
+            tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
         }
       }
       // drain: every issued load must have landed before the CTA can exit
@@ -225,7 +261,7 @@ __global__ void __launch_bounds__(192, 1)
       int64_t g = 0;
       int64_t local = 0;
       bool stop = false;
-      for (int64_t t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++local) {
+      for (int64_t t = unit0; t < tiles && !stop; t += ustride, ++local) {
         const int b = (int)(local & 1);
         const uint32_t u = (uint32_t)(local >> 1);
         if (local >= 2 && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) break;
@@ -252,9 +288,16 @@ __global__ void __launch_bounds__(192, 1)
                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                 : "memory");
           }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&empty[s]))
-                       : "memory");
+          if (C2)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                    smem_u32(&empty[s])),
+                "h"((uint16_t)0x3)
+                : "memory");
+          else
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
         }
         // tfull[b] completes when this tile's MMAs (and all earlier ones) finish
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -274,8 +317,9 @@ __global__ void __launch_bounds__(192, 1)
     const int et = threadIdx.x - 64;  // 0..127
     const int quarter = warp & 3;
     int64_t local = 0;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
-      const int n_tile = (int)(t % n_n), m_tile = (int)((t / n_n) % n_m), bt = (int)(t / (n_n * n_m));
+    for (int64_t t = unit0; t < tiles; t += ustride, ++local) {
+      const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
+      const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
       const int b = (int)(local & 1);
       const uint32_t u = (uint32_t)(local >> 1);
       const int64_t nbase = (int64_t)n_tile * BN / 2;
@@ -346,6 +390,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (C2) cluster_sync_all();  // no CTA leaves while its peer may still multicast into it
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
@@ -381,19 +426,44 @@ void make_map(CUtensorMap* map, const void* base, bool bf16, uint64_t inner, uin
   TN_CHECK(r == CUDA_SUCCESS, TN_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2>
+void launch_bn5(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+                const TcGemmParams& p, cudaStream_t s) {
+  const size_t sm = smem_bytes<BN, STAGE>();
+  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2>;
+  static bool attr = false;
+  if (!attr) {
+    TN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  const int64_t n_m = (p.M + BM - 1) / BM, n_n = (2 * p.N + BN - 1) / BN;
+  if (!C2) {
+    const unsigned grid = (unsigned)std::min<int64_t>(n_m * n_n * p.nbt, 152);
+    kern<<<grid, 192, sm, s>>>(ma, ma2, mb, mb2, p);
+    return;
+  }
+  const int64_t pairs = ((n_m + 1) / 2) * n_n * p.nbt;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(pairs, 76)));
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  TN_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, ma2, mb, mb2, p));
+}
 template <int BN, bool BF16, bool HILO, bool STAGE>
 void launch_bn4(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
-  const size_t sm = smem_bytes<BN, STAGE>();
-  static bool attr = false;
-  if (!attr) {
-    TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, BF16, HILO, STAGE>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
-  const int64_t tiles = ((2 * p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM) * p.nbt;
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152);
-  tc_gemm_kernel<BN, BF16, HILO, STAGE><<<grid, 192, sm, s>>>(ma, ma2, mb, mb2, p);
+  if (p.cluster2)
+    launch_bn5<BN, BF16, HILO, STAGE, true>(ma, ma2, mb, mb2, p, s);
+  else
+    launch_bn5<BN, BF16, HILO, STAGE, false>(ma, ma2, mb, mb2, p, s);
 }
 template <int BN, bool BF16, bool HILO>
 void launch_bn(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
@@ -437,13 +507,13 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
   CUtensorMap ma, ma2, mb, mb2;
   const uint64_t a_row = (uint64_t)sa_m * 4, a_bt = p.nbt > 1 ? (uint64_t)sa_bt * 4 : a_row * (uint64_t)p.M;
   make_map(&ma, A, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row, (a_bt + 15) / 16 * 16, BM);
-  make_map(&mb, Bx, bf16, pitch, (uint64_t)(2 * p.N), (uint64_t)p.nbt, pitch * 2, pitch * 2 * 2 * p.N,
-           (uint32_t)bn);
+  const uint32_t b_box = (uint32_t)(p.cluster2 ? bn / 2 : bn);
+  make_map(&mb, Bx, bf16, pitch, (uint64_t)(2 * p.N), (uint64_t)p.nbt, pitch * 2, pitch * 2 * 2 * p.N, b_box);
   if (hilo) {
     make_map(&ma2, A_lo, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row, (a_bt + 15) / 16 * 16,
              BM);
     make_map(&mb2, Bx_lo, bf16, pitch, (uint64_t)(2 * p.N), (uint64_t)p.nbt, pitch * 2, pitch * 2 * 2 * p.N,
-             (uint32_t)bn);
+             b_box);
   } else {
     ma2 = ma;
     mb2 = mb;
@@ -647,12 +717,19 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
     p.scale = 1.0f;
     p.err = d_err;
     p.bn = tc_gemm_bn(N);
+    // both variants: one CTA per tile, and two-CTA clusters sharing B by multicast;
+    // the second overwrites the first, then is compared; the first is compared below
+    p.cluster2 = 0;
     launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
     if (bf16)
       ref_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>((const __nv_bfloat162*)A, (const __nv_bfloat162*)B,
                                                      (float2*)R, nbt, M, N, K);
     else
       ref_kernel<__half2><<<1024, 256, 0, s>>>((const __half2*)A, (const __half2*)B, (float2*)R, nbt, M, N, K);
+    diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
+    TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
+    p.cluster2 = 1;
+    launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
     diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
     unsigned h[2] = {0, 0};
     TN_CUDA(cudaMemcpyAsync(h, mx, 8, cudaMemcpyDeviceToHost, s));

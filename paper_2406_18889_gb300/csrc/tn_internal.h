@@ -122,6 +122,7 @@ struct TcGemmParams {
   int* err;                   // device flag raised when a bounded wait times out
   int bn;                     // real-column tile (32, 64, 128 or 256)
   int stage_n;                // write tiles out along n (n is the output's contiguous index)
+  int cluster2;               // two-CTA clusters sharing B tiles by TMA multicast
 };
 
 // ------------------------------------------------------------ launchers
