@@ -124,15 +124,18 @@ __host__ __device__ constexpr uint32_t make_idesc(int n, bool bf16) {
 
 // epilogue staging: per warp 32 rows x 16 complex (padded) + 32 row offsets
 constexpr int kStagePitch = 17;
-constexpr size_t kStageBytes = 4 * 32 * kStagePitch * 8 + 4 * 32 * 8;
+constexpr int kEpiWarps = 8;  // two warps per TMEM lane quarter, each taking half the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr size_t kStageBytes = kEpiWarps * 32 * kStagePitch * 8 + kEpiWarps * 32 * 8;
 
-template <int BN>
+template <int BN, bool STAGE = false>
 __host__ __device__ constexpr int stages_for() {
-  return BN >= 256 ? 4 : BN >= 128 ? 6 : 8;
+  return BN >= 256 ? (STAGE ? 3 : 4) : BN >= 128 ? 6 : 8;
 }
 template <int BN, bool STAGE>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8 + (STAGE ? kStageBytes : 0);
+  return 1024 + (size_t)stages_for<BN, STAGE>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8 +
+         (STAGE ? kStageBytes : 0);
 }
 
 // one complex output element, converted to the output kind (hi + lo when split)
@@ -170,11 +173,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // after both CTAs' MMAs released it (their commits arrive on both CTAs'
 // `empty` barriers).
 template <int BN, bool BF16, bool HILO, bool STAGE, bool C2>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
                    TcGemmParams p) {
-  constexpr int S = stages_for<BN>();
+  constexpr int S = stages_for<BN, STAGE>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -185,8 +188,8 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int64_t* n_off = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 256);  // [BN / 2]
-  float2* stage_buf = reinterpret_cast<float2*>(n_off + BN / 2);                         // [4][32][pitch]
-  int64_t* row_base = reinterpret_cast<int64_t*>(stage_buf + 4 * 32 * kStagePitch);      // [4][32]
+  float2* stage_buf = reinterpret_cast<float2*>(n_off + BN / 2);                         // [warps][32][pitch]
+  int64_t* row_base = reinterpret_cast<int64_t*>(stage_buf + kEpiWarps * 32 * kStagePitch);  // [warps][32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+      mbar_init(&tempty[b], kEpiWarps);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -314,8 +317,10 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else {
     // epilogue warps 2..5
-    const int et = threadIdx.x - 64;  // 0..127
-    const int quarter = warp & 3;
+    const int et = threadIdx.x - 64;  // 0..32*kEpiWarps-1
+    const int quarter = warp & 3;      // TMEM lanes 32*quarter.. (warp w may read lanes 32*(w%4)..)
+    const int ew = warp - 2;           // epilogue warp index
+    const int col_half = ew / 4;       // columns [col_half*BN/2, (col_half+1)*BN/2)
     int64_t local = 0;
     for (int64_t t = unit0; t < tiles; t += ustride, ++local) {
       const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
@@ -323,23 +328,27 @@ __global__ void __launch_bounds__(192, 1)
       const int b = (int)(local & 1);
       const uint32_t u = (uint32_t)(local >> 1);
       const int64_t nbase = (int64_t)n_tile * BN / 2;
-      asm volatile("bar.sync 1, 128;" ::: "memory");  // previous tile's table no longer read
-      for (int j = et; j < BN / 2; j += 128) n_off[j] = nbase + j < p.N ? run_offset(p.c_n, nbase + j) : 0;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");  // previous table no longer read
+      for (int j = et; j < BN / 2; j += 32 * kEpiWarps) n_off[j] = nbase + j < p.N ? run_offset(p.c_n, nbase + j) : 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
       // every epilogue thread runs every iteration (the named barriers above need all
-      // 128); after a timed-out wait (warp-uniform) the tile's reads and stores are skipped
+      // of them); after a timed-out wait (warp-uniform) the tile's reads and stores are skipped
       const bool ok = __all_sync(0xffffffffu, wait_bounded(&tfull[b], u & 1, p.err));
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t m = (int64_t)m_tile * BM + quarter * 32 + lane;
       const int64_t base = m < p.M ? run_offset(p.c_bt, bt) + run_offset(p.c_m, m) : 0;
-      float2* stg = stage_buf + quarter * 32 * kStagePitch;
-      int64_t* rb = row_base + quarter * 32;
+      float2* stg = stage_buf + ew * 32 * kStagePitch;
+      int64_t* rb = row_base + ew * 32;
       if (STAGE) {
         rb[lane] = base;
         __syncwarp();
       }
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN && ok; c0 += 32) {
+      // column range of this warp (32-column loads): halves for BN >= 64, else all in half 0
+      constexpr int kHalf = BN >= 64 ? BN / 2 : BN;
+      const int c_beg = BN >= 64 ? col_half * kHalf : (col_half ? BN : 0);
+      const int c_end = BN >= 64 ? c_beg + kHalf : BN;
+      for (int c0 = c_beg; c0 < c_end && ok; c0 += 32) {
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
         asm volatile(
@@ -439,13 +448,13 @@ void launch_bn5(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap
   const int64_t n_m = (p.M + BM - 1) / BM, n_n = (2 * p.N + BN - 1) / BN;
   if (!C2) {
     const unsigned grid = (unsigned)std::min<int64_t>(n_m * n_n * p.nbt, 152);
-    kern<<<grid, 192, sm, s>>>(ma, ma2, mb, mb2, p);
+    kern<<<grid, kThreads, sm, s>>>(ma, ma2, mb, mb2, p);
     return;
   }
   const int64_t pairs = ((n_m + 1) / 2) * n_n * p.nbt;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(pairs, 76)));
-  cfg.blockDim = dim3(192);
+  cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -500,8 +509,8 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     // stage the epilogue when n is the output's more contiguous index
     const int64_t big = int64_t(1) << 62;
     const int64_t sn = p.c_n.n > 0 ? p.c_n.st[0] : big, sm = p.c_m.n > 0 ? p.c_m.st[0] : big;
-    // only for write-bound tiles (one or two k tiles); deeper tiles hide the per-row stores
-    p.stage_n = (sn < sm && 2 * p.K <= 2 * BK) ? 1 : 0;
+    // only for write-heavy tiles (up to four k tiles); deeper tiles hide the per-row stores
+    p.stage_n = (sn < sm && 2 * p.K <= 4 * BK) ? 1 : 0;
   }
   const uint64_t pitch = (uint64_t)((2 * p.K + BK - 1) / BK * BK);
   CUtensorMap ma, ma2, mb, mb2;
