@@ -128,9 +128,13 @@ constexpr int kEpiWarps = 8;  // two warps per TMEM lane quarter, each taking ha
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr size_t kStageBytes = kEpiWarps * 32 * kStagePitch * 8 + kEpiWarps * 32 * 8;
 
+// ring depth: as many stages as fit in 227 KB of shared memory next to the
+// barriers, the column-offset table and (STAGE) the epilogue staging, at most 8
 template <int BN, bool STAGE = false>
 __host__ __device__ constexpr int stages_for() {
-  return BN >= 256 ? (STAGE ? 3 : 4) : BN >= 128 ? 6 : 8;
+  constexpr long budget = 232448 - 1024 - 256 - (long)BN / 2 * 8 - (STAGE ? (long)kStageBytes : 0L) - 512;
+  constexpr long per = (long)(BM + BN) * BK * 2;
+  return budget / per > 8 ? 8 : (int)(budget / per);
 }
 template <int BN, bool STAGE>
 __host__ __device__ constexpr size_t smem_bytes() {
