@@ -183,7 +183,16 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
   const TI* __restrict__ Bm = (const TI*)p.B;
   TO* __restrict__ C = (TO*)p.C;
   const I total = (I)(p.nbt * p.M * p.N);
-  const I K = (I)p.K;
+  const int K = (int)p.K;
+  // the contracted offsets of K <= 4 are the same for every output: tabulate them
+  I ak[4] = {0, 0, 0, 0}, bk[4] = {0, 0, 0, 0};
+  const bool small_k = K <= 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k < K) {
+      ak[k] = run_off<I>(p.a_k, (I)k);
+      bk[k] = run_off<I>(p.b_k, (I)k);
+    }
   // four consecutive outputs per thread when C's fastest run (pos 0) spans >= 4
   // elements: they differ only in that run's digit, i.e. in one group's index
   const bool vec = p.c_dec.n > 0 && p.c_dec.pos[0] == 0 && p.c_dec.lg[0] >= 2 && (total & 3) == 0;
@@ -191,16 +200,30 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
   const I step0 = I(1) << p.c_dec.shift[0];
   const I per = vec ? 4 : 1;
   for (I x = (blockIdx.x * (I)blockDim.x + threadIdx.x) * per; x < total; x += (I)gridDim.x * blockDim.x * per) {
-    I idx[3] = {0, 0, 0};
-    for (int e = 0; e < p.c_dec.n; ++e)
-      idx[p.c_dec.grp[e]] |= ((x >> p.c_dec.pos[e]) & ((I(1) << p.c_dec.lg[e]) - 1)) << p.c_dec.shift[e];
+    I i0 = 0, i1 = 0, i2 = 0;  // (bt, m, n) in registers (no dynamically indexed array)
+    for (int e = 0; e < p.c_dec.n; ++e) {
+      const I d = ((x >> p.c_dec.pos[e]) & ((I(1) << p.c_dec.lg[e]) - 1)) << p.c_dec.shift[e];
+      const int g = p.c_dec.grp[e];
+      i0 |= g == 0 ? d : I(0);
+      i1 |= g == 1 ? d : I(0);
+      i2 |= g == 2 ? d : I(0);
+    }
     for (I v = 0; v < per; ++v) {
-      const TI* a = A + run_off<I>(p.a_bt, idx[0]) + run_off<I>(p.a_m, idx[1]);
-      const TI* b = Bm + run_off<I>(p.b_bt, idx[0]) + run_off<I>(p.b_n, idx[2]);
+      const TI* a = A + run_off<I>(p.a_bt, i0) + run_off<I>(p.a_m, i1);
+      const TI* b = Bm + run_off<I>(p.b_bt, i0) + run_off<I>(p.b_n, i2);
       float2 acc = make_float2(0.f, 0.f);
-      for (I k = 0; k < K; ++k) cmac(acc, In::ld(a[run_off<I>(p.a_k, k)]), In::ld(b[run_off<I>(p.b_k, k)]));
+      if (small_k) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < K) cmac(acc, In::ld(a[ak[k]]), In::ld(b[bk[k]]));
+      } else {
+        for (int k = 0; k < K; ++k)
+          cmac(acc, In::ld(a[run_off<I>(p.a_k, (I)k)]), In::ld(b[run_off<I>(p.b_k, (I)k)]));
+      }
       store_out<Out>(C, (TO*)p.C2, (int64_t)(x + v), make_float2(acc.x * scale, acc.y * scale), hilo);
-      idx[g0] += step0;
+      i0 += g0 == 0 ? step0 : I(0);
+      i1 += g0 == 1 ? step0 : I(0);
+      i2 += g0 == 2 ? step0 : I(0);
     }
   }
 }

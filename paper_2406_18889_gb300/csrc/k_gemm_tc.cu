@@ -347,11 +347,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         rb[lane] = base;
         __syncwarp();
       }
-#pragma unroll 1
       // column range of this warp (32-column loads): halves for BN >= 64, else all in half 0
       constexpr int kHalf = BN >= 64 ? BN / 2 : BN;
       const int c_beg = BN >= 64 ? col_half * kHalf : (col_half ? BN : 0);
       const int c_end = BN >= 64 ? c_beg + kHalf : BN;
+#pragma unroll 1
       for (int c0 = c_beg; c0 < c_end && ok; c0 += 32) {
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
@@ -572,18 +572,30 @@ __device__ __forceinline__ __nv_bfloat16 neg16(__nv_bfloat16 x) {
 // Bx[bt][2n+0][2k..2k+1] = (Re B, -Im B)[k][n], Bx[bt][2n+1][2k..2k+1] = (Im B, Re B)[k][n];
 // columns past 2K up to the pitch are zero.  With Bx_lo, every entry's
 // rounding residual (exact value - 16-bit value) goes to Bx_lo.
-template <class T2, class T, class TIN>
+template <class I>
+__device__ __forceinline__ I run_off_i(const Runs& R, I i) {
+  I o = 0;
+  for (int r = 0; r < R.n; ++r) {
+    o += (i & ((I(1) << R.lg[r]) - 1)) * (I)R.st[r];
+    i >>= R.lg[r];
+  }
+  return o;
+}
+
+// I: index type (32-bit when B and Bx have fewer than 2^31 elements)
+template <class T2, class T, class TIN, class I>
 __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, Runs b_n, int64_t nbt, int64_t N,
                                 int64_t K, int64_t half_pitch, T2* __restrict__ Bx, T2* __restrict__ Bx_lo,
                                 float bscale) {
-  const int64_t total = nbt * N * half_pitch;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = x % half_pitch;
-    const int64_t t = x / half_pitch;
-    const int64_t n = t % N, bt = t / N;
+  const I total = (I)(nbt * N * half_pitch);
+  const I hp = (I)half_pitch, NN = (I)N, KK = (I)K;
+  for (I x = blockIdx.x * (I)blockDim.x + threadIdx.x; x < total; x += (I)gridDim.x * blockDim.x) {
+    const I k = x % hp;
+    const I t = x / hp;
+    const I n = t % NN, bt = t / NN;
     float re = 0.f, im = 0.f;
-    if (k < K) {
-      const TIN v = B[run_offset(b_bt, bt) + run_offset(b_k, k) + run_offset(b_n, n)];
+    if (k < KK) {
+      const TIN v = B[run_off_i<I>(b_bt, bt) + run_off_i<I>(b_k, k) + run_off_i<I>(b_n, n)];
       re = (float)v.x * bscale;  // power of two: exact unless out of range
       im = (float)v.y * bscale;
     }
@@ -593,7 +605,7 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, 
     r0.y = neg16<T>(him);
     r1.x = him;
     r1.y = hre;
-    const int64_t row0 = (bt * 2 * N + 2 * n) * half_pitch;
+    const int64_t row0 = ((int64_t)bt * 2 * N + 2 * (int64_t)n) * half_pitch;
     Bx[row0 + k] = r0;
     Bx[row0 + half_pitch + k] = r1;
     if (Bx_lo) {
@@ -608,6 +620,29 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, 
     }
   }
 }
+
+template <class I>
+void expand_typed(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
+                  int64_t K, int64_t half_pitch, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo,
+                  float bscale, unsigned blocks) {
+  if (bf16) {
+    if (in_c64)
+      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2, I><<<blocks, 256, 0, s>>>(
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo,
+          bscale);
+    else
+      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162, I><<<blocks, 256, 0, s>>>(
+          (const __nv_bfloat162*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
+          (__nv_bfloat162*)Bx_lo, bscale);
+  } else {
+    if (in_c64)
+      expand_b_kernel<__half2, __half, float2, I><<<blocks, 256, 0, s>>>(
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
+    else
+      expand_b_kernel<__half2, __half, __half2, I><<<blocks, 256, 0, s>>>(
+          (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
+  }
+}
 }  // namespace
 
 void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
@@ -616,22 +651,11 @@ void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Run
   const int64_t total = nbt * N * half_pitch;
   if (total <= 0) return;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  if (bf16) {
-    if (in_c64)
-      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2><<<blocks, 256, 0, s>>>(
-          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo, bscale);
-    else
-      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162><<<blocks, 256, 0, s>>>(
-          (const __nv_bfloat162*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
-          (__nv_bfloat162*)Bx_lo, bscale);
-  } else {
-    if (in_c64)
-      expand_b_kernel<__half2, __half, float2><<<blocks, 256, 0, s>>>(
-          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
-    else
-      expand_b_kernel<__half2, __half, __half2><<<blocks, 256, 0, s>>>(
-          (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
-  }
+  // 32-bit indices when every index and offset of B and the expanded copy fits
+  if (2 * total < (int64_t(1) << 31) && nbt * N * K < (int64_t(1) << 30))
+    expand_typed<int32_t>(B, b_bt, b_k, b_n, nbt, N, K, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks);
+  else
+    expand_typed<int64_t>(B, b_bt, b_k, b_n, nbt, N, K, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks);
 }
 
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K) {
