@@ -16,7 +16,20 @@
 //    offsets once per TK-deep slice); operands are staged through shared
 //    memory with loads coalesced along whichever index is contiguous; each
 //    thread keeps RM x RN complex accumulators.
-//  * direct: one thread per output element, for shapes too small for a tile.
+//  * small-K: for K <= 4 (outer-product-like steps, bound by writing C).  A
+//    CTA owns 2^P consecutive outputs of C's memory order; the A and B
+//    entries those outputs use are staged in shared memory once per tile,
+//    and every position map involved (output position -> A entry, B entry,
+//    destination offset) is linear over the position's bits, so two small
+//    per-CTA tables give each thread its operands and destination.  The
+//    destination is C itself, or -- when the result is the expanded operand
+//    of a tensor-core step -- that operand's real 2x2 form, written in place
+//    of a separate expansion pass.
+//  * direct: one thread per output element, for the remaining shapes too
+//    small for a tile.
+#include <algorithm>
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -228,6 +241,149 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
   }
 }
 
+// ------------------------------------------------------------------ small K
+constexpr int kSkMaxTileBits = 12;  // outputs per tile <= 4096
+constexpr int kSkMaxStage = 2048;   // staged entries per operand (16 KB)
+
+struct SmallK {
+  const float2* A;
+  const float2* B;
+  void* C;
+  void* C2;
+  int K, lgK;    // contracted extent (1, 2 or 4)
+  int nbits;     // log2 of the outputs
+  int P;         // log2 of the outputs per tile
+  int na, nb;    // bits of the staged A / B index
+  int8_t a_rank[kSkMaxTileBits], b_rank[kSkMaxTileBits];  // tile bit -> staged-index bit (-1: none)
+  int64_t a_wt[kSkMaxTileBits], b_wt[kSkMaxTileBits];     // staged-index bit -> operand offset
+  int64_t a_w[kMaxBits], b_w[kMaxBits], o_w[kMaxBits];    // output-position bit -> offsets
+  int64_t ak[4], bk[4];                                   // contracted-index offsets
+  int64_t hp;    // expanded destination: row pitch in 16-bit pairs
+  float scale;
+};
+
+// v into the expanded form at row pair (o, o + hp): [[Re, -Im], [Im, Re]];
+// with Xlo also the rounding residual of every entry
+template <class H>
+__device__ __forceinline__ void store_expanded(typename H::T* X, typename H::T* Xlo, int64_t o, int64_t hp,
+                                               float2 v) {
+  X[o] = H::st(make_float2(v.x, -v.y));  // round-to-nearest is odd-symmetric: this is -(rounded Im)
+  X[o + hp] = H::st(make_float2(v.y, v.x));
+  if (Xlo) {
+    const float2 h = H::ld(H::st(v));
+    const float2 l = make_float2(v.x - h.x, v.y - h.y);
+    Xlo[o] = H::st(make_float2(l.x, -l.y));
+    Xlo[o + hp] = H::st(make_float2(l.y, l.x));
+  }
+}
+
+// MODE 0: C[o] = result (Out storage, hi + lo when `hilo`); MODE 1: expanded destination
+template <class Out, int MODE>
+__global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
+  using TO = typename Out::T;
+  extern __shared__ float2 staged[];
+  __shared__ uint32_t sel_lo[256], sel_hi[16];
+  __shared__ int64_t off_lo[256], off_hi[16];
+  float2* As = staged;
+  float2* Bs = staged + (p.K << p.na);
+  // tables of the tile's low 8 and high 4 position bits (linear maps: OR / sum of parts)
+  {
+    const int j = threadIdx.x;
+    uint32_t sel = 0;
+    int64_t off = 0;
+    for (int b = 0; b < 8 && b < p.P; ++b)
+      if ((j >> b) & 1) {
+        if (p.a_rank[b] >= 0) sel |= 1u << p.a_rank[b];
+        if (p.b_rank[b] >= 0) sel |= 1u << (16 + p.b_rank[b]);
+        off += p.o_w[b];
+      }
+    sel_lo[j] = sel;
+    off_lo[j] = off;
+    if (j < 16) {
+      sel = 0;
+      off = 0;
+      for (int b = 8; b < kSkMaxTileBits && b < p.P; ++b)
+        if ((j >> (b - 8)) & 1) {
+          if (p.a_rank[b] >= 0) sel |= 1u << p.a_rank[b];
+          if (p.b_rank[b] >= 0) sel |= 1u << (16 + p.b_rank[b]);
+          off += p.o_w[b];
+        }
+      sel_hi[j] = sel;
+      off_hi[j] = off;
+    }
+  }
+  const int64_t ntiles = int64_t(1) << (p.nbits - p.P);
+  const int tile_n = 1 << p.P;
+  const int na_n = p.K << p.na, nb_n = p.K << p.nb;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int64_t a0 = 0, b0 = 0, o0 = 0;
+    for (int j = p.P; j < p.nbits; ++j)
+      if ((t >> (j - p.P)) & 1) {
+        a0 += p.a_w[j];
+        b0 += p.b_w[j];
+        o0 += p.o_w[j];
+      }
+    __syncthreads();  // tables written; the previous tile's staged entries consumed
+    for (int i = threadIdx.x; i < na_n; i += blockDim.x) {
+      const int u = i >> p.lgK;
+      int64_t o = a0 + p.ak[i & (p.K - 1)];
+      for (int b = 0; b < p.na; ++b)
+        if ((u >> b) & 1) o += p.a_wt[b];
+      As[i] = p.A[o];
+    }
+    for (int i = threadIdx.x; i < nb_n; i += blockDim.x) {
+      const int u = i >> p.lgK;
+      int64_t o = b0 + p.bk[i & (p.K - 1)];
+      for (int b = 0; b < p.nb; ++b)
+        if ((u >> b) & 1) o += p.b_wt[b];
+      Bs[i] = p.B[o];
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < tile_n; x += blockDim.x) {
+      const uint32_t sel = sel_lo[x & 255] | sel_hi[x >> 8];
+      const float2* a = As + ((sel & 0xffffu) << p.lgK);
+      const float2* b = Bs + ((sel >> 16) << p.lgK);
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < p.K) cmac(acc, a[k], b[k]);
+      acc.x *= p.scale;
+      acc.y *= p.scale;
+      const int64_t o = o0 + off_lo[x & 255] + off_hi[x >> 8];
+      if constexpr (MODE == 0)
+        store_out<Out>((TO*)p.C, (TO*)p.C2, o, acc, hilo);
+      else
+        store_expanded<Out>((TO*)p.C, (TO*)p.C2, o, p.hp, acc);
+    }
+  }
+}
+
+int ilog2_exact(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  TN_CHECK((int64_t(1) << r) == x, TN_ERR_UNSUPPORTED, "extent is not a power of two");
+  return r;
+}
+
+// group and natural bit of every position bit of a dense tensor decoded by d
+// (groups 0..2 with extents ext[]); false when some bit is not covered
+bool position_bits(const RunDecode& d, int nbits, const int64_t ext[3], int8_t* grp, int8_t* nat) {
+  for (int j = 0; j < nbits; ++j) grp[j] = -1;
+  int lg_ext[3];
+  for (int g = 0; g < 3; ++g) lg_ext[g] = ilog2_exact(ext[g]);
+  for (int e = 0; e < d.n; ++e)
+    for (int b = 0; b < d.lg[e]; ++b) {
+      const int pos = d.pos[e] + b, q = d.shift[e] + b;
+      if (pos >= nbits || q >= lg_ext[d.grp[e]]) break;
+      if (grp[pos] >= 0) return false;
+      grp[pos] = d.grp[e];
+      nat[pos] = (int8_t)q;
+    }
+  for (int j = 0; j < nbits; ++j)
+    if (grp[j] < 0) return false;
+  return true;
+}
+
 bool fastest_unit(const Runs& r) { return r.n > 0 && r.st[0] == 1; }
 
 template <int TM, int TN, int TK, int TY, int TX, class In, class Out>
@@ -240,9 +396,106 @@ void launch_tiled(const GemmParams& p, float scale, bool hilo, cudaStream_t s) {
                                                                                              flags);
 }
 
+// Small-K launch; `ex` non-null: the result goes to that expanded operand.
+template <class Out>
+void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, const ExpandedDst* ex) {
+  SmallK p{};
+  p.A = (const float2*)g.A;
+  p.B = (const float2*)g.B;
+  p.K = (int)g.K;
+  p.lgK = ilog2_exact(g.K);
+  TN_CHECK(g.K <= 4, TN_ERR_UNSUPPORTED, "small-K kernel needs K <= 4");
+  const int64_t total = g.nbt * g.M * g.N;
+  p.nbits = ilog2_exact(total);
+  TN_CHECK(p.nbits <= kMaxBits, TN_ERR_UNSUPPORTED, "result too large");
+  int8_t grp[kMaxBits], nat[kMaxBits];
+  const int64_t ext[3] = {g.nbt, g.M, g.N};
+  TN_CHECK(position_bits(g.c_dec, p.nbits, ext, grp, nat), TN_ERR_UNSUPPORTED, "result is not dense");
+  for (int j = 0; j < p.nbits; ++j) {
+    const int64_t bit = int64_t(1) << nat[j];
+    p.a_w[j] = grp[j] == 0 ? run_offset(g.a_bt, bit) : grp[j] == 1 ? run_offset(g.a_m, bit) : 0;
+    p.b_w[j] = grp[j] == 0 ? run_offset(g.b_bt, bit) : grp[j] == 2 ? run_offset(g.b_n, bit) : 0;
+    p.o_w[j] = int64_t(1) << j;
+  }
+  if (ex) {
+    // destination: expanded rows [bt][2N][hp] of the consuming step; this
+    // tensor's position bits decoded through that step's index maps
+    p.hp = expanded_half_pitch(ex->K);
+    TN_CHECK(p.hp == ex->K, TN_ERR_UNSUPPORTED, "expanded destination needs K a multiple of the k tile");
+    TN_CHECK(ex->nbt * ex->N * ex->K == total, TN_ERR_INVALID_ARG, "expanded destination size");
+    int8_t g2[kMaxBits], n2[kMaxBits];
+    const int64_t ext2[3] = {ex->nbt, ex->K, ex->N};
+    TN_CHECK(position_bits(decode_of(ex->b_bt, ex->b_k, ex->b_n), p.nbits, ext2, g2, n2), TN_ERR_UNSUPPORTED,
+             "expanded destination is not dense");
+    for (int j = 0; j < p.nbits; ++j) {
+      const int64_t unit = g2[j] == 0 ? 2 * ex->N * p.hp : g2[j] == 1 ? 1 : 2 * p.hp;
+      p.o_w[j] = unit << n2[j];
+    }
+    p.C = ex->Bx;
+    p.C2 = ex->Bx_lo;
+  } else {
+    p.C = g.C;
+    p.C2 = g.C2;
+  }
+  for (int k = 0; k < 4; ++k) {
+    p.ak[k] = k < p.K ? run_offset(g.a_k, k) : 0;
+    p.bk[k] = k < p.K ? run_offset(g.b_k, k) : 0;
+  }
+  // every offset the kernel forms is a sum over a subset of these non-negative
+  // weights: bound the full sums by the (dense) tensors' sizes
+  {
+    int64_t sa = 0, sb = 0, so = 0, ka = 0, kb = 0;
+    for (int j = 0; j < p.nbits; ++j) {
+      TN_CHECK(p.a_w[j] >= 0 && p.b_w[j] >= 0 && p.o_w[j] >= 0, TN_ERR_UNSUPPORTED, "negative stride");
+      sa += p.a_w[j];
+      sb += p.b_w[j];
+      so += p.o_w[j];
+    }
+    for (int k = 0; k < p.K; ++k) {
+      ka = std::max(ka, p.ak[k]);
+      kb = std::max(kb, p.bk[k]);
+    }
+    const int64_t dst = ex ? ex->nbt * 2 * ex->N * p.hp : total;
+    TN_CHECK(sa + ka < g.nbt * g.M * g.K && sb + kb < g.nbt * g.K * g.N && so + (ex ? p.hp : 0) < dst,
+             TN_ERR_INVALID_ARG, "internal: small-K index maps exceed their tensors");
+  }
+  // the widest tile whose staged A and B entries fit
+  for (p.P = std::min(kSkMaxTileBits, p.nbits); p.P > 0; --p.P) {
+    int na = 0, nb = 0;
+    for (int j = 0; j < p.P; ++j) {
+      na += grp[j] != 2;
+      nb += grp[j] != 1;
+    }
+    if ((p.K << na) <= kSkMaxStage && (p.K << nb) <= kSkMaxStage) break;
+  }
+  p.na = p.nb = 0;
+  for (int j = 0; j < kSkMaxTileBits; ++j) p.a_rank[j] = p.b_rank[j] = -1;
+  for (int j = 0; j < p.P; ++j) {
+    if (grp[j] != 2) {
+      p.a_rank[j] = (int8_t)p.na;
+      p.a_wt[p.na++] = p.a_w[j];
+    }
+    if (grp[j] != 1) {
+      p.b_rank[j] = (int8_t)p.nb;
+      p.b_wt[p.nb++] = p.b_w[j];
+    }
+  }
+  p.scale = scale;
+  const size_t smem = (size_t)((p.K << p.na) + (p.K << p.nb)) * sizeof(float2);
+  const int64_t tiles = int64_t(1) << (p.nbits - p.P);
+  const unsigned blocks = (unsigned)std::min<int64_t>(tiles, 152 * 6);
+  if (ex)
+    gemm_smallk<Out, 1><<<blocks, 256, smem, s>>>(p, hilo);
+  else
+    gemm_smallk<Out, 0><<<blocks, 256, smem, s>>>(p, hilo);
+}
+
 template <class In, class Out>
 void launch_typed(const GemmParams& p, float scale, cudaStream_t s, bool hilo = false) {
   const int64_t outputs = p.nbt * p.M * p.N;
+  if constexpr (std::is_same_v<In, C64>) {
+    if (p.K <= 4) return launch_smallk<Out>(p, scale, s, hilo, nullptr);
+  }
   if (p.K <= 4 || (p.M < 16 && p.N < 16) || outputs * p.K < (1 << 16)) {
     int64_t blocks = std::min<int64_t>((outputs / 4 + 255) / 256 + 1, 152 * 64);
     if (p.elems_max < (int64_t(1) << 31))
@@ -271,8 +524,14 @@ void launch_gemm_c64(const GemmParams& p, int accumulate, cudaStream_t s) {
 
 // in_kind / out_kind: 0 = fp16 complex, 1 = bf16 complex, 2 = fp32 complex;
 // out_hilo: a 16-bit output also stores its rounding residual in p.C2
-void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s, bool out_hilo) {
+void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s, bool out_hilo,
+                      const ExpandedDst* ex) {
   if (p.nbt <= 0 || p.M <= 0 || p.N <= 0) return;
+  if (ex) {
+    TN_CHECK(in_kind == 2 && p.K <= 4, TN_ERR_UNSUPPORTED, "expanded destination needs a complex64 small-K step");
+    if (ex->bf16) return launch_smallk<BF16>(p, scale, s, false, ex);
+    return launch_smallk<F16>(p, scale, s, false, ex);
+  }
   if (in_kind == 2 && out_kind == 2) return launch_typed<C64, C64>(p, scale, s);
   if (in_kind == 2 && out_kind == 0) return launch_typed<C64, F16>(p, scale, s, out_hilo);
   if (in_kind == 2 && out_kind == 1) return launch_typed<C64, BF16>(p, scale, s, out_hilo);

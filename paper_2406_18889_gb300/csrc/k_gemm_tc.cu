@@ -658,6 +658,8 @@ void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Run
     expand_typed<int64_t>(B, b_bt, b_k, b_n, nbt, N, K, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks);
 }
 
+int64_t expanded_half_pitch(int64_t K) { return (2 * K + BK - 1) / BK * BK / 2; }
+
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K) {
   return nbt * 2 * N * ((2 * K + BK - 1) / BK * BK) * 2;
 }

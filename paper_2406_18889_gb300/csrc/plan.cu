@@ -49,6 +49,22 @@ std::vector<int> set_minus(const std::vector<int>& a, const std::vector<int>& b)
 }
 bool contains(const std::vector<int>& v, int e) { return std::find(v.begin(), v.end(), e) != v.end(); }
 
+// Is operand a of step S the one stored [batch][free][contracted] and read
+// as stored by the tensor cores (the other is expanded)?  The larger one; on
+// a tie, the expanded one is preferably the result of a step with K <= 4,
+// which can write the expanded form directly.
+bool small_k_result(const Plan& P, int node) {
+  if (P.nodes[node].leaf) return false;
+  int64_t K = 1;
+  for (int e : P.steps[node - P.n_leaves].k) K *= P.dim[e];
+  return K <= 4;
+}
+bool a_is_big(const Plan& P, const Step& S) {
+  const int64_t ea = P.nodes[S.a].elems, eb = P.nodes[S.b].elems;
+  if (ea != eb) return ea > eb;
+  return !(small_k_result(P, S.a) && !small_k_result(P, S.b));
+}
+
 // edges of `group` in the order they appear in `layout`
 std::vector<int> order_by(const std::vector<int>& group, const std::vector<int>& layout) {
   std::vector<int> r;
@@ -157,7 +173,7 @@ struct Builder {
       S.lc_nat = Lc;
       S.post_perm = false;
       std::vector<int> bt_o = order_by(S.bt, Lc), m_o = order_by(S.m, Lc), n_o = order_by(S.n, Lc);
-      const bool a_big = P.nodes[S.a].elems >= P.nodes[S.b].elems;
+      const bool a_big = a_is_big(P, S);
       std::vector<int> k_o = S.k;
       const int q = producer(a_big ? S.a : S.b);
       if (q >= 0) {
@@ -209,7 +225,7 @@ struct Builder {
     const auto& Lb = P.nodes[S.b].layout;
     const auto& Lc = P.nodes[S.c].layout;
     std::vector<int> bt_o = order_by(S.bt, Lc), m_o = order_by(S.m, Lc), n_o = order_by(S.n, Lc);
-    std::vector<int> k_o = order_by(S.k, P.nodes[S.a].elems >= P.nodes[S.b].elems ? La : Lb);
+    std::vector<int> k_o = order_by(S.k, a_is_big(P, S) ? La : Lb);
     GemmParams& g = S.gp;
     g.nbt = dims_prod(bt_o);
     g.M = dims_prod(m_o);
@@ -367,12 +383,22 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
   for (size_t t = 0; t < P.steps.size(); ++t) {
     const Step& S = P.steps[t];
     if (S.hoisted) continue;
-    M.off[S.c] = ws.alloc(node_bytes(P, S.c, c64));
+    if (!c64 && S.fuse_expand) {
+      // the result is stored only as its consumer's expanded operand
+      const Step& U = P.steps[P.nodes[S.c].consumer];
+      TcRoles r = tc_roles(U);
+      M.off[S.c] = ws.alloc(expanded_b_bytes(U.gp.nbt, r.N, r.K) * (U.hilo ? 2 : 1));
+    } else {
+      M.off[S.c] = ws.alloc(node_bytes(P, S.c, c64));
+    }
     int64_t tmp = -1, bx = -1;
     if (S.post_perm) tmp = M.tmp_off[t] = ws.alloc(node_bytes(P, S.c, c64));
     if (!c64 && S.tc) {
       TcRoles r = tc_roles(S);
-      bx = M.bx_off[t] = ws.alloc(expanded_b_bytes(S.gp.nbt, r.N, r.K) * (S.hilo ? 2 : 1));
+      if (S.b_fused)
+        M.bx_off[t] = M.off[r.b_node];
+      else
+        bx = M.bx_off[t] = ws.alloc(expanded_b_bytes(S.gp.nbt, r.N, r.K) * (S.hilo ? 2 : 1));
     }
     if (tmp >= 0) ws.release(tmp);
     if (bx >= 0) ws.release(bx);
@@ -474,10 +500,12 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     char* bx_lo = S.hilo ? bx + bx_bytes : nullptr;
     const bool b_c64 = P.nodes[r.b_node].kind == KIND_C64;
     TN_CHECK(NA.kind == P.skind && NA.hilo == S.hilo, TN_ERR_INVALID_ARG, "internal: tensor-core operand storage");
-    R.begin(4, 0, (double)node_bytes(P, r.b_node, false) + (double)bx_bytes * (S.hilo ? 2 : 1));
-    launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s,
-                    b_c64, bx_lo, ldexpf(1.0f, -S.bexp));
-    R.end();
+    if (!S.b_fused) {
+      R.begin(4, 0, (double)node_bytes(P, r.b_node, false) + (double)bx_bytes * (S.hilo ? 2 : 1));
+      launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s,
+                      b_c64, bx_lo, ldexpf(1.0f, -S.bexp));
+      R.end();
+    }
     TcGemmParams tp{};
     tp.nbt = S.gp.nbt;
     tp.M = r.M;
@@ -507,9 +535,28 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     g.B = X.base(S.b);
     g.C = out;
     g.C2 = out_hilo ? out + lo_off : nullptr;
-    R.begin(0, flops, bytes);
-    launch_gemm_simt(g, KIND_C64, out_kind, scale, s, out_hilo);
-    R.end();
+    if (S.fuse_expand) {
+      // written as the consumer's expanded operand, scaled by its 2^-bexp
+      const Step& U = P.steps[NC.consumer];
+      TcRoles r = tc_roles(U);
+      ExpandedDst ex{};
+      ex.b_bt = r.b_bt;
+      ex.b_k = r.b_k;
+      ex.b_n = r.b_n;
+      ex.nbt = U.gp.nbt;
+      ex.N = r.N;
+      ex.K = r.K;
+      ex.Bx = dst;
+      ex.Bx_lo = U.hilo ? dst + expanded_b_bytes(U.gp.nbt, r.N, r.K) : nullptr;
+      ex.bf16 = P.skind == KIND_BF16;
+      R.begin(0, flops, bytes);
+      launch_gemm_simt(g, KIND_C64, out_kind, ldexpf(scale, -U.bexp), s, false, &ex);
+      R.end();
+    } else {
+      R.begin(0, flops, bytes);
+      launch_gemm_simt(g, KIND_C64, out_kind, scale, s, out_hilo);
+      R.end();
+    }
   }
   if (S.post_perm) {
     const int pe = out_kind == KIND_C64 ? 8 : 4;
@@ -725,7 +772,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       const GemmParams& g = S.gp;
       const bool big = g.K >= 8 && (double)g.nbt * g.M * g.N * g.K >= double(1 << 18);
       // the operand laid out [bt][free][contracted] is the one read as stored
-      S.tc_swap = P.nodes[S.b].elems > P.nodes[S.a].elems;
+      S.tc_swap = !a_is_big(P, S);
       bool ok = false;
       TcRoles r = tc_roles(S, &ok);
       const int an = r.a_node;
@@ -742,6 +789,19 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       Node& A = P.nodes[S.tc_swap ? S.b : S.a];
       A.kind = P.skind;
       A.hilo = S.hilo;
+    }
+  // a small-K step whose result is the expanded operand of a tensor-core step
+  // writes that expanded form itself (per-batch steps, k a multiple of the k tile)
+  if (P.skind != KIND_C64)
+    for (auto& S : P.steps) {
+      if (!S.tc || S.hoisted) continue;
+      TcRoles r = tc_roles(S);
+      const Node& NB = P.nodes[r.b_node];
+      if (NB.leaf || NB.kind != KIND_C64) continue;
+      Step& Q = P.steps[r.b_node - P.n_leaves];
+      if (Q.hoisted || Q.tc || Q.post_perm || Q.gp.K > 4 || expanded_half_pitch(r.K) != r.K) continue;
+      Q.fuse_expand = true;
+      S.b_fused = true;
     }
   // leaf storage layouts (variant leaves: sliced edges outermost, then the batch copy's order)
   std::vector<std::vector<int>> leaf_src_layout(P.n_leaves);

@@ -39,6 +39,8 @@ struct Step {
   bool tc_swap = false;                // tensor-core A operand is node b (else node a)
   bool hilo = false;                   // split-precision product (A, B as hi + lo)
   int bexp = 0;                        // the expanded operand is scaled by 2^-bexp into 16 bits
+  bool fuse_expand = false;            // writes its result as the consumer's expanded operand
+  bool b_fused = false;                // tensor-core step whose expanded operand its producer wrote
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network
 };

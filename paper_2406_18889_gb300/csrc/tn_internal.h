@@ -139,8 +139,20 @@ void launch_accumulate_c64(const void* root, int64_t sb, int64_t sg, int64_t sj,
 void launch_bit_permute(const void* in, void* out, const BitPermute& bp, int elem_bytes, cudaStream_t s);
 void launch_strided_copy_c128(const void* in, void* out, const StridedCopy& sc, int64_t n_out, int out_kind,
                               double scale, cudaStream_t s);
+// Destination of a CUDA-core step whose result is the expanded (real 2x2)
+// operand of the tensor-core step that consumes it: the result is written
+// straight into that step's expanded copy, [bt][2N][2K] 16-bit reals.
+struct ExpandedDst {
+  Runs b_bt, b_k, b_n;   // the consuming step's index maps of this tensor
+  int64_t nbt, N, K;     // the consuming step's extents (K: a multiple of the k tile)
+  void* Bx;
+  void* Bx_lo;           // rounding residuals (split precision), else null
+  bool bf16;
+};
 void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scale, cudaStream_t s,
-                      bool out_hilo = false);
+                      bool out_hilo = false, const ExpandedDst* ex = nullptr);
+// row pitch of an expanded operand, in 16-bit pairs (2K rounded up to the k tile, halved)
+int64_t expanded_half_pitch(int64_t K);
 void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
 struct TopkParams {
