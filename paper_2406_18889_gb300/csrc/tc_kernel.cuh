@@ -1,0 +1,541 @@
+// Tensor-core GEMM kernel (tcgen05 + TMA + TMEM) for the reduced-precision
+// complex path; included by one translation unit per tile width
+// (k_gemm_tc_bn*.cu), each of which instantiates launch_tc_tiles<BN>.
+//
+// A pairwise contraction (arXiv 2406.18889, Sec. III, per-step contraction) in
+// complex numbers is lowered to ONE real GEMM ("stacked 4M"): with complex
+// elements stored interleaved (re, im) in fp16/bf16,
+//   A'[m][2k+r]          = (Re A, Im A)[m][k]            (A used as stored)
+//   B'[2n+c][2k+r]       = [[Re B, -Im B], [Im B, Re B]]  (expanded from B)
+//   C'[m][2n+c] = sum_k' A'[m][k'] B'[2n+c][k']  = (Re C, Im C)[m][n]
+// so the real GEMM's output is already interleaved complex.  8 real flops per
+// complex multiply-add: the useful flop count of the paper's Table I
+// convention, with no 3M cancellation.
+//
+// Kernel: persistent CTAs over 128 x BN output tiles (real columns), 2 + 8 warps:
+//   warp 0      TMA producer: 3-D tiled loads of A' (box 64 x 128) and B'
+//               (box 64 x BN), 128-byte swizzle, into a ring of stages;
+//   warp 1      allocates 2 x BN TMEM columns (double-buffered accumulator);
+//               one thread issues tcgen05.mma (kind::f16, M = 128, N = BN,
+//               K = 16, FP32 accumulate in TMEM); tcgen05.commit releases ring
+//               stages and hands finished accumulators to the epilogue;
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//               lanes 32*(w%4)..+31; two warps per lane quarter split the
+//               columns), scale by 2^shift, convert, store -- directly along
+//               m, or (STAGE) transposed through shared memory so that lanes
+//               run along n when n is the output's contiguous index.
+// Every mbarrier wait is bounded by the global timer (2 s); on timeout the
+// kernel raises the device error flag and every role stops; the producer and
+// the MMA thread drain their own in-flight work (bounded) before TMEM is freed.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+constexpr int kTcBK = 64;  // real k per stage: one 128-byte swizzle row of 16-bit values
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = kTcBK;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true when the phase with `parity` has completed; false on abort or timeout
+__device__ bool wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*(volatile int*)err) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
+                                            int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+// the same load delivered to every CTA of the cluster in `mask` (same smem
+// offset, each CTA's own mbarrier at the same offset)
+__device__ __forceinline__ void tma_load_3d_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1 (tcgen05)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // version
+  d |= (uint64_t)2 << 61;             // swizzle: 128B
+  return d;
+}
+// instruction descriptor, kind::f16: D = F32, A/B = F16 (0) or BF16 (1), both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int n, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+// epilogue staging: per warp 32 rows x 16 complex (padded) + 32 row offsets
+constexpr int kStagePitch = 17;
+constexpr int kEpiWarps = 8;  // two warps per TMEM lane quarter, each taking half the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr size_t kStageBytes = kEpiWarps * 32 * kStagePitch * 8 + kEpiWarps * 32 * 8;
+
+// ring depth: as many stages as fit in 227 KB of shared memory next to the
+// barriers, the column-offset table and (STAGE) the epilogue staging, at most 8
+template <int BN, bool STAGE = false>
+__host__ __device__ constexpr int stages_for() {
+  constexpr long budget = 232448 - 1024 - 256 - (long)BN / 2 * 8 - (STAGE ? (long)kStageBytes : 0L) - 512;
+  constexpr long per = (long)(BM + BN) * BK * 2;
+  return budget / per > 8 ? 8 : (int)(budget / per);
+}
+template <int BN, bool STAGE>
+__host__ __device__ constexpr size_t smem_bytes() {
+  return 1024 + (size_t)stages_for<BN, STAGE>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8 +
+         (STAGE ? kStageBytes : 0);
+}
+
+
+// complex value -> one 32-bit word of two 16-bit reals
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack16(float re, float im) {
+  uint32_t w;
+  if constexpr (BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    memcpy(&w, &h, 4);
+  } else {
+    const __half2 h = __floats2half2_rn(re, im);
+    memcpy(&w, &h, 4);
+  }
+  return w;
+}
+// rounding residual of (re, im) given its 16-bit word
+template <bool BF16>
+__device__ __forceinline__ uint32_t resid16(float re, float im, uint32_t w) {
+  float2 h;
+  if constexpr (BF16) {
+    __nv_bfloat162 x;
+    memcpy(&x, &w, 4);
+    h = __bfloat1622float2(x);
+  } else {
+    __half2 x;
+    memcpy(&x, &w, 4);
+    h = __half22float2(x);
+  }
+  return pack16<BF16>(re - h.x, im - h.y);
+}
+// one complex output element at element offset o: fp32 pair, or 16-bit pair
+// (plus its residual in the second array when split)
+template <bool BF16, bool HILO, bool F32OUT>
+__device__ __forceinline__ void store_el(char* Cb, char* C2b, int64_t o, float re, float im) {
+  if constexpr (F32OUT) {
+    *reinterpret_cast<float2*>(Cb + o * 8) = make_float2(re, im);
+  } else {
+    const uint32_t h = pack16<BF16>(re, im);
+    *reinterpret_cast<uint32_t*>(Cb + o * 4) = h;
+    if constexpr (HILO) *reinterpret_cast<uint32_t*>(C2b + o * 4) = resid16<BF16>(re, im, h);
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent: CTA c walks output tiles c, c + gridDim.x, ... (n tile fastest,
+// then m tile, then batch).  The TMEM accumulator is double-buffered (2 x BN
+// columns): the MMA thread fills buffer (i & 1) for the CTA's i-th tile while
+// the epilogue drains the other; tfull/tempty hand the buffers back and forth.
+// C2: a cluster of two CTAs takes two adjacent m tiles of one n tile; each CTA
+// loads its own A tile and one half of the shared B tile, multicast to both,
+// so every SM reads a third less from L2 per k step.  A stage is refilled only
+// after both CTAs' MMAs released it (their commits arrive on both CTAs'
+// `empty` barriers).
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
+                   TcGemmParams p) {
+  constexpr int S = stages_for<BN, STAGE>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + S * BM * BK * 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * BN * BK * 2);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;   // [2] MMA -> epilogue
+  uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  int64_t* n_rel = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 256);  // [BN / 2]
+  float2* stage_buf = reinterpret_cast<float2*>(n_rel + BN / 2);                         // [warps][32][pitch]
+  int64_t* row_base = reinterpret_cast<int64_t*>(stage_buf + kEpiWarps * 32 * kStagePitch);  // [warps][32]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
+  const int k_tiles = HILO ? 3 * k_tiles1 : k_tiles1;
+  const int64_t n_n = (2 * p.N + BN - 1) / BN, n_m = (p.M + BM - 1) / BM;
+  // work units: single tiles, or (C2) pairs of m tiles sharing an n tile
+  const int64_t n_mu = C2 ? (n_m + 1) / 2 : n_m;
+  const int64_t tiles = p.nbt * n_mu * n_n;
+  const int rank = C2 ? (int)cluster_rank() : 0;
+  const int64_t unit0 = C2 ? blockIdx.x / 2 : blockIdx.x;
+  const int64_t ustride = C2 ? gridDim.x / 2 : gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C2 ? 2 : 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarps);  // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)(2 * BN))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (C2) cluster_sync_all();  // the peer's barriers are initialised before any multicast
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t g = 0;  // ring position over all of this CTA's k tiles
+      bool stop = false;
+      for (int64_t t = unit0; t < tiles && !stop; t += ustride) {
+        const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
+        const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
+        for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+          const int s = (int)(g % S);
+          const uint32_t use = (uint32_t)(g / S);
+          if (g >= S && !wait_bounded(&empty[s], (use & 1) ^ 1, p.err)) {
+            stop = true;
+            break;
+          }
+          const int pass = HILO ? kt / k_tiles1 : 0;
+          const int kx = (kt - pass * k_tiles1) * BK;
+          mbar_expect_tx(&full[s], (uint32_t)((BM + BN) * BK * 2));
+          tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + s * BM * BK * 2, kx, m_tile * BM, bt);
+          if (C2)
+            tma_load_3d_mc(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2 + rank * (BN / 2) * BK * 2, kx,
+                           n_tile * BN + rank * (BN / 2), bt, (uint16_t)0x3);
+          else
+            tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
+        }
+      }
+      // drain: every issued load must have landed before the CTA can exit
+      for (int64_t q = (g > S ? g - S : 0); q < g; ++q) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(&full[q % S], (uint32_t)((q / S) & 1)) && gtimer() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BN, BF16);
+      int64_t g = 0;
+      int64_t local = 0;
+      bool stop = false;
+      for (int64_t t = unit0; t < tiles && !stop; t += ustride, ++local) {
+        const int b = (int)(local & 1);
+        const uint32_t u = (uint32_t)(local >> 1);
+        if (local >= 2 && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_addr = tmem + (uint32_t)(b * BN);
+        for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+          const int s = (int)(g % S);
+          if (!wait_bounded(&full[s], (uint32_t)((g / S) & 1), p.err)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
+          const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ad = sw128_desc(a0 + kk * 32);
+            const uint64_t bd = sw128_desc(b0 + kk * 32);
+            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+          if (C2)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                    smem_u32(&empty[s])),
+                "h"((uint16_t)0x3)
+                : "memory");
+          else
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        // tfull[b] completes when this tile's MMAs (and all earlier ones) finish
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&tfull[b]))
+                     : "memory");
+      }
+      // before TMEM is freed: wait (bounded) for the last committed tile's MMAs
+      if (local > 0) {
+        const int64_t last = local - 1;
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(&tfull[last & 1], (uint32_t)((last >> 1) & 1)) && gtimer() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else {
+    // epilogue warps
+    const int et = threadIdx.x - 64;  // 0..32*kEpiWarps-1
+    const int quarter = warp & 3;      // TMEM lanes 32*quarter.. (warp w may read lanes 32*(w%4)..)
+    const int ew = warp - 2;           // epilogue warp index
+    constexpr int kGroups = kEpiWarps / 4;  // warps per lane quarter
+    constexpr int kChunks = BN / 32;        // 32-column accumulator loads per tile
+    const int cgrp = ew >> 2;               // this warp takes chunks cgrp, cgrp + kGroups, ...
+    // Tile-relative output offsets, once per CTA: tile origins are multiples of
+    // the (power-of-two) tile extents, and a run offset is linear over disjoint
+    // index bits, so offset(origin + i) = offset(origin) + offset(i).
+    for (int j = et; j < BN / 2; j += 32 * kEpiWarps) n_rel[j] = run_offset(p.c_n, j);
+    const int64_t m_rel = run_offset(p.c_m, quarter * 32 + lane);
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+    char* const Cb = reinterpret_cast<char*>(p.C);
+    char* const C2b = reinterpret_cast<char*>(p.C2);
+    // staging (STAGE): float2 [32][pitch] (fp32 out), or words [32][pitch] hi then lo
+    uint32_t* stg = reinterpret_cast<uint32_t*>(stage_buf + ew * 32 * kStagePitch);
+    int64_t* rb = row_base + ew * 32;
+    int64_t local = 0;
+    for (int64_t t = unit0; t < tiles; t += ustride, ++local) {
+      const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
+      const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
+      const int b = (int)(local & 1);
+      const uint32_t u = (uint32_t)(local >> 1);
+      const int64_t nbase = (int64_t)n_tile * BN / 2, mbase = (int64_t)m_tile * BM;
+      const int64_t row = run_offset(p.c_bt, bt) + run_offset(p.c_m, mbase) + run_offset(p.c_n, nbase) + m_rel;
+      const bool row_ok = mbase + quarter * 32 + lane < p.M;
+      // the tile lies wholly inside M x N (a cluster's second tile may lie past M)
+      const bool whole = mbase + BM <= p.M && nbase + BN / 2 <= p.N;
+      // every epilogue thread runs every iteration; after a timed-out wait
+      // (warp-uniform) the tile's reads and stores are skipped
+      const bool ok = __all_sync(0xffffffffu, wait_bounded(&tfull[b], u & 1, p.err));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (STAGE) {
+        rb[lane] = row;
+        __syncwarp();
+      }
+#pragma unroll 1
+      for (int c = cgrp; c < kChunks && ok; c += kGroups) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int j0 = c * 16;  // first complex column of the chunk
+        if (STAGE) {
+          // transpose through shared memory, already converted: lanes then run along n
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float re = __uint_as_float(v[2 * j]) * p.scale, im = __uint_as_float(v[2 * j + 1]) * p.scale;
+            if constexpr (F32OUT) {
+              reinterpret_cast<float2*>(stg)[lane * kStagePitch + j] = make_float2(re, im);
+            } else {
+              const uint32_t h = pack16<BF16>(re, im);
+              stg[lane * kStagePitch + j] = h;
+              if constexpr (HILO) stg[32 * kStagePitch + lane * kStagePitch + j] = resid16<BF16>(re, im, h);
+            }
+          }
+          __syncwarp();
+          const int jj = lane & 15;
+          const int64_t col = n_rel[j0 + jj];
+          const bool col_ok = nbase + j0 + jj < p.N;
+#pragma unroll 4
+          for (int it = 0; it < 16; ++it) {
+            const int r = 2 * it + (lane >> 4);
+            if (whole || (col_ok && mbase + quarter * 32 + r < p.M)) {
+              const int64_t o = rb[r] + col;
+              if constexpr (F32OUT) {
+                *reinterpret_cast<float2*>(Cb + o * 8) = reinterpret_cast<const float2*>(stg)[r * kStagePitch + jj];
+              } else {
+                *reinterpret_cast<uint32_t*>(Cb + o * 4) = stg[r * kStagePitch + jj];
+                if constexpr (HILO)
+                  *reinterpret_cast<uint32_t*>(C2b + o * 4) = stg[32 * kStagePitch + r * kStagePitch + jj];
+              }
+            }
+          }
+          __syncwarp();
+        } else if (whole) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
+                                         __uint_as_float(v[2 * j + 1]) * p.scale);
+        } else if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (nbase + j0 + j >= p.N) break;
+            store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
+                                         __uint_as_float(v[2 * j + 1]) * p.scale);
+          }
+        }
+      }
+      // hand the accumulator buffer back to the MMA thread
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (C2) cluster_sync_all();  // no CTA leaves while its peer may still multicast into it
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                 : "memory");
+  }
+}
+
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT>
+void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+                const TcGemmParams& p, cudaStream_t s) {
+  const size_t sm = smem_bytes<BN, STAGE>();
+  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2, F32OUT>;
+  static bool attr = false;
+  if (!attr) {
+    TN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  const int64_t n_m = (p.M + BM - 1) / BM, n_n = (2 * p.N + BN - 1) / BN;
+  if (!C2) {
+    const unsigned grid = (unsigned)std::min<int64_t>(n_m * n_n * p.nbt, 152);
+    kern<<<grid, kThreads, sm, s>>>(ma, ma2, mb, mb2, p);
+    return;
+  }
+  const int64_t pairs = ((n_m + 1) / 2) * n_n * p.nbt;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(pairs, 76)));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  TN_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, ma2, mb, mb2, p));
+}
+// the two-CTA cluster form is built for fp32 outputs only
+template <int BN, bool BF16, bool HILO, bool STAGE>
+void launch_tc4(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+                const TcGemmParams& p, cudaStream_t s) {
+  if (p.cluster2)
+    launch_tc6<BN, BF16, HILO, STAGE, true, true>(ma, ma2, mb, mb2, p, s);
+  else if (p.out_kind == 2)
+    launch_tc6<BN, BF16, HILO, STAGE, false, true>(ma, ma2, mb, mb2, p, s);
+  else
+    launch_tc6<BN, BF16, HILO, STAGE, false, false>(ma, ma2, mb, mb2, p, s);
+}
+template <int BN, bool BF16, bool HILO>
+void launch_tc3(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+                const TcGemmParams& p, cudaStream_t s) {
+  if (p.stage_n)
+    launch_tc4<BN, BF16, HILO, true>(ma, ma2, mb, mb2, p, s);
+  else
+    launch_tc4<BN, BF16, HILO, false>(ma, ma2, mb, mb2, p, s);
+}
+
+}  // namespace
+
+// Launch the persistent tensor-core kernel of tile width BN for p (maps built
+// by the host side); the variant follows the precision, the split, the
+// epilogue form and the output kind.
+template <int BN>
+void launch_tc_tiles(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
+                     const TcGemmParams& p, bool bf16, bool hilo, cudaStream_t s) {
+  if (bf16) {
+    if (hilo)
+      launch_tc3<BN, true, true>(ma, ma2, mb, mb2, p, s);
+    else
+      launch_tc3<BN, true, false>(ma, ma2, mb, mb2, p, s);
+  } else {
+    if (hilo)
+      launch_tc3<BN, false, true>(ma, ma2, mb, mb2, p, s);
+    else
+      launch_tc3<BN, false, false>(ma, ma2, mb, mb2, p, s);
+  }
+}
+
+}  // namespace tn
