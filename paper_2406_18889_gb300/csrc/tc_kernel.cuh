@@ -12,16 +12,16 @@
 // complex multiply-add: the useful flop count of the paper's Table I
 // convention, with no 3M cancellation.
 //
-// Kernel: persistent CTAs over 128 x BN output tiles (real columns), 2 + 8 warps:
+// Kernel: persistent CTAs over 128 x BN output tiles (real columns), 2 + 16 warps:
 //   warp 0      TMA producer: 3-D tiled loads of A' (box 64 x 128) and B'
 //               (box 64 x BN), 128-byte swizzle, into a ring of stages;
 //   warp 1      allocates 2 x BN TMEM columns (double-buffered accumulator);
 //               one thread issues tcgen05.mma (kind::f16, M = 128, N = BN,
 //               K = 16, FP32 accumulate in TMEM); tcgen05.commit releases ring
 //               stages and hands finished accumulators to the epilogue;
-//   warps 2..9  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//               lanes 32*(w%4)..+31; two warps per lane quarter split the
-//               columns), scale by 2^shift, convert, store -- directly along
+//   warps 2..17 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//               lanes 32*(w%4)..+31; four warps per lane quarter share its
+//               32-column chunks), scale by 2^shift, convert, store -- directly along
 //               m, or (STAGE) transposed through shared memory so that lanes
 //               run along n when n is the output's contiguous index.
 // Every mbarrier wait is bounded by the global timer (2 s); on timeout the
@@ -133,7 +133,7 @@ __host__ __device__ constexpr uint32_t make_idesc(int n, bool bf16) {
 
 // epilogue staging: per warp 32 rows x 16 complex (padded) + 32 row offsets
 constexpr int kStagePitch = 17;
-constexpr int kEpiWarps = 8;  // two warps per TMEM lane quarter, each taking half the columns
+constexpr int kEpiWarps = 16;  // four warps per TMEM lane quarter, each taking every fourth column chunk
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr size_t kStageBytes = kEpiWarps * 32 * kStagePitch * 8 + kEpiWarps * 32 * 8;
 
