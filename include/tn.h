@@ -168,7 +168,8 @@ tn_status tn_plan_query(tn_plan_t plan, int64_t* useful_flops_per_slice,
  * at plan creation), bit 3 = tensor-core GEMM (reduced precision), bit 4 =
  * split-precision (hi + lo) tensor-core GEMM, bit 5 = writes its result
  * directly as the expanded operand of the tensor-core step consuming it,
- * bit 6 = tensor-core step whose expanded operand its producer wrote. */
+ * bit 6 = tensor-core step whose expanded operand its producer wrote,
+ * bit 7 = small step run inside the one fused launch of small steps. */
 tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64_t* m,
                         int64_t* n, int64_t* k, int32_t* kinds, int32_t* n_steps_out);
 

@@ -367,7 +367,7 @@ int ilog2_exact(int64_t x) {
 
 // group and natural bit of every position bit of a dense tensor decoded by d
 // (groups 0..2 with extents ext[]); false when some bit is not covered
-bool position_bits(const RunDecode& d, int nbits, const int64_t ext[3], int8_t* grp, int8_t* nat) {
+bool position_bits_impl(const RunDecode& d, int nbits, const int64_t ext[3], int8_t* grp, int8_t* nat) {
   for (int j = 0; j < nbits; ++j) grp[j] = -1;
   int lg_ext[3];
   for (int g = 0; g < 3; ++g) lg_ext[g] = ilog2_exact(ext[g]);
@@ -410,7 +410,7 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
   TN_CHECK(p.nbits <= kMaxBits, TN_ERR_UNSUPPORTED, "result too large");
   int8_t grp[kMaxBits], nat[kMaxBits];
   const int64_t ext[3] = {g.nbt, g.M, g.N};
-  TN_CHECK(position_bits(g.c_dec, p.nbits, ext, grp, nat), TN_ERR_UNSUPPORTED, "result is not dense");
+  TN_CHECK(position_bits_impl(g.c_dec, p.nbits, ext, grp, nat), TN_ERR_UNSUPPORTED, "result is not dense");
   for (int j = 0; j < p.nbits; ++j) {
     const int64_t bit = int64_t(1) << nat[j];
     p.a_w[j] = grp[j] == 0 ? run_offset(g.a_bt, bit) : grp[j] == 1 ? run_offset(g.a_m, bit) : 0;
@@ -425,7 +425,7 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
     TN_CHECK(ex->nbt * ex->N * ex->K == total, TN_ERR_INVALID_ARG, "expanded destination size");
     int8_t g2[kMaxBits], n2[kMaxBits];
     const int64_t ext2[3] = {ex->nbt, ex->K, ex->N};
-    TN_CHECK(position_bits(decode_of(ex->b_bt, ex->b_k, ex->b_n), p.nbits, ext2, g2, n2), TN_ERR_UNSUPPORTED,
+    TN_CHECK(position_bits_impl(decode_of(ex->b_bt, ex->b_k, ex->b_n), p.nbits, ext2, g2, n2), TN_ERR_UNSUPPORTED,
              "expanded destination is not dense");
     for (int j = 0; j < p.nbits; ++j) {
       const int64_t unit = g2[j] == 0 ? 2 * ex->N * p.hp : g2[j] == 1 ? 1 : 2 * p.hp;
@@ -536,6 +536,10 @@ void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scal
   if (in_kind == 2 && out_kind == 0) return launch_typed<C64, F16>(p, scale, s, out_hilo);
   if (in_kind == 2 && out_kind == 1) return launch_typed<C64, BF16>(p, scale, s, out_hilo);
   fail(TN_ERR_UNSUPPORTED, "GEMM storage combination");
+}
+
+bool output_position_bits(const RunDecode& d, int nbits, const int64_t ext[3], int8_t* grp, int8_t* nat) {
+  return position_bits_impl(d, nbits, ext, grp, nat);
 }
 
 RunDecode decode_of(const Runs& bt, const Runs& m, const Runs& n) {

@@ -128,6 +128,8 @@ Plan::~Plan() {
   if (d_n_valid) cudaFree(d_n_valid);
   if (d_gather) cudaFree(d_gather);
   if (d_err) cudaFree(d_err);
+  if (d_micro) cudaFree(d_micro);
+  if (d_micro_start) cudaFree(d_micro_start);
 }
 
 // ---------------------------------------------------------------- layouts
@@ -332,9 +334,11 @@ TcRoles tc_roles(const Step& S, bool* ok_out = nullptr) {
   return r;
 }
 
-MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>& leaf_src_layout) {
+MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>& leaf_src_layout,
+                    bool micro) {
   MemPlan M;
   M.c64 = c64;
+  M.micro = micro && !P.micro_groups.empty();
   const int nn = (int)P.nodes.size();
   M.off.assign(nn, -1);
   M.in_plan.assign(nn, 0);
@@ -380,9 +384,19 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
       M.gather_node.push_back(i);
       M.off[i] = ws.alloc(node_bytes(P, i, c64));
     }
+  if (M.micro) {
+    // the fused small steps run together right after the gather: each result
+    // gets its own region; their operands and inner results are free afterwards
+    for (const Step& S : P.steps)
+      if (S.micro) M.off[S.c] = ws.alloc(node_bytes(P, S.c, c64));
+    for (const Step& S : P.steps)
+      if (S.micro)
+        for (int x : {S.a, S.b})
+          if (!M.in_plan[x] && (P.nodes[x].leaf || P.steps[x - P.n_leaves].micro)) ws.release(M.off[x]);
+  }
   for (size_t t = 0; t < P.steps.size(); ++t) {
     const Step& S = P.steps[t];
-    if (S.hoisted) continue;
+    if (S.hoisted || (M.micro && S.micro)) continue;
     if (!c64 && S.fuse_expand) {
       // the result is stored only as its consumer's expanded operand
       const Step& U = P.steps[P.nodes[S.c].consumer];
@@ -582,8 +596,15 @@ void enqueue_batch_mem(const Plan& P, const MemPlan& M, char* pb, void* ws, void
   }
   if (amax)
     for (int i = 0; i < P.n_leaves; ++i) launch_amax_c64(X.base(i), P.nodes[i].elems, amax + i, s);
+  if (M.micro) {
+    TN_CHECK(P.d_micro && !amax, TN_ERR_INVALID_ARG, "internal: fused small steps unavailable");
+    R.begin(0, P.micro_flops, P.micro_bytes);
+    launch_micro(P.d_micro, P.d_micro_start, (int)P.micro_groups.size(), pb, (char*)ws, s);
+    R.end();
+  }
   for (size_t t = 0; t < P.steps.size(); ++t) {
     if (P.steps[t].hoisted && !hoisted_too) continue;
+    if (M.micro && P.steps[t].micro) continue;
     enqueue_step(X, t, s, R, amax);
   }
   if (amps) {
@@ -803,6 +824,35 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       Q.fuse_expand = true;
       S.b_fused = true;
     }
+  // micro steps: per-batch CUDA-core steps with at most 2^14 outputs and K <= 4
+  // whose operands are leaves, plan-resident results or other micro steps;
+  // grouped into subtrees (a step joins its consumer's group)
+  for (auto& S : P.steps) {
+    if (S.hoisted || S.tc || S.fuse_expand || S.post_perm || S.gp.K > 4) continue;
+    if (S.gp.nbt * S.gp.M * S.gp.N > (int64_t(1) << kMicroMaxBits)) continue;
+    bool ok = P.nodes[S.a].elems < (int64_t(1) << 31) && P.nodes[S.b].elems < (int64_t(1) << 31);
+    for (int x : {S.a, S.b})
+      if (!P.nodes[x].leaf) {
+        const Step& Q = P.steps[x - P.n_leaves];
+        ok = ok && (Q.hoisted || Q.micro);
+      }
+    S.micro = ok;
+  }
+  {
+    std::vector<int> group(P.steps.size(), -1);
+    for (int t = (int)P.steps.size() - 1; t >= 0; --t) {
+      if (!P.steps[t].micro) continue;
+      const int u = P.nodes[P.steps[t].c].consumer;
+      if (u >= 0 && P.steps[u].micro) {
+        group[t] = group[u];
+      } else {
+        group[t] = (int)P.micro_groups.size();
+        P.micro_groups.emplace_back();
+      }
+    }
+    for (size_t t = 0; t < P.steps.size(); ++t)
+      if (group[t] >= 0) P.micro_groups[group[t]].push_back((int)t);
+  }
   // leaf storage layouts (variant leaves: sliced edges outermost, then the batch copy's order)
   std::vector<std::vector<int>> leaf_src_layout(P.n_leaves);
   for (int i = 0; i < P.n_leaves; ++i) {
@@ -823,7 +873,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     P.algo_bytes_per_slice += per(S.a) + per(S.b) + per(S.c);
     P.peak_intermediate_bytes = std::max(P.peak_intermediate_bytes, per(S.c));
   }
-  P.mem = plan_memory(P, P.skind == KIND_C64, leaf_src_layout);
+  P.mem = plan_memory(P, P.skind == KIND_C64, leaf_src_layout, true);
   if (opt->mem_cap_bytes > 0)
     TN_CHECK(P.mem.ws_bytes <= opt->mem_cap_bytes, TN_ERR_OOM, "workspace exceeds mem_cap_bytes");
   {
@@ -905,7 +955,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
   if (P.skind != KIND_C64) {
     // calibration: one complex64 batch (slice ids 0..B-1) records every tensor's
     // largest component; exponents make the stored maxima lie in [1/2, 1)
-    MemPlan Mc = plan_memory(P, true, leaf_src_layout);
+    MemPlan Mc = plan_memory(P, true, leaf_src_layout, false);
     char *cplan = nullptr, *cws = nullptr;
     unsigned* d_amax = nullptr;
     GatherLeaf* cgather = nullptr;
@@ -956,6 +1006,40 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       throw;
     }
     cleanup();
+  }
+  if (P.mem.micro) {
+    // fused small-step descriptors (scales need the calibrated exponents)
+    std::vector<MicroStep> desc;
+    std::vector<int> start{0};
+    for (const auto& grp : P.micro_groups) {
+      for (int t : grp) {
+        const Step& S = P.steps[t];
+        const Node& NC = P.nodes[S.c];
+        MicroStep d{};
+        fill_micro_weights(S.gp, d);
+        d.a_off = P.mem.off[S.a];
+        d.b_off = P.mem.off[S.b];
+        d.a_ws = P.mem.in_plan[S.a] ? 0 : 1;
+        d.b_ws = P.mem.in_plan[S.b] ? 0 : 1;
+        TN_CHECK(!P.mem.in_plan[S.c], TN_ERR_INVALID_ARG, "internal: micro result in plan memory");
+        d.c_off = P.mem.off[S.c];
+        const bool c64 = P.mem.c64;
+        d.out_kind = (int8_t)(c64 ? KIND_C64 : NC.kind);
+        d.out_hilo = (int8_t)(!c64 && NC.hilo ? 1 : 0);
+        d.c2_off = d.c_off + (d.out_hilo ? NC.elems * 4 : 0);
+        d.scale = c64 ? 1.0f : ldexpf(1.0f, P.nodes[S.a].exp2 + P.nodes[S.b].exp2 - NC.exp2);
+        desc.push_back(d);
+        P.micro_flops += 8.0 * S.cost;
+        P.micro_bytes += (double)(node_bytes(P, S.a, c64) + node_bytes(P, S.b, c64) + node_bytes(P, S.c, c64));
+      }
+      start.push_back((int)desc.size());
+    }
+    TN_CUDA(cudaMalloc(&P.d_micro, sizeof(MicroStep) * desc.size()));
+    TN_CUDA(cudaMalloc(&P.d_micro_start, sizeof(int) * start.size()));
+    TN_CUDA(cudaMemcpyAsync(P.d_micro, desc.data(), sizeof(MicroStep) * desc.size(), cudaMemcpyHostToDevice,
+                            stream));
+    TN_CUDA(cudaMemcpyAsync(P.d_micro_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice,
+                            stream));
   }
   TN_CUDA(cudaMalloc(&P.d_plan, std::max<int64_t>(P.mem.plan_bytes, 256)));
   upload_leaves(P.mem, (char*)P.d_plan, KIND_C64);

@@ -41,6 +41,7 @@ struct Step {
   int bexp = 0;                        // the expanded operand is scaled by 2^-bexp into 16 bits
   bool fuse_expand = false;            // writes its result as the consumer's expanded operand
   bool b_fused = false;                // tensor-core step whose expanded operand its producer wrote
+  bool micro = false;                  // small per-batch step run inside the fused small-step launch
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network
 };
@@ -48,6 +49,7 @@ struct Step {
 // Where every tensor lives for one storage precision.
 struct MemPlan {
   bool c64 = true;                      // complex64 everywhere (else 16-bit, root in complex64)
+  bool micro = false;                   // small steps run fused (their results never share memory)
   std::vector<int64_t> off;             // per node: byte offset
   std::vector<char> in_plan;            // per node: plan memory (1) or workspace (0)
   std::vector<int64_t> tmp_off;         // per step: natural-layout result before the transpose
@@ -86,6 +88,11 @@ struct Plan {
   int32_t* d_n_valid = nullptr;
   GatherLeaf* d_gather = nullptr;       // gather table (device)
   int* d_err = nullptr;                 // raised by a timed-out device wait
+  // fused small steps: subtrees of micro steps, each in topological order (one CTA each)
+  std::vector<std::vector<int>> micro_groups;
+  MicroStep* d_micro = nullptr;
+  int* d_micro_start = nullptr;
+  double micro_flops = 0, micro_bytes = 0;
   // root readout strides (elements)
   int64_t root_sb = 0, root_sg = 0, root_sj = 1;
   // statistics

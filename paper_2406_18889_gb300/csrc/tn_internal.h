@@ -153,6 +153,28 @@ void launch_gemm_simt(const GemmParams& p, int in_kind, int out_kind, float scal
                       bool out_hilo = false, const ExpandedDst* ex = nullptr);
 // row pitch of an expanded operand, in 16-bit pairs (2K rounded up to the k tile, halved)
 int64_t expanded_half_pitch(int64_t K);
+// group (0 bt, 1 m, 2 n) and natural bit of every position bit of a dense
+// result decoded by d (group extents ext[]); false when a bit is not covered
+bool output_position_bits(const RunDecode& d, int nbits, const int64_t ext[3], int8_t* grp, int8_t* nat);
+
+// One small step run inside the fused small-step kernel (k_micro.cu): result
+// C (dense, 2^nbits elements, memory order x) with operand offsets linear
+// over the bits of x.
+constexpr int kMicroMaxBits = 14;
+struct MicroStep {
+  int64_t a_off, b_off;          // operand byte offsets from their memory's base
+  int64_t c_off, c2_off;         // result (and residual) byte offsets in the workspace
+  int32_t a_w[kMicroMaxBits];    // element offset in A of output bit j
+  int32_t b_w[kMicroMaxBits];    // element offset in B of output bit j
+  int32_t ak[4], bk[4];          // contracted-index offsets
+  float scale;
+  int8_t a_ws, b_ws;             // operand lives in the workspace (else plan memory)
+  int8_t nbits, K, out_kind, out_hilo;
+};
+void fill_micro_weights(const GemmParams& g, MicroStep& d);
+// steps [group_start[g], group_start[g + 1]) run in order on CTA g
+void launch_micro(const MicroStep* d_steps, const int* d_group_start, int n_groups, const char* plan_base,
+                  char* ws_base, cudaStream_t s);
 void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
 struct TopkParams {
