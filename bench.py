@@ -355,7 +355,9 @@ def run_ours(args):
                                         plan.workspace.numel(), stream.cuda_stream)
     roofline, per_kind = roofline_from_profile(prof)
     permute = permute_bandwidth(B, torch, stream)
-    launches_per_step = prof["n_launches"] + 2  # + top-k + XEB
+    # recorded kernels + slice-id uploads (one launch per 256 ids of each batch) + top-k + XEB
+    n_batches = -(-S // args.batch)
+    launches_per_step = prof["n_launches"] + n_batches * (-(-args.batch // 256)) + 2
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
         plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch,

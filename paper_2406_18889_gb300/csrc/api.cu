@@ -2,6 +2,7 @@
 // work; no C++ exception crosses the boundary.
 #include <cstring>
 #include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -49,6 +50,22 @@ static tn_status guarded(F&& f) {
 // entry points defined in other translation units).
 tn_status guarded_call(const std::function<void()>& f) { return guarded(f); }
 
+// 256 bytes of device memory per host thread and device for small results the
+// host reads back within the same call (a flag, a scalar).  Allocated once,
+// outside any stream-ordered pool (whose memory may be handed back to the
+// driver at every synchronisation), and kept for the process's lifetime.
+static void* thread_scratch() {
+  thread_local std::map<int, void*> by_dev;
+  int dev = 0;
+  TN_CUDA(cudaGetDevice(&dev));
+  auto it = by_dev.find(dev);
+  if (it != by_dev.end()) return it->second;
+  void* p = nullptr;
+  TN_CUDA(cudaMalloc(&p, 256));
+  by_dev[dev] = p;
+  return p;
+}
+
 static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
                          size_t ws_bytes, cudaStream_t s, std::vector<LaunchRecord>* rec = nullptr) {
   TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
@@ -73,9 +90,7 @@ static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int
   for (int64_t start = 0; start < n; start += P.B) {
     int32_t nv = (int32_t)std::min<int64_t>(P.B, n - start);
     for (int b = 0; b < P.B; ++b) chunk[b] = ids[start + (b < nv ? b : 0)];
-    // pageable host -> device: the source is staged before the call returns
-    TN_CUDA(cudaMemcpyAsync(P.d_slice_ids, chunk.data(), sizeof(int64_t) * P.B, cudaMemcpyHostToDevice, s));
-    TN_CUDA(cudaMemcpyAsync(P.d_n_valid, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    launch_set_slice_ids(P.d_slice_ids, P.d_n_valid, chunk.data(), P.B, nv, s);
     run_batch(P, ws, amps, start == 0 ? accumulate : 1, s, rec);
   }
   TN_CUDA(cudaGetLastError());
@@ -192,13 +207,11 @@ tn_status tn_topk_postprocess(const void* amps, int64_t G, int64_t B, int32_t k,
       tp.open_pos[i] = (int8_t)open_bit_pos[i];
     }
     cudaStream_t s = (cudaStream_t)stream;
-    int* d_flag = nullptr;
-    TN_CUDA(cudaMallocAsync(&d_flag, sizeof(int), s));
+    int* d_flag = reinterpret_cast<int*>(thread_scratch());
     TN_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
     launch_topk((const double2*)amps, tp, block_base_idx, out_idx, out_p, d_flag, s);
     int h_flag = 0;
     TN_CUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TN_CUDA(cudaFreeAsync(d_flag, s));
     TN_CUDA(cudaStreamSynchronize(s));
     TN_CHECK(h_flag == 0, TN_ERR_NUMERIC, "NaN probability in top-k input");
   });
@@ -210,11 +223,9 @@ tn_status tn_xeb(const double* q, int64_t n_sel, int32_t n_qubits, double* out_x
     TN_CHECK(n_sel >= 1, TN_ERR_INVALID_ARG, "empty selection");
     TN_CHECK(n_qubits >= 1 && n_qubits <= 1000, TN_ERR_INVALID_ARG, "n_qubits out of range");
     cudaStream_t s = (cudaStream_t)stream;
-    double* d_out = nullptr;
-    TN_CUDA(cudaMallocAsync(&d_out, sizeof(double), s));
+    double* d_out = reinterpret_cast<double*>(reinterpret_cast<char*>(thread_scratch()) + 64);
     launch_xeb(q, n_sel, n_qubits, d_out, s);
     TN_CUDA(cudaMemcpyAsync(out_xeb, d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TN_CUDA(cudaFreeAsync(d_out, s));
     TN_CUDA(cudaStreamSynchronize(s));
   });
 }

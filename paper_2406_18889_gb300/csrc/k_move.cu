@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "tn_internal.h"
 
 namespace tn {
@@ -291,6 +293,33 @@ void launch_zero(void* p, size_t bytes, cudaStream_t s) {
   if (n16 == 0) return;
   unsigned blocks = (unsigned)std::min<int64_t>((n16 + 255) / 256, 4096);
   zero_kernel<<<blocks, 256, 0, s>>>((uint4*)p, n16);
+}
+
+// ------------------------------------------------------------ slice ids
+// Slice ids of one batch travel as kernel parameters (no host staging copy,
+// no stream synchronisation): each launch writes up to kIdsPerLaunch ids.
+namespace {
+constexpr int kIdsPerLaunch = 256;
+struct SliceIdChunk {
+  int64_t ids[kIdsPerLaunch];
+  int32_t count, n_valid, write_n_valid;
+};
+__global__ void set_ids_kernel(int64_t* dst, int32_t* n_valid, SliceIdChunk c) {
+  if ((int)threadIdx.x < c.count) dst[threadIdx.x] = c.ids[threadIdx.x];
+  if (threadIdx.x == 0 && c.write_n_valid) *n_valid = c.n_valid;
+}
+}  // namespace
+
+void launch_set_slice_ids(int64_t* d_ids, int32_t* d_n_valid, const int64_t* ids, int B, int32_t n_valid,
+                          cudaStream_t s) {
+  for (int off = 0; off < B; off += kIdsPerLaunch) {
+    SliceIdChunk c{};
+    c.count = std::min(kIdsPerLaunch, B - off);
+    for (int i = 0; i < c.count; ++i) c.ids[i] = ids[off + i];
+    c.n_valid = n_valid;
+    c.write_n_valid = off == 0 ? 1 : 0;
+    set_ids_kernel<<<1, kIdsPerLaunch, 0, s>>>(d_ids + off, d_n_valid, c);
+  }
 }
 
 }  // namespace tn

@@ -81,8 +81,7 @@ extern "C" tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* s
       int32_t nv = (int32_t)std::min<int64_t>(P.B, n_slices - start);
       for (int b = 0; b < P.B; ++b) chunk[b] = slice_ids[start + (b < nv ? b : 0)];
       // pageable host -> device: the runtime stages the source before returning
-      TN_CUDA(cudaMemcpyAsync(P.d_slice_ids, chunk.data(), sizeof(int64_t) * P.B, cudaMemcpyHostToDevice, s));
-      TN_CUDA(cudaMemcpyAsync(P.d_n_valid, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      launch_set_slice_ids(P.d_slice_ids, P.d_n_valid, chunk.data(), P.B, nv, s);
       run_batch_direct(P, ws, amps, start == 0 ? accumulate : 1, s);
     }
     TN_CUDA(cudaGetLastError());

@@ -176,6 +176,9 @@ void fill_micro_weights(const GemmParams& g, MicroStep& d);
 void launch_micro(const MicroStep* d_steps, const int* d_group_start, int n_groups, const char* plan_base,
                   char* ws_base, cudaStream_t s);
 void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s);
+// d_ids[0..B) = ids, *d_n_valid = n_valid, through kernel parameters (asynchronous)
+void launch_set_slice_ids(int64_t* d_ids, int32_t* d_n_valid, const int64_t* ids, int B, int32_t n_valid,
+                          cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
 struct TopkParams {
   int64_t G, Bsz;   // blocks and entries per block
