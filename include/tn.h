@@ -60,6 +60,9 @@ typedef enum {
                                         contraction calls on the plan fail (for inspection) */
 #define TN_FLAG_HILO 0x8u            /* reduced precision: every tensor-core step multiplies
                                         split-precision operands (hi + lo, three passes) */
+#define TN_FLAG_TC_PAIR 0x10u        /* reduced precision: tensor-core steps with 256-column tiles
+                                        run as two-CTA clusters that share each B tile (TMA
+                                        multicast), halving B's reads from L2 */
 
 typedef struct tn_plan_s* tn_plan_t;
 

@@ -23,6 +23,7 @@ TN_FLAG_HOIST_INVARIANT = 0x1
 TN_FLAG_NO_GRAPH = 0x2
 TN_FLAG_PLAN_ONLY = 0x4
 TN_FLAG_HILO = 0x8
+TN_FLAG_TC_PAIR = 0x10
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",

@@ -79,8 +79,9 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
   // a 16-bit output has the operands' type, and a residual exactly when the product is split
   TN_CHECK(p.out_kind == 2 || (p.out_kind == (bf16 ? 1 : 0) && (p.out_hilo != 0) == hilo), TN_ERR_UNSUPPORTED,
            "tensor-core output storage must match the operand precision");
-  TN_CHECK(!p.cluster2 || p.out_kind == 2, TN_ERR_UNSUPPORTED, "two-CTA tensor-core form writes fp32 only");
   const int bn = p.bn;
+  TN_CHECK(!p.cluster2 || p.out_kind == 2 || bn == 256, TN_ERR_UNSUPPORTED,
+           "two-CTA tensor-core form: 16-bit output needs tile width 256");
   {
     // stage the epilogue when n is the output's more contiguous index
     const int64_t big = int64_t(1) << 62;

@@ -535,7 +535,7 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     tp.scale = scale;
     tp.err = P.d_err;
     tp.bn = tc_gemm_bn(r.N);
-    tp.cluster2 = 0;  // two-CTA multicast clusters: no gain measured on these shapes
+    tp.cluster2 = (P.flags & TN_FLAG_TC_PAIR) && tp.bn == 256 ? 1 : 0;
     const char* a_hi = X.base(r.a_node);
     R.begin(5, flops, bytes);
     launch_gemm_tc(a_hi, S.hilo ? a_hi + NA.elems * 4 : nullptr, r.a_bt, r.a_m, bx, bx_lo, tp,

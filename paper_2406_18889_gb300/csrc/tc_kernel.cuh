@@ -497,13 +497,21 @@ void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap
   cfg.numAttrs = 1;
   TN_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, ma2, mb, mb2, p));
 }
-// the two-CTA cluster form is built for fp32 outputs only
+// the two-CTA cluster form: fp32 outputs at every width, 16-bit outputs at width 256
 template <int BN, bool BF16, bool HILO, bool STAGE>
 void launch_tc4(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
-  if (p.cluster2)
-    launch_tc6<BN, BF16, HILO, STAGE, true, true>(ma, ma2, mb, mb2, p, s);
-  else if (p.out_kind == 2)
+  if (p.cluster2) {
+    if (p.out_kind == 2) {
+      launch_tc6<BN, BF16, HILO, STAGE, true, true>(ma, ma2, mb, mb2, p, s);
+      return;
+    }
+    if constexpr (BN == 256) {
+      launch_tc6<BN, BF16, HILO, STAGE, true, false>(ma, ma2, mb, mb2, p, s);
+      return;
+    }
+    fail(TN_ERR_UNSUPPORTED, "two-CTA tensor-core form: 16-bit output needs tile width 256");
+  } else if (p.out_kind == 2)
     launch_tc6<BN, BF16, HILO, STAGE, false, true>(ma, ma2, mb, mb2, p, s);
   else
     launch_tc6<BN, BF16, HILO, STAGE, false, false>(ma, ma2, mb, mb2, p, s);

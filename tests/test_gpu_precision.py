@@ -84,3 +84,17 @@ def test_reduced_precision_deterministic(E, grid):
     a = plan.contract().cpu().numpy()
     b = plan.contract().cpu().numpy()
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec,flags", [("fp16", 0), ("bf16", 8)], ids=["fp16", "bf16+hilo"])
+def test_tc_pair_clusters_match_single_ctas(E, grid, prec, flags):
+    # two-CTA clusters sharing B tiles change only which SM loads what: every
+    # output is the same k loop, so the amplitudes agree bit for bit
+    from paper_2406_18889_gb300 import binding as B
+    w, psi, ref, x_ref, prep = grid
+    single = E.Plan(prep.tn, prep.tree, prec=prec, flags=flags, max_slice_batch=64)
+    pair = E.Plan(prep.tn, prep.tree, prec=prec, flags=flags | B.TN_FLAG_TC_PAIR, max_slice_batch=64)
+    a = single.contract().cpu().numpy()
+    b = pair.contract().cpu().numpy()
+    assert np.array_equal(a, b)
+    assert pp.relative_l2(b, ref) <= LOWP_TOL
