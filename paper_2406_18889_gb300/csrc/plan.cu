@@ -792,15 +792,32 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     if (P.skind != KIND_C64) {
       const GemmParams& g = S.gp;
       const bool big = g.K >= 8 && (double)g.nbt * g.M * g.N * g.K >= double(1 << 18);
-      // the operand laid out [bt][free][contracted] is the one read as stored
-      S.tc_swap = !a_is_big(P, S);
-      bool ok = false;
-      TcRoles r = tc_roles(S, &ok);
-      const int an = r.a_node;
-      if (big && ok && !P.nodes[an].leaf && r.M >= 64 &&
-          tc_gemm_supported(g.nbt, r.M, r.N, r.K, r.a_bt, r.a_m, 1)) {
+      // Both operands are stored [bt][free][contracted], so either can be the
+      // one read as stored (A); the other is expanded.  Preferred: A owns the
+      // result's unit-stride index (the epilogue then stores along TMEM lanes),
+      // if the other operand is small enough to expand; else the larger one.
+      auto valid = [&](bool swap) {
+        S.tc_swap = swap;
+        bool ok = false;
+        TcRoles r = tc_roles(S, &ok);
+        return ok && !P.nodes[r.a_node].leaf && r.M >= 64 &&
+               tc_gemm_supported(g.nbt, r.M, r.N, r.K, r.a_bt, r.a_m, 1);
+      };
+      const bool larger = !a_is_big(P, S);
+      bool want = larger;
+      if (g.c_n.n > 0 && g.c_n.st[0] == 1)
+        want = true;
+      else if (g.c_m.n > 0 && g.c_m.st[0] == 1)
+        want = false;
+      const int64_t expanded = P.nodes[want ? S.a : S.b].elems;
+      if (want != larger && expanded > (int64_t(1) << 22)) want = larger;
+      bool ok = big && valid(want);
+      if (big && !ok && want != larger) ok = valid(larger);
+      if (ok) {
         S.tc = true;
         S.hilo = (P.flags & TN_FLAG_HILO) != 0;
+      } else {
+        S.tc_swap = larger;
       }
     }
   }
