@@ -195,12 +195,26 @@ KIND_NAMES = {0: "gemm_cuda_core", 1: "bit_permute", 2: "gather", 3: "accumulate
               4: "expand_operand", 5: "gemm_tensor_core"}
 
 
-def roofline_from_profile(prof) -> tuple:
-    """Roofline of the kernel class with the largest share of one profiled step:
-    achieved = algorithmic FLOPs (or bytes) of its launches / their summed event time."""
+# DRAM bytes (read + write) of the largest tensor-core launch of one step of the
+# default configuration (fp16, slice batch 64, invariant subtrees hoisted), from
+# the ncu capture summarised in profiles/tc_gemm_grid4x6_d14_fp16_dram.md
+# (dram__bytes_read.sum + dram__bytes_write.sum of that launch)
+DOMINANT_TRAFFIC = {("fp16", 64, False, True): 2101993984}
+
+
+def roofline_from_profile(prof, cfg_key=None) -> tuple:
+    """Per-launch rooflines of one profiled step (CUDA events around every launch).
+
+    Each launch i has algorithmic FLOPs F_i and bytes B_i (operands and result
+    once, at their storage size) and time t_i; its roofline time is
+    max(F_i / P, B_i / BW), with P the tensor (or FP32 ALU) peak and BW the HBM
+    peak.  Reported: the dominant launch (largest t_i) with its binding
+    resource, the path's sum of roofline times over its summed time, and the
+    per-class totals."""
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    alu_peak = fp32_alu_peak_tflops()
     src = "of measured" if peaks else "of fallback"
     kinds, ms, flops, nbytes = prof["kind"], prof["ms"], prof["flops"], prof["bytes"]
     per_kind = {}
@@ -212,21 +226,36 @@ def roofline_from_profile(prof) -> tuple:
             entry["tflops"] = float(flops[sel].sum() / (t / 1e3) / 1e12) if t > 0 else None
         entry["gbs"] = float(nbytes[sel].sum() / (t / 1e3) / 1e9) if t > 0 else None
         per_kind[KIND_NAMES[int(k)]] = entry
-    dom = max(per_kind, key=lambda n: per_kind[n]["ms"])
-    e = per_kind[dom]
-    if dom == "gemm_tensor_core":
-        r = {"bound": "tensor", "achieved": e["tflops"], "peak": tc_peak, "unit": "TFLOP/s",
+    t_roof, t_all, launches = 0.0, 0.0, []
+    for k, t, f, b in zip(kinds, ms, flops, nbytes):
+        pk = tc_peak if k == 5 else alu_peak if k == 0 else None
+        tf = f / (pk * 1e12) * 1e3 if pk else 0.0
+        tb = b / (hbm * 1e9) * 1e3
+        t_roof += max(tf, tb)
+        t_all += float(t)
+        if k == 5:
+            launches.append({"ms": float(t), "tflops": float(f / (t / 1e3) / 1e12), "gbs": float(b / (t / 1e3) / 1e9),
+                             "bound": "tensor" if tf >= tb else "hbm", "frac": float(max(tf, tb) / t)})
+    i = int(np.argmax(ms))
+    k, t, f, b = int(kinds[i]), float(ms[i]), float(flops[i]), float(nbytes[i])
+    tf = f / (tc_peak * 1e12) * 1e3 if k == 5 else f / (alu_peak * 1e12) * 1e3 if k == 0 else 0.0
+    tb = b / (hbm * 1e9) * 1e3
+    if k == 5 and tf >= tb:
+        r = {"bound": "tensor", "achieved": f / (t / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
              "peak_source": f"bf16_tflops burst {src} (fp16 dense rate is the same)"}
-    elif dom == "gemm_cuda_core":
-        p = fp32_alu_peak_tflops()
-        r = {"bound": "alu", "achieved": e["tflops"], "peak": p, "unit": "TFLOP/s",
+    elif k == 0 and tf >= tb:
+        r = {"bound": "alu", "achieved": f / (t / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     else:
-        r = {"bound": "hbm", "achieved": e["gbs"], "peak": hbm, "unit": "GB/s",
+        r = {"bound": "hbm", "achieved": b / (t / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
              "peak_source": f"hbm_gbs {src}"}
-    r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
-    r["traffic"] = None
-    r["kernel"] = f"{dom} (all {e['launches']} launches of one step)"
+    r["frac"] = r["achieved"] / r["peak"]
+    r["traffic"] = DOMINANT_TRAFFIC.get(cfg_key) if k == 5 else None
+    r["kernel"] = f"{KIND_NAMES[k]}: the step's longest launch ({t:.3f} ms)"
+    r["algorithmic"] = {"flops": f, "bytes": b}
+    r["path"] = {"roofline_ms": t_roof, "ms": t_all, "frac": t_roof / t_all if t_all > 0 else None,
+                 "note": "sum over launches of max(F/P, B/BW) over their summed event time"}
+    r["tensor_core_launches"] = launches
     r["per_kind"] = per_kind
     return r, per_kind
 
@@ -353,7 +382,7 @@ def run_ours(args):
     # per-kernel roofline: one profiled pass (events around every launch)
     prof = B.tn_contract_slices_profile(plan.handle, ids, amps.data_ptr(), 0, plan.workspace.data_ptr(),
                                         plan.workspace.numel(), stream.cuda_stream)
-    roofline, per_kind = roofline_from_profile(prof)
+    roofline, per_kind = roofline_from_profile(prof, (args.prec, args.batch, bool(args.hilo), not args.no_hoist))
     permute = permute_bandwidth(B, torch, stream)
     # recorded kernels + slice-id uploads (one launch per 256 ids of each batch) + top-k + XEB
     n_batches = -(-S // args.batch)

@@ -277,44 +277,98 @@ __device__ __forceinline__ void store_expanded(typename H::T* X, typename H::T* 
   }
 }
 
-// MODE 0: C[o] = result (Out storage, hi + lo when `hilo`); MODE 1: expanded destination
-template <class Out, int MODE>
-__global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
+// V adjacent results (V = 1 or 2) at element offset o of the destination
+template <class Out, int MODE, int V>
+__device__ __forceinline__ void store_v(const SmallK& p, int64_t o, const float2 (&v)[V], bool hilo) {
   using TO = typename Out::T;
+  TO* C = reinterpret_cast<TO*>(p.C);
+  TO* C2 = reinterpret_cast<TO*>(p.C2);
+  if constexpr (V == 1) {
+    if constexpr (MODE == 0)
+      store_out<Out>(C, C2, o, v[0], hilo);
+    else
+      store_expanded<Out>(C, C2, o, p.hp, v[0]);
+  } else if constexpr (MODE == 0 && std::is_same_v<Out, C64>) {
+    *reinterpret_cast<float4*>(reinterpret_cast<float2*>(p.C) + o) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  } else if constexpr (MODE == 0) {
+    // two 16-bit complex values (8 bytes), and their residuals when split
+    TO h[2] = {Out::st(v[0]), Out::st(v[1])};
+    *reinterpret_cast<uint2*>(C + o) = *reinterpret_cast<const uint2*>(h);
+    if (hilo) {
+      const float2 f0 = Out::ld(h[0]), f1 = Out::ld(h[1]);
+      TO l[2] = {Out::st(make_float2(v[0].x - f0.x, v[0].y - f0.y)), Out::st(make_float2(v[1].x - f1.x, v[1].y - f1.y))};
+      *reinterpret_cast<uint2*>(C2 + o) = *reinterpret_cast<const uint2*>(l);
+    }
+  } else {
+    // expanded rows o (Re, -Im) and o + hp (Im, Re), two columns each
+    TO r0[2] = {Out::st(make_float2(v[0].x, -v[0].y)), Out::st(make_float2(v[1].x, -v[1].y))};
+    TO r1[2] = {Out::st(make_float2(v[0].y, v[0].x)), Out::st(make_float2(v[1].y, v[1].x))};
+    *reinterpret_cast<uint2*>(C + o) = *reinterpret_cast<const uint2*>(r0);
+    *reinterpret_cast<uint2*>(C + o + p.hp) = *reinterpret_cast<const uint2*>(r1);
+    if (C2) {
+      float2 l[2];
+      for (int i = 0; i < 2; ++i) {
+        const float2 h = Out::ld(Out::st(v[i]));
+        l[i] = make_float2(v[i].x - h.x, v[i].y - h.y);
+      }
+      TO q0[2] = {Out::st(make_float2(l[0].x, -l[0].y)), Out::st(make_float2(l[1].x, -l[1].y))};
+      TO q1[2] = {Out::st(make_float2(l[0].y, l[0].x)), Out::st(make_float2(l[1].y, l[1].x))};
+      *reinterpret_cast<uint2*>(C2 + o) = *reinterpret_cast<const uint2*>(q0);
+      *reinterpret_cast<uint2*>(C2 + o + p.hp) = *reinterpret_cast<const uint2*>(q1);
+    }
+  }
+}
+
+// MODE 0: C[o] = result (Out storage, hi + lo when `hilo`); MODE 1: expanded
+// destination.  KC: the contracted extent; V: adjacent outputs per thread (the
+// tile's bit 0 is then a unit-stride bit of the destination).  Thread t of a
+// tile takes outputs V*(t + 256*i) + v: the part of every map that depends on
+// t is read once into registers, the part that depends on i is a broadcast.
+template <class Out, int MODE, int KC, int V>
+__global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
   extern __shared__ float2 staged[];
   __shared__ uint32_t sel_lo[256], sel_hi[16];
   __shared__ int64_t off_lo[256], off_hi[16];
+  constexpr int lgK = KC == 1 ? 0 : KC == 2 ? 1 : 2;
+  constexpr int sh = V - 1;  // tile bits below the thread index
   float2* As = staged;
-  float2* Bs = staged + (p.K << p.na);
-  // tables of the tile's low 8 and high 4 position bits (linear maps: OR / sum of parts)
+  float2* Bs = staged + (KC << p.na);
+  // tables over tile bits sh..sh+7 (thread index) and sh+8.. (iteration);
+  // linear maps: OR / sum of the parts
   {
     const int j = threadIdx.x;
     uint32_t sel = 0;
     int64_t off = 0;
-    for (int b = 0; b < 8 && b < p.P; ++b)
+    for (int b = 0; b < 8 && b + sh < p.P; ++b)
       if ((j >> b) & 1) {
-        if (p.a_rank[b] >= 0) sel |= 1u << p.a_rank[b];
-        if (p.b_rank[b] >= 0) sel |= 1u << (16 + p.b_rank[b]);
-        off += p.o_w[b];
+        if (p.a_rank[b + sh] >= 0) sel |= 1u << p.a_rank[b + sh];
+        if (p.b_rank[b + sh] >= 0) sel |= 1u << (16 + p.b_rank[b + sh]);
+        off += p.o_w[b + sh];
       }
     sel_lo[j] = sel;
     off_lo[j] = off;
     if (j < 16) {
       sel = 0;
       off = 0;
-      for (int b = 8; b < kSkMaxTileBits && b < p.P; ++b)
-        if ((j >> (b - 8)) & 1) {
-          if (p.a_rank[b] >= 0) sel |= 1u << p.a_rank[b];
-          if (p.b_rank[b] >= 0) sel |= 1u << (16 + p.b_rank[b]);
-          off += p.o_w[b];
+      for (int b = 0; b + 8 + sh < p.P; ++b)
+        if ((j >> b) & 1) {
+          if (p.a_rank[b + 8 + sh] >= 0) sel |= 1u << p.a_rank[b + 8 + sh];
+          if (p.b_rank[b + 8 + sh] >= 0) sel |= 1u << (16 + p.b_rank[b + 8 + sh]);
+          off += p.o_w[b + 8 + sh];
         }
       sel_hi[j] = sel;
       off_hi[j] = off;
     }
   }
+  // tile bit 0 (V = 2): its staged-index bits (rank 0 when it is an A / B bit)
+  const uint32_t a_v = (V == 2 && p.a_rank[0] >= 0) ? 1u : 0u;
+  const uint32_t b_v = (V == 2 && p.b_rank[0] >= 0) ? 1u : 0u;
   const int64_t ntiles = int64_t(1) << (p.nbits - p.P);
-  const int tile_n = 1 << p.P;
-  const int na_n = p.K << p.na, nb_n = p.K << p.nb;
+  const int n_q = (1 << p.P) / V;
+  const int na_n = KC << p.na, nb_n = KC << p.nb;
+  __syncthreads();
+  const uint32_t sel_t = sel_lo[threadIdx.x];
+  const int64_t off_t = off_lo[threadIdx.x];
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int64_t a0 = 0, b0 = 0, o0 = 0;
     for (int j = p.P; j < p.nbits; ++j)
@@ -323,37 +377,38 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
         b0 += p.b_w[j];
         o0 += p.o_w[j];
       }
-    __syncthreads();  // tables written; the previous tile's staged entries consumed
+    __syncthreads();  // the previous tile's staged entries consumed
     for (int i = threadIdx.x; i < na_n; i += blockDim.x) {
-      const int u = i >> p.lgK;
-      int64_t o = a0 + p.ak[i & (p.K - 1)];
+      const int u = i >> lgK;
+      int64_t o = a0 + p.ak[i & (KC - 1)];
       for (int b = 0; b < p.na; ++b)
         if ((u >> b) & 1) o += p.a_wt[b];
       As[i] = p.A[o];
     }
     for (int i = threadIdx.x; i < nb_n; i += blockDim.x) {
-      const int u = i >> p.lgK;
-      int64_t o = b0 + p.bk[i & (p.K - 1)];
+      const int u = i >> lgK;
+      int64_t o = b0 + p.bk[i & (KC - 1)];
       for (int b = 0; b < p.nb; ++b)
         if ((u >> b) & 1) o += p.b_wt[b];
       Bs[i] = p.B[o];
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < tile_n; x += blockDim.x) {
-      const uint32_t sel = sel_lo[x & 255] | sel_hi[x >> 8];
-      const float2* a = As + ((sel & 0xffffu) << p.lgK);
-      const float2* b = Bs + ((sel >> 16) << p.lgK);
-      float2 acc = make_float2(0.f, 0.f);
+    const int64_t ot = o0 + off_t;
+    for (int q = threadIdx.x; q < n_q; q += blockDim.x) {
+      const int h = q >> 8;
+      const uint32_t sel = sel_t | sel_hi[h];
+      const uint32_t ua = sel & 0xffffu, ub = sel >> 16;
+      float2 r[V];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < p.K) cmac(acc, a[k], b[k]);
-      acc.x *= p.scale;
-      acc.y *= p.scale;
-      const int64_t o = o0 + off_lo[x & 255] + off_hi[x >> 8];
-      if constexpr (MODE == 0)
-        store_out<Out>((TO*)p.C, (TO*)p.C2, o, acc, hilo);
-      else
-        store_expanded<Out>((TO*)p.C, (TO*)p.C2, o, p.hp, acc);
+      for (int v = 0; v < V; ++v) {
+        const float2* a = As + ((ua | (v ? a_v : 0u)) << lgK);
+        const float2* b = Bs + ((ub | (v ? b_v : 0u)) << lgK);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KC; ++k) cmac(acc, a[k], b[k]);
+        r[v] = make_float2(acc.x * p.scale, acc.y * p.scale);
+      }
+      store_v<Out, MODE, V>(p, ot + off_hi[h], r, hilo);
     }
   }
 }
@@ -484,10 +539,29 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
   const size_t smem = (size_t)((p.K << p.na) + (p.K << p.nb)) * sizeof(float2);
   const int64_t tiles = int64_t(1) << (p.nbits - p.P);
   const unsigned blocks = (unsigned)std::min<int64_t>(tiles, 152 * 6);
-  if (ex)
-    gemm_smallk<Out, 1><<<blocks, 256, smem, s>>>(p, hilo);
-  else
-    gemm_smallk<Out, 0><<<blocks, 256, smem, s>>>(p, hilo);
+  // two adjacent outputs per thread when the tile's bit 0 has unit stride in the
+  // destination and every other bit an even one (aligned vector stores)
+  bool pair = p.P >= 1 && p.o_w[0] == 1 && (!ex || p.hp % 2 == 0);
+  for (int j = 1; j < p.nbits && pair; ++j) pair = p.o_w[j] % 2 == 0;
+  auto go = [&](auto kc, auto v) {
+    constexpr int KC = decltype(kc)::value, V = decltype(v)::value;
+    if (ex)
+      gemm_smallk<Out, 1, KC, V><<<blocks, 256, smem, s>>>(p, hilo);
+    else
+      gemm_smallk<Out, 0, KC, V><<<blocks, 256, smem, s>>>(p, hilo);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using I4 = std::integral_constant<int, 4>;
+  if (pair) {
+    if (p.K == 1) go(I1{}, I2{});
+    else if (p.K == 2) go(I2{}, I2{});
+    else go(I4{}, I2{});
+  } else {
+    if (p.K == 1) go(I1{}, I1{});
+    else if (p.K == 2) go(I2{}, I1{});
+    else go(I4{}, I1{});
+  }
 }
 
 template <class In, class Out>
