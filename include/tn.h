@@ -221,9 +221,12 @@ tn_status tn_contract_slices_batched(const tn_plan_t* plans, int32_t n_plans,
  *   open_bit_pos  : host int64 [l], bit position (0 = LSB) of open edge i
  *                   (open edge 0 is the most significant bit of j).
  *   out_idx, out_p: device int64 / double outputs.
- * Constraints: 1 <= k <= B (per block) or k <= G*B (global), k <= 512,
- * B <= 2^16.  A NaN probability makes the call return TN_ERR_NUMERIC after
- * synchronising the stream.
+ * Constraints: per block, 1 <= k <= B, k <= 512, B <= 2^16; global, 1 <= k
+ * <= G*B, k <= 2^26, B <= 2^40, G*B <= 2^40.  The global selection is exact (a
+ * radix select on the FP64 bit patterns of p, then on the full indices of
+ * candidates tied at the threshold) and allocates scratch of about 16 bytes per
+ * selected string for the final sort.  A NaN probability makes the call return
+ * TN_ERR_NUMERIC after synchronising the stream.
  */
 tn_status tn_topk_postprocess(const void* amps, int64_t G, int64_t B, int32_t k, double inv_f,
                               int global_mode, const int64_t* block_base_idx,

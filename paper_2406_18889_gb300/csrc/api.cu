@@ -188,11 +188,15 @@ tn_status tn_topk_postprocess(const void* amps, int64_t G, int64_t B, int32_t k,
                               int64_t* out_idx, double* out_p, void* stream) {
   return guarded([&] {
     TN_CHECK(amps && block_base_idx && out_idx && out_p, TN_ERR_INVALID_ARG, "null pointer");
-    TN_CHECK(G >= 1 && B >= 1 && B <= 65536, TN_ERR_INVALID_ARG, "bad G or B");
-    TN_CHECK(l >= 0 && l <= 16 && (int64_t(1) << l) == B, TN_ERR_INVALID_ARG, "B must equal 2^l");
-    TN_CHECK(l == 0 || open_bit_pos, TN_ERR_INVALID_ARG, "open_bit_pos is null");
     TN_CHECK(global_mode == 0 || global_mode == 1, TN_ERR_INVALID_ARG, "global_mode must be 0 or 1");
-    TN_CHECK(k >= 1 && k <= 512 && k <= (global_mode ? G * B : B), TN_ERR_INVALID_ARG, "k out of range");
+    // per block: B <= 2^16, k <= 512; global: G * B <= 2^40 candidates, k <= 2^26
+    const int max_l = global_mode ? 40 : 16;
+    TN_CHECK(G >= 1 && B >= 1 && l >= 0 && l <= max_l && (int64_t(1) << l) == B, TN_ERR_INVALID_ARG,
+             "bad G or B (B must equal 2^l)");
+    TN_CHECK(l == 0 || open_bit_pos, TN_ERR_INVALID_ARG, "open_bit_pos is null");
+    TN_CHECK(!global_mode || G <= (int64_t(1) << 40) / B, TN_ERR_INVALID_ARG, "too many candidates");
+    TN_CHECK(k >= 1 && k <= (global_mode ? (1 << 26) : 512) && k <= (global_mode ? G * B : B), TN_ERR_INVALID_ARG,
+             "k out of range");
     TN_CHECK(global_mode || G <= 0x7fffffff, TN_ERR_INVALID_ARG, "too many blocks");
     TN_CHECK(inv_f > 0 && inv_f == inv_f, TN_ERR_INVALID_ARG, "inv_f must be positive");
     TopkParams tp{};
@@ -209,7 +213,10 @@ tn_status tn_topk_postprocess(const void* amps, int64_t G, int64_t B, int32_t k,
     cudaStream_t s = (cudaStream_t)stream;
     int* d_flag = reinterpret_cast<int*>(thread_scratch());
     TN_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
-    launch_topk((const double2*)amps, tp, block_base_idx, out_idx, out_p, d_flag, s);
+    if (global_mode)
+      topk_global((const double2*)amps, tp, block_base_idx, out_idx, out_p, d_flag, s);
+    else
+      launch_topk((const double2*)amps, tp, block_base_idx, out_idx, out_p, d_flag, s);
     int h_flag = 0;
     TN_CUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     TN_CUDA(cudaStreamSynchronize(s));

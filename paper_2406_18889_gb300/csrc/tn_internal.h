@@ -189,6 +189,10 @@ struct TopkParams {
 void launch_topk(const double2* amps, const TopkParams& tp, const int64_t* block_base,
                  int64_t* out_idx, double* out_p, int* d_flag, cudaStream_t s);
 void launch_xeb(const double* q, int64_t n, int n_qubits, double* d_out, cudaStream_t s);
+// exact global top-k over all G * Bsz candidates (radix select + bitonic sort),
+// synchronous on s; d_flag is raised on a NaN probability
+void topk_global(const double2* amps, const TopkParams& tp, const int64_t* block_base, int64_t* out_idx,
+                 double* out_p, int* d_flag, cudaStream_t s);
 bool tc_gemm_supported(int64_t nbt, int64_t M, int64_t N, int64_t K, int64_t sa_bt, int64_t sa_m, int64_t sa_k);
 int tc_gemm_bn(int64_t N);
 // A/A_lo: 16-bit complex [bt][M][K] (k contiguous); Bx/Bx_lo: expanded operand.

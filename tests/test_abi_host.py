@@ -124,4 +124,14 @@ def test_topk_argument_validation(lib):
     with pytest.raises(lib.TNError):
         lib.tn_topk_postprocess(16, 4, 1024, 0, 1.0, 0, 16, np.arange(10), 16, 16)  # k = 0
     with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(16, 4, 1024, 513, 1.0, 0, 16, np.arange(10), 16, 16)  # per block: k <= 512
+    with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(16, 1, 1 << 17, 8, 1.0, 0, 16, np.arange(17), 16, 16)  # per block: B <= 2^16
+    with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(16, 4, 1024, 4097, 1.0, 1, 16, np.arange(10), 16, 16)  # global: k <= G*B
+    with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(16, 1 << 20, 1 << 21, (1 << 26) + 1, 1.0, 1, 16, np.arange(21), 16, 16)  # k <= 2^26
+    with pytest.raises(lib.TNError):
+        lib.tn_topk_postprocess(16, 1 << 20, 1 << 21, 8, 1.0, 1, 16, np.arange(21), 16, 16)  # G*B <= 2^40
+    with pytest.raises(lib.TNError):
         lib.tn_xeb(16, 0, 10)
