@@ -48,24 +48,28 @@ def _engine():
     return engine
 
 
-def _metropolis(p: np.ndarray, n_chains: int, n_steps: int, burn: int, seed: int) -> np.ndarray:
+def _metropolis(p, n_chains: int, n_steps: int, burn: int, seed: int):
     """Independent Metropolis chains over all strings, uniform proposals,
-    acceptance min(1, p(y) / p(x)); the states after the burn-in."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    N = p.size
-    x = rng.integers(0, N, size=n_chains)
+    acceptance min(1, p(y) / p(x)); the states after the burn-in (device
+    arrays: the 30-qubit case has 2^30 candidates)."""
+    import torch
+    g = torch.Generator(device=p.device)
+    g.manual_seed(seed)
+    N = p.numel()
+    x = torch.randint(0, N, (n_chains,), generator=g, device=p.device)
     out = []
     for t in range(n_steps):
-        y = rng.integers(0, N, size=n_chains)
-        u = rng.random(n_chains)
-        acc = u * p[x] < p[y]
-        x = np.where(acc, y, x)
+        y = torch.randint(0, N, (n_chains,), generator=g, device=p.device)
+        u = torch.rand(n_chains, generator=g, device=p.device, dtype=torch.float64)
+        x = torch.where(u * p[x] < p[y], y, x)
         if t >= burn:
-            out.append(x.copy())
-    return np.concatenate(out)
+            out.append(x.clone())
+    return torch.cat(out)
 
 
 def _study(E, w, psi, k, batch, prec="fp16"):
+    """Per D: contract f = 2^-D of the sub-networks, keep the global top k, score
+    them with the state vector's q; the large arrays stay on the device."""
     from paper_2406_18889_gb300 import binding as B
     import torch
     n = w.n_qubits
@@ -74,24 +78,28 @@ def _study(E, w, psi, k, batch, prec="fp16"):
     plan = E.Plan(prep.tn, prep.tree, prec=prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=batch)
     base = torch.zeros(1, dtype=torch.int64, device="cuda")
     pos = w.open_bit_pos()
-    exact = psi.reshape(-1)
-    q = np.abs(exact) ** 2
+    exact = torch.from_numpy(psi.reshape(-1)).to("cuda")  # O1 amplitudes, index = n-bit string
+    q = exact.abs() ** 2
+    e_norm = float(q.sum())
     rows = []
     for D in range(0, 5):
         ids = W.draw_slice_subset(S, S >> D, seed=1000 + D)
         f = len(ids) / S
         amps = plan.contract(ids)
         idx, _ = E.topk(amps, k, 1.0 / f, base, pos, global_mode=True)
-        x_topk = pp.xeb(q[idx.cpu().numpy()], n)
-        a = amps.cpu().numpy().reshape(-1)
-        F = pp.numerical_fidelity(a, exact)
-        p = np.abs(a) ** 2
+        x_topk = pp.xeb(q[idx].cpu().numpy(), n)
+        a = amps.reshape(-1)
+        # numerical fidelity: normalised overlap of the contracted and exact amplitudes
+        ov = torch.vdot(a, exact)
+        F = float((ov.abs() ** 2) / ((a.abs() ** 2).sum() * e_norm))
+        p = a.abs() ** 2
+        del a, amps
         samples = _metropolis(p, n_chains=1024, n_steps=96, burn=32, seed=77 + D)
-        x_mcmc = pp.xeb(q[samples], n)
+        x_mcmc = pp.xeb(q[samples].cpu().numpy(), n)
+        del p
         rows.append(dict(D=D, f=f, F_num=F, xeb_topk=x_topk, ratio=x_topk / F, xeb_mcmc=x_mcmc))
         print(f"n={n} D={D} f={f:.4f} F_num={F:.4f} XEB_topk={x_topk:.4f} "
               f"XEB_topk/F_num={x_topk / F:.4f} XEB_topk/f={x_topk / f:.4f} XEB_mcmc={x_mcmc:.4f}", flush=True)
-        del amps
     plan.close()
     return rows
 
@@ -123,6 +131,6 @@ def test_topk_amplification_24_qubits(sv_grid4x6):
 def test_topk_amplification_30_qubits_paper_scale():
     E = _engine()
     w = W.workload("grid4x6_d14", rows=5, cols=6, l=30, G=1, seed=SEED0 + 6)
-    psi = sv.simulate(w.circuit)
+    psi = sv.simulate(w.circuit)  # 16 GiB, plain C oracle on the host cores
     rows = _study(E, w, psi, k=1 << 15, batch=4)
     _check(rows, 30, 1 << 15)
