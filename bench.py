@@ -387,6 +387,24 @@ def run_ours(args):
     # recorded kernels + slice-id uploads (one launch per 256 ids of each batch) + top-k + XEB
     n_batches = -(-S // args.batch)
     launches_per_step = prof["n_launches"] + n_batches * (-(-args.batch // 256)) + 2
+    # complex64 accuracy on the tensor cores: fp16 hi + lo operands, K accumulated
+    # one k tile at a time in FP32 (relative L2 8.7e-6 on this workload, the
+    # complex64 path's 8.4e-6; tests/test_gpu_precision.py holds it to 1e-5)
+    fine_value = None
+    if args.prec != "c64" and not args.no_c64:
+        planf = E.Plan(prep.tn, prep.tree, prec="fp16", max_slice_batch=args.batch,
+                       flags=B.TN_FLAG_HILO | B.TN_FLAG_FINE_ACC |
+                       (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT))
+        for _ in range(2):
+            planf.contract(ids, out=amps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            planf.contract(ids, out=amps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fine_value = S * 3 / (e0.elapsed_time(e1) / 1e3)
+        planf.close()
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
         plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch,
@@ -425,6 +443,11 @@ def run_ours(args):
         "complex64_path": None if c64_value is None else {
             "value": c64_value, "unit": "slices/s", "speedup": value / c64_value,
             "note": "same workload and batch through the complex64 CUDA-core path (contraction only)"},
+        "complex64_accuracy_tensor_core_path": None if fine_value is None else {
+            "value": fine_value, "unit": "slices/s",
+            "vs_complex64_path": None if c64_value is None else fine_value / c64_value,
+            "note": "fp16 hi+lo operands, K accumulated one k tile at a time in FP32 (TN_FLAG_HILO | "
+                    "TN_FLAG_FINE_ACC): complex64 accuracy on the tensor cores (contraction only)"},
         "useful_flops_per_slice": useful_per_slice,
         "wall_s": wall,
         "roofline": roofline,

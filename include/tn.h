@@ -62,7 +62,12 @@ typedef enum {
                                         split-precision operands (hi + lo, three passes) */
 #define TN_FLAG_TC_PAIR 0x10u        /* reduced precision: tensor-core steps with 256-column tiles
                                         run as two-CTA clusters that share each B tile (TMA
-                                        multicast), halving B's reads from L2 */
+                                        multicast), halving B's reads from L2 (not combined with
+                                        chunked accumulation) */
+#define TN_FLAG_FINE_ACC 0x20u       /* reduced precision: tensor-core steps accumulate K one k tile
+                                        (64 real products) at a time, summed in FP32 registers;
+                                        with TN_FLAG_HILO the result has complex64 accuracy (without
+                                        it, TN_FLAG_HILO accumulates 4 k tiles at a time) */
 
 typedef struct tn_plan_s* tn_plan_t;
 

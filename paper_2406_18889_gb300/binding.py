@@ -24,6 +24,7 @@ TN_FLAG_NO_GRAPH = 0x2
 TN_FLAG_PLAN_ONLY = 0x4
 TN_FLAG_HILO = 0x8
 TN_FLAG_TC_PAIR = 0x10
+TN_FLAG_FINE_ACC = 0x20
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",

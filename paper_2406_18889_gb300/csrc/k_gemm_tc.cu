@@ -82,6 +82,8 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
   const int bn = p.bn;
   TN_CHECK(!p.cluster2 || p.out_kind == 2 || bn == 256, TN_ERR_UNSUPPORTED,
            "two-CTA tensor-core form: 16-bit output needs tile width 256");
+  TN_CHECK(p.acc_split >= 0 && !(p.cluster2 && p.acc_split), TN_ERR_UNSUPPORTED,
+           "chunked accumulation runs on single CTAs");
   {
     // stage the epilogue when n is the output's more contiguous index
     const int64_t big = int64_t(1) << 62;
@@ -334,6 +336,12 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
     diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
     TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
     p.cluster2 = 1;
+    launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
+    diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
+    // and single CTAs accumulating K in chunks summed in FP32 registers
+    TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
+    p.cluster2 = 0;
+    p.acc_split = 2;
     launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
     diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
     unsigned h[2] = {0, 0};

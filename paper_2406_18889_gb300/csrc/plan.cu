@@ -535,7 +535,11 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     tp.scale = scale;
     tp.err = P.d_err;
     tp.bn = tc_gemm_bn(r.N);
-    tp.cluster2 = (P.flags & TN_FLAG_TC_PAIR) && tp.bn == 256 ? 1 : 0;
+    // split products also accumulate K in chunks (the tensor cores' own
+    // accumulation error grows with K): 4 k tiles, or 1 with TN_FLAG_FINE_ACC;
+    // single CTAs then
+    tp.acc_split = (P.flags & TN_FLAG_FINE_ACC) ? 1 : S.hilo ? 4 : 0;
+    tp.cluster2 = !tp.acc_split && (P.flags & TN_FLAG_TC_PAIR) && tp.bn == 256 ? 1 : 0;
     const char* a_hi = X.base(r.a_node);
     R.begin(5, flops, bytes);
     launch_gemm_tc(a_hi, S.hilo ? a_hi + NA.elems * 4 : nullptr, r.a_bt, r.a_m, bx, bx_lo, tp,

@@ -193,6 +193,19 @@ __device__ __forceinline__ void store_el(char* Cb, char* C2b, int64_t o, float r
   }
 }
 
+// 16 consecutive accumulator columns of this warp's TMEM lane quarter
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -206,7 +219,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // so every SM reads a third less from L2 per k step.  A stage is refilled only
 // after both CTAs' MMAs released it (their commits arrive on both CTAs'
 // `empty` barriers).
-template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT>
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
@@ -295,16 +308,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(BN, BF16);
+      // accumulation units: one per tile, or (SPLIT) one per chunk of k tiles;
+      // the two TMEM buffers alternate between consecutive units
+      // SPLIT: K accumulated in chunks of p.acc_split k tiles; each chunk's
+      // partial sums are added in FP32 registers by the epilogue (round to
+      // nearest), so the tensor cores never accumulate more than
+      // p.acc_split * BK real products
+      const int kch = SPLIT ? p.acc_split : k_tiles;
       int64_t g = 0;
-      int64_t local = 0;
+      int64_t gu = 0;
       bool stop = false;
-      for (int64_t t = unit0; t < tiles && !stop; t += ustride, ++local) {
-        const int b = (int)(local & 1);
-        const uint32_t u = (uint32_t)(local >> 1);
-        if (local >= 2 && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) break;
+      for (int64_t t = unit0; t < tiles && !stop; t += ustride)
+      for (int c0 = 0; c0 < k_tiles && !stop; c0 += kch, ++gu) {
+        const int c1 = c0 + kch < k_tiles ? c0 + kch : k_tiles;
+        const int b = (int)(gu & 1);
+        const uint32_t u = (uint32_t)(gu >> 1);
+        if (gu >= 2 && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) {
+          stop = true;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc_addr = tmem + (uint32_t)(b * BN);
-        for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+        for (int kt = c0; kt < c1; ++kt, ++g) {
           const int s = (int)(g % S);
           if (!wait_bounded(&full[s], (uint32_t)((g / S) & 1), p.err)) {
             stop = true;
@@ -317,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t ad = sw128_desc(a0 + kk * 32);
             const uint64_t bd = sw128_desc(b0 + kk * 32);
-            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            const uint32_t acc = (kt > c0 || kk > 0) ? 1u : 0u;
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
                 "setp.ne.b32 p, %4, 0;\n\t"
@@ -336,14 +361,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                              smem_u32(&empty[s]))
                          : "memory");
         }
-        // tfull[b] completes when this tile's MMAs (and all earlier ones) finish
+        // tfull[b] completes when this unit's MMAs (and all earlier ones) finish
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&tfull[b]))
                      : "memory");
       }
-      // before TMEM is freed: wait (bounded) for the last committed tile's MMAs
-      if (local > 0) {
-        const int64_t last = local - 1;
+      // before TMEM is freed: wait (bounded) for the last committed unit's MMAs
+      if (gu > 0) {
+        const int64_t last = gu - 1;
         const uint64_t t0 = gtimer();
         while (!mbar_try_wait(&tfull[last & 1], (uint32_t)((last >> 1) & 1)) && gtimer() - t0 < kWaitNs) {
         }
@@ -369,6 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* stg = reinterpret_cast<uint32_t*>(stage_buf + ew * 32 * kStagePitch);
     int64_t* rb = row_base + ew * 32;
     int64_t local = 0;
+    int64_t gu = 0;  // SPLIT: accumulation units consumed
     for (int64_t t = unit0; t < tiles; t += ustride, ++local) {
       const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
       const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
@@ -379,6 +405,64 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool row_ok = mbase + quarter * 32 + lane < p.M;
       // the tile lies wholly inside M x N (a cluster's second tile may lie past M)
       const bool whole = mbase + BM <= p.M && nbase + BN / 2 <= p.N;
+      if constexpr (SPLIT) {
+        // sum the tile's K chunks in FP32 registers, then store once
+        constexpr int kMaxCh = (kChunks + kGroups - 1) / kGroups;
+        float acc[kMaxCh][32];
+#pragma unroll
+        for (int ci = 0; ci < kMaxCh; ++ci)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[ci][j] = 0.f;
+        bool ok_all = true;
+        for (int c0 = 0; c0 < k_tiles; c0 += p.acc_split, ++gu) {
+          const int b = (int)(gu & 1);
+          const uint32_t u = (uint32_t)(gu >> 1);
+          const bool ok = __all_sync(0xffffffffu, wait_bounded(&tfull[b], u & 1, p.err));
+          ok_all = ok_all && ok;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (ok) {
+#pragma unroll
+            for (int ci = 0; ci < kMaxCh; ++ci) {
+              const int c = cgrp + ci * kGroups;
+              if (c < kChunks) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  uint32_t v[16];
+                  tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c * 32 + h * 16), v);
+#pragma unroll
+                  for (int j = 0; j < 16; ++j) acc[ci][h * 16 + j] += __uint_as_float(v[j]);
+                }
+              }
+            }
+          }
+          // hand the accumulator buffer back to the MMA thread
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        if (ok_all) {
+#pragma unroll
+          for (int ci = 0; ci < kMaxCh; ++ci) {
+            const int c = cgrp + ci * kGroups;
+            if (c >= kChunks) continue;
+            const int j0 = c * 16;
+            if (whole) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], acc[ci][2 * j] * p.scale,
+                                             acc[ci][2 * j + 1] * p.scale);
+            } else if (row_ok) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                if (nbase + j0 + j >= p.N) break;
+                store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], acc[ci][2 * j] * p.scale,
+                                             acc[ci][2 * j + 1] * p.scale);
+              }
+            }
+          }
+        }
+        continue;
+      }
       // every epilogue thread runs every iteration; after a timed-out wait
       // (warp-uniform) the tile's reads and stores are skipped
       const bool ok = __all_sync(0xffffffffu, wait_bounded(&tfull[b], u & 1, p.err));
@@ -466,11 +550,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT>
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT = false>
 void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
   const size_t sm = smem_bytes<BN, STAGE>();
-  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2, F32OUT>;
+  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2, F32OUT, SPLIT>;
   static bool attr = false;
   if (!attr) {
     TN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -519,6 +603,14 @@ void launch_tc4(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap
 template <int BN, bool BF16, bool HILO>
 void launch_tc3(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
+  // K accumulated in chunks: single CTAs, direct stores along m (no staging)
+  if (p.acc_split) {
+    if (p.out_kind == 2)
+      launch_tc6<BN, BF16, HILO, false, false, true, true>(ma, ma2, mb, mb2, p, s);
+    else
+      launch_tc6<BN, BF16, HILO, false, false, false, true>(ma, ma2, mb, mb2, p, s);
+    return;
+  }
   if (p.stage_n)
     launch_tc4<BN, BF16, HILO, true>(ma, ma2, mb, mb2, p, s);
   else

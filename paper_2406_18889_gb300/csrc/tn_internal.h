@@ -123,6 +123,7 @@ struct TcGemmParams {
   int bn;                     // real-column tile (32, 64, 128 or 256)
   int stage_n;                // write tiles out along n (n is the output's contiguous index)
   int cluster2;               // two-CTA clusters sharing B tiles by TMA multicast
+  int acc_split;              // > 0: accumulate K in chunks of this many k tiles, summed in FP32 registers
 };
 
 // ------------------------------------------------------------ launchers

@@ -98,3 +98,19 @@ def test_tc_pair_clusters_match_single_ctas(E, grid, prec, flags):
     b = pair.contract().cpu().numpy()
     assert np.array_equal(a, b)
     assert pp.relative_l2(b, ref) <= LOWP_TOL
+
+
+@pytest.mark.parametrize("prec,flags,tol", [
+    ("fp16", "hilo", 2e-5), ("bf16", "hilo", 3e-5), ("fp16", "hilo+fine", 1e-5)],
+    ids=["fp16+hilo", "bf16+hilo", "fp16+hilo+fine"])
+def test_chunked_accumulation_accuracy(E, grid, prec, flags, tol):
+    # the tensor cores' own accumulation error grows with K; split products
+    # accumulate K in chunks summed in FP32 registers (4 k tiles, or 1 with
+    # TN_FLAG_FINE_ACC, which meets the complex64 bar of 1e-5)
+    from paper_2406_18889_gb300 import binding as B
+    w, psi, ref, x_ref, prep = grid
+    f = B.TN_FLAG_HILO | (B.TN_FLAG_FINE_ACC if "fine" in flags else 0)
+    plan = E.Plan(prep.tn, prep.tree, prec=prec, flags=f | B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=64)
+    got = plan.contract().cpu().numpy()
+    err = pp.relative_l2(got, ref)
+    assert err <= tol, err
