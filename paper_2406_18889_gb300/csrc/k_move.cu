@@ -240,8 +240,20 @@ __global__ void accumulate_kernel(const float2* __restrict__ root, int64_t sb, i
   const int nv = *n_valid;
   double re = 0.0, im = 0.0;
   const float2* p = root + g * sg + j * sj;
-  for (int b = 0; b < nv; ++b) {
-    float2 v = p[b * sb];
+  // loads issued eight at a time (independent), summed in batch order
+  int b = 0;
+  for (; b + 8 <= nv; b += 8) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = p[(b + u) * sb];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      re += (double)v[u].x;
+      im += (double)v[u].y;
+    }
+  }
+  for (; b < nv; ++b) {
+    const float2 v = p[b * sb];
     re += (double)v.x;
     im += (double)v.y;
   }

@@ -80,10 +80,12 @@ __global__ void __launch_bounds__(kSortN) topk_kernel(const double2* __restrict_
   Key mine;
   mine.p = -1.0;
   mine.idx = 0x7fffffffffffffffLL;
+  // the first pass fills all kSortN slots; later passes refill slots [k, kSortN)
+  // while slots [0, k) carry the best so far (a block of <= kSortN strings: one sort)
   const int chunk = kSortN - k;
-  for (long long start = 0; start < n_total; start += chunk) {
-    if (i >= k) {
-      long long e = start + (i - k);
+  for (long long start = 0; start < n_total; start += (start == 0 ? kSortN : chunk)) {
+    if (start == 0 || i >= k) {
+      long long e = start == 0 ? i : start + (i - k);
       if (e < n_total) {
         long long g = tp.global_mode ? e / tp.Bsz : g0;
         long long j = tp.global_mode ? e % tp.Bsz : e;
