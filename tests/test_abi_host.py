@@ -135,3 +135,62 @@ def test_topk_argument_validation(lib):
         lib.tn_topk_postprocess(16, 1 << 20, 1 << 21, 8, 1.0, 1, 16, np.arange(21), 16, 16)  # G*B <= 2^40
     with pytest.raises(lib.TNError):
         lib.tn_xeb(16, 0, 10)
+
+
+@pytest.fixture(scope="module")
+def bench_plan_steps(lib):
+    # the 24-qubit workload's reduced-precision plan with invariant subtrees hoisted
+    from paper_2406_18889_gb300 import engine as E
+    w = W.workload("grid4x6_d14")
+    prep = E.prepare(w)
+    h = _create(lib, prep, flags=lib.TN_FLAG_PLAN_ONLY | lib.TN_FLAG_HOIST_INVARIANT, prec=2, max_slice_batch=64)
+    st = lib.tn_plan_steps(h)
+    lib.tn_plan_destroy(h)
+    return prep, st
+
+
+def test_fused_expansion_pairs(lib, bench_plan_steps):
+    # every producer that writes an expanded operand (bit 5) is a per-batch CUDA-core
+    # step with K <= 4 whose consumer is a tensor-core step marked as fed (bit 6)
+    prep, st = bench_plan_steps
+    k = st["kinds"]
+    n_leaves = len(prep.tn.leaf_edges)
+    pairs = np.asarray(prep.tree.pairs)
+    consumer = {}
+    for t, (a, b) in enumerate(pairs):
+        consumer[a] = t
+        consumer[b] = t
+    producers = np.where(k & 32)[0]
+    assert len(producers) >= 1
+    for t in producers:
+        assert not k[t] & 8 and not k[t] & 4 and st["k"][t] <= 4
+        u = consumer[n_leaves + t]
+        assert k[u] & 8 and k[u] & 64
+    assert (k & 64 > 0).sum() == len(producers)
+
+
+def test_fused_small_steps(lib, bench_plan_steps):
+    # small steps (bit 7): per-batch, CUDA cores, K <= 4, <= 2^14 outputs, operands
+    # from leaves, hoisted results or other small steps
+    prep, st = bench_plan_steps
+    k = st["kinds"]
+    n_leaves = len(prep.tn.leaf_edges)
+    pairs = np.asarray(prep.tree.pairs)
+    micro = np.where(k & 128)[0]
+    assert len(micro) >= 1
+    for t in micro:
+        assert not k[t] & 4 and not k[t] & 8 and not k[t] & 32
+        assert st["k"][t] <= 4 and st["batch"][t] * st["m"][t] * st["n"][t] <= 1 << 14
+        for x in pairs[t]:
+            if x >= n_leaves:
+                q = x - n_leaves
+                assert k[q] & 4 or k[q] & 128
+
+
+def test_tensor_core_steps_carry_the_flops(lib, bench_plan_steps):
+    prep, st = bench_plan_steps
+    k = st["kinds"]
+    cost = st["batch"] * st["m"] * st["n"] * st["k"]
+    per_batch = (k & 4) == 0
+    tc = (k & 8) > 0
+    assert cost[per_batch & tc].sum() >= 0.99 * cost[per_batch].sum()
