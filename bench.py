@@ -462,6 +462,57 @@ def run_ours(args):
     plan.close()
 
 
+def run_uneven(args):
+    """The 64 uneven circuits contracted in one tn_contract_slices_batched call
+    (every slice of every circuit, FP64 sums per circuit), on one GPU."""
+    import torch
+    import workloads as W
+    from paper_2406_18889_gb300 import binding as B
+    from paper_2406_18889_gb300 import engine as E
+    torch.cuda.set_device(0)
+    ws = W.configs.uneven_batch(64)
+    t0 = time.perf_counter()
+    preps = [E.prepare(w, restarts=1) for w in ws]
+    plan_s = time.perf_counter() - t0
+    flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
+    # slice batch at most 16: at 64 the largest (28-qubit) circuit alone needs a 164 GB workspace
+    batch = min(args.batch, 16)
+    plans = [E.Plan(p.tn, p.tree, prec=args.prec, flags=flags, own_workspace=False,
+                    max_slice_batch=min(batch, 1 << len(p.tree.sliced_edges))) for p in preps]
+    outs = [torch.empty((w.G, 1 << w.l), dtype=torch.complex128, device="cuda") for w in ws]
+    wsz = max(max(p.info["workspace_bytes"], 256) for p in plans)
+    wsb = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+    ids = [np.arange(p.n_slices_total, dtype=np.int64) for p in plans]
+    slices = sum(len(x) for x in ids)
+    flops = sum(p.info["useful_flops_per_slice"] * len(x) for p, x in zip(plans, ids))
+    stream = torch.cuda.current_stream()
+
+    def call():
+        B.tn_contract_slices_batched([p.handle for p in plans], ids, [o.data_ptr() for o in outs], 0,
+                                     wsb.data_ptr(), wsz, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({
+        "metric": "uneven 64-circuit batch slices/s on 1 GB300", "value": slices / (ms / 1e3),
+        "unit": "slices/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": "64 seeded circuits, 4x4..4x7 grids, depth 10..16, 2^2..2^8 slices, "
+                               "l = 8, G = 16 (16..28 qubits)", "circuits": len(ws), "slices": slices,
+                   "slice_batch": batch, "hilo": args.hilo, "l2": "not flushed (one batched call)"},
+        "useful_tflops": flops / (ms / 1e3) / 1e12, "host_planning_s": plan_s}), flush=True)
+    for p in plans:
+        p.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,10 +528,15 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="run warm-up and timed steps only (for ncu launch lists)")
+    ap.add_argument("--workload", default="grid4x6_d14", choices=["grid4x6_d14", "uneven64"],
+                    help="uneven64: the 64-circuit batch (4x4..4x7 grids, depth 10..16, 2^2..2^8 "
+                         "slices, l = 8, G = 16) in one batched call, timed as total slices / call time")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.workload == "uneven64":
+        run_uneven(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -36,7 +36,8 @@ class Plan:
     """A contraction plan living on the current CUDA device."""
 
     def __init__(self, tn: TensorNetwork, tree: Tree, prec: str = "c64", flags: int = 0,
-                 max_slice_batch: int = 64, mem_cap_bytes: int = 0, stream=None):
+                 max_slice_batch: int = 64, mem_cap_bytes: int = 0, stream=None,
+                 own_workspace: bool = True):
         torch = _torch()
         self.tn, self.tree = tn, tree
         self.n_slices_total = 1 << len(tree.sliced_edges)
@@ -51,8 +52,9 @@ class Plan:
         self.J = 1
         for e in tn.open_edges:
             self.J *= tn.edge_dim[e]
+        # plans run back to back in one batched call share the caller's workspace
         self.workspace = torch.empty(max(self.info["workspace_bytes"], 256), dtype=torch.uint8,
-                                     device="cuda")
+                                     device="cuda") if own_workspace else None
 
     def steps(self) -> dict:
         return B.tn_plan_steps(self.handle)
@@ -66,6 +68,8 @@ class Plan:
         if out is None:
             out = torch.empty((self.G, self.J), dtype=torch.complex128, device="cuda")
         s = stream if stream is not None else torch.cuda.current_stream()
+        if self.workspace is None:
+            raise ValueError("plan created without a workspace: use tn_contract_slices_batched")
         B.tn_contract_slices(self.handle, slice_ids, out.data_ptr(), int(accumulate),
                              self.workspace.data_ptr(), self.workspace.numel(), s.cuda_stream)
         return out
