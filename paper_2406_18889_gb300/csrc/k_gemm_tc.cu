@@ -91,6 +91,11 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     // only for write-heavy tiles (up to four k tiles); deeper tiles hide the per-row stores
     p.stage_n = (sn < sm && 2 * p.K <= 4 * BK) ? 1 : 0;
   }
+  {
+    // offsets inside a tile are at most those of its all-ones row and column indices
+    const int64_t local_max = run_offset(p.c_m, BM - 1) + run_offset(p.c_n, bn / 2 - 1);
+    p.off32 = local_max < (int64_t(1) << 31) ? 1 : 0;
+  }
   const uint64_t pitch = (uint64_t)((2 * p.K + BK - 1) / BK * BK);
   CUtensorMap ma, ma2, mb, mb2;
   const uint64_t a_row = (uint64_t)sa_m * 4, a_bt = p.nbt > 1 ? (uint64_t)sa_bt * 4 : a_row * (uint64_t)p.M;

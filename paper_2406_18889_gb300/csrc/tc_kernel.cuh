@@ -141,13 +141,13 @@ constexpr size_t kStageBytes = kEpiWarps * 32 * kStagePitch * 8 + kEpiWarps * 32
 // barriers, the column-offset table and (STAGE) the epilogue staging, at most 8
 template <int BN, bool STAGE = false>
 __host__ __device__ constexpr int stages_for() {
-  constexpr long budget = 232448 - 1024 - 256 - (long)BN / 2 * 8 - (STAGE ? (long)kStageBytes : 0L) - 512;
+  constexpr long budget = 232448 - 1024 - 256 - (long)BN / 2 * 12 - (STAGE ? (long)kStageBytes : 0L) - 512;
   constexpr long per = (long)(BM + BN) * BK * 2;
   return budget / per > 8 ? 8 : (int)(budget / per);
 }
 template <int BN, bool STAGE>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)stages_for<BN, STAGE>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 8 +
+  return 1024 + (size_t)stages_for<BN, STAGE>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 12 +
          (STAGE ? kStageBytes : 0);
 }
 
@@ -179,6 +179,17 @@ __device__ __forceinline__ uint32_t resid16(float re, float im, uint32_t w) {
     h = __half22float2(x);
   }
   return pack16<BF16>(re - h.x, im - h.y);
+}
+// the same at 32-bit element offset o from a tile's base pointers
+template <bool BF16, bool HILO, bool F32OUT>
+__device__ __forceinline__ void store_el32(char* Ct, char* C2t, uint32_t o, float re, float im) {
+  if constexpr (F32OUT) {
+    *reinterpret_cast<float2*>(Ct + (size_t)o * 8) = make_float2(re, im);
+  } else {
+    const uint32_t h = pack16<BF16>(re, im);
+    *reinterpret_cast<uint32_t*>(Ct + (size_t)o * 4) = h;
+    if constexpr (HILO) *reinterpret_cast<uint32_t*>(C2t + (size_t)o * 4) = resid16<BF16>(re, im, h);
+  }
 }
 // one complex output element at element offset o: fp32 pair, or 16-bit pair
 // (plus its residual in the second array when split)
@@ -235,7 +246,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int64_t* n_rel = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 256);  // [BN / 2]
-  float2* stage_buf = reinterpret_cast<float2*>(n_rel + BN / 2);                         // [warps][32][pitch]
+  uint32_t* n32 = reinterpret_cast<uint32_t*>(n_rel + BN / 2);                           // [BN / 2]
+  float2* stage_buf = reinterpret_cast<float2*>(n32 + BN / 2);                           // [warps][32][pitch]
   int64_t* row_base = reinterpret_cast<int64_t*>(stage_buf + kEpiWarps * 32 * kStagePitch);  // [warps][32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -385,8 +397,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Tile-relative output offsets, once per CTA: tile origins are multiples of
     // the (power-of-two) tile extents, and a run offset is linear over disjoint
     // index bits, so offset(origin + i) = offset(origin) + offset(i).
-    for (int j = et; j < BN / 2; j += 32 * kEpiWarps) n_rel[j] = run_offset(p.c_n, j);
+    for (int j = et; j < BN / 2; j += 32 * kEpiWarps) {
+      n_rel[j] = run_offset(p.c_n, j);
+      n32[j] = (uint32_t)n_rel[j];  // used when p.off32: a tile's offsets fit in 32 bits
+    }
     const int64_t m_rel = run_offset(p.c_m, quarter * 32 + lane);
+    const uint32_t m32 = (uint32_t)m_rel;
+    constexpr int ES = F32OUT ? 8 : 4;  // bytes per output element
     asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
     char* const Cb = reinterpret_cast<char*>(p.C);
     char* const C2b = reinterpret_cast<char*>(p.C2);
@@ -401,7 +418,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int b = (int)(local & 1);
       const uint32_t u = (uint32_t)(local >> 1);
       const int64_t nbase = (int64_t)n_tile * BN / 2, mbase = (int64_t)m_tile * BM;
-      const int64_t row = run_offset(p.c_bt, bt) + run_offset(p.c_m, mbase) + run_offset(p.c_n, nbase) + m_rel;
+      const int64_t tbase = run_offset(p.c_bt, bt) + run_offset(p.c_m, mbase) + run_offset(p.c_n, nbase);
+      const int64_t row = tbase + m_rel;
+      char* const Ct = Cb + tbase * ES;
+      char* const C2t = HILO ? C2b + tbase * 4 : nullptr;
       const bool row_ok = mbase + quarter * 32 + lane < p.M;
       // the tile lies wholly inside M x N (a cluster's second tile may lie past M)
       const bool whole = mbase + BM <= p.M && nbase + BN / 2 <= p.N;
@@ -446,7 +466,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int c = cgrp + ci * kGroups;
             if (c >= kChunks) continue;
             const int j0 = c * 16;
-            if (whole) {
+            if (whole && p.off32) {
+#pragma unroll
+              for (int j = 0; j < 16; j += 4) {
+                const uint4 nn = *reinterpret_cast<const uint4*>(n32 + j0 + j);
+                const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  store_el32<BF16, HILO, F32OUT>(Ct, C2t, m32 + o4[q], acc[ci][2 * (j + q)] * p.scale,
+                                                 acc[ci][2 * (j + q) + 1] * p.scale);
+              }
+            } else if (whole) {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
                 store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], acc[ci][2 * j] * p.scale,
@@ -520,6 +550,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           __syncwarp();
+        } else if (whole && p.off32) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            const uint4 nn = *reinterpret_cast<const uint4*>(n32 + j0 + j);
+            const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              store_el32<BF16, HILO, F32OUT>(Ct, C2t, m32 + o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
+                                             __uint_as_float(v[2 * (j + q) + 1]) * p.scale);
+          }
         } else if (whole) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)

@@ -124,6 +124,7 @@ struct TcGemmParams {
   int stage_n;                // write tiles out along n (n is the output's contiguous index)
   int cluster2;               // two-CTA clusters sharing B tiles by TMA multicast
   int acc_split;              // > 0: accumulate K in chunks of this many k tiles, summed in FP32 registers
+  int off32;                  // every offset inside a tile (from its base) fits in 32 bits (set by the launcher)
 };
 
 // ------------------------------------------------------------ launchers
