@@ -202,7 +202,16 @@ KIND_NAMES = {0: "gemm_cuda_core", 1: "bit_permute", 2: "gather", 3: "accumulate
 DOMINANT_TRAFFIC = {("fp16", 64, False, True): 2102178560}
 
 
-def roofline_from_profile(prof, cfg_key=None) -> tuple:
+def fp32_peak_measured(B) -> tuple:
+    """(TFLOP/s, source): the library's FP32 FMA microbenchmark on this GPU, else
+    the derived 152 SMs x 128 lanes x 2 flop x clock."""
+    try:
+        return float(B.tn_selftest_fp32_peak()), "measured: FP32 FMA microbenchmark (tn_selftest_fp32_peak)"
+    except Exception:
+        return fp32_alu_peak_tflops(), "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+
+
+def roofline_from_profile(prof, cfg_key=None, alu=None) -> tuple:
     """Per-launch rooflines of one profiled step (CUDA events around every launch).
 
     Each launch i has algorithmic FLOPs F_i and bytes B_i (operands and result
@@ -214,7 +223,7 @@ def roofline_from_profile(prof, cfg_key=None) -> tuple:
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
-    alu_peak = fp32_alu_peak_tflops()
+    alu_peak, alu_src = alu if alu is not None else (fp32_alu_peak_tflops(), "derived")
     src = "of measured" if peaks else "of fallback"
     kinds, ms, flops, nbytes = prof["kind"], prof["ms"], prof["flops"], prof["bytes"]
     per_kind = {}
@@ -245,7 +254,7 @@ def roofline_from_profile(prof, cfg_key=None) -> tuple:
              "peak_source": f"bf16_tflops burst {src} (fp16 dense rate is the same)"}
     elif k == 0 and tf >= tb:
         r = {"bound": "alu", "achieved": f / (t / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+             "peak_source": alu_src}
     else:
         r = {"bound": "hbm", "achieved": b / (t / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
              "peak_source": f"hbm_gbs {src}"}
@@ -382,7 +391,9 @@ def run_ours(args):
     # per-kernel roofline: one profiled pass (events around every launch)
     prof = B.tn_contract_slices_profile(plan.handle, ids, amps.data_ptr(), 0, plan.workspace.data_ptr(),
                                         plan.workspace.numel(), stream.cuda_stream)
-    roofline, per_kind = roofline_from_profile(prof, (args.prec, args.batch, bool(args.hilo), not args.no_hoist))
+    alu = fp32_peak_measured(B)
+    roofline, per_kind = roofline_from_profile(prof, (args.prec, args.batch, bool(args.hilo), not args.no_hoist),
+                                               alu)
     permute = permute_bandwidth(B, torch, stream)
     # recorded kernels + slice-id uploads (one launch per 256 ids of each batch) + top-k + XEB
     n_batches = -(-S // args.batch)
@@ -442,6 +453,8 @@ def run_ours(args):
         "useful_tflops": value * useful_per_slice / 1e12,
         "complex64_path": None if c64_value is None else {
             "value": c64_value, "unit": "slices/s", "speedup": value / c64_value,
+            "useful_tflops": c64_value * useful_per_slice / 1e12, "fp32_peak_tflops": alu[0],
+            "alu_frac": c64_value * useful_per_slice / 1e12 / alu[0], "fp32_peak_source": alu[1],
             "note": "same workload and batch through the complex64 CUDA-core path (contraction only)"},
         "complex64_accuracy_tensor_core_path": None if fine_value is None else {
             "value": fine_value, "unit": "slices/s",

@@ -53,6 +53,12 @@ typedef enum {
   TN_PREC_FP16 = 2  /* fp16 complex storage, real tensor-core GEMMs, FP32 accumulate */
 } tn_precision;
 
+/* Host-side fault injection (tests of callers' failure handling; no device
+ * work is done by a call that fails this way): the environment variable
+ * TN_FAULT=alloc makes tn_plan_create return TN_ERR_OOM, TN_FAULT=invalid_plan
+ * makes it return TN_ERR_INVALID_ARG, and TN_FAULT=stream makes the
+ * tn_contract_slices* calls return TN_ERR_CUDA, each before any device work. */
+
 /* tn_plan_options.flags */
 #define TN_FLAG_HOIST_INVARIANT 0x1u /* contract slice-independent subtrees once, at plan creation */
 #define TN_FLAG_NO_GRAPH 0x2u        /* launch kernels directly instead of replaying a CUDA graph */
@@ -302,6 +308,24 @@ tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* slice_ids, i
  */
 tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int32_t prec, uint64_t seed,
                               double* max_rel_err, void* stream);
+
+/*
+ * Failure detection self-test: one device thread waits, bounded by limit_ns
+ * nanoseconds of the global timer, on an mbarrier that nothing completes --
+ * the same bounded wait every persistent kernel of the library uses.  The
+ * wait must give up and raise its error flag: the call returns
+ * TN_ERR_TIMEOUT (the expected outcome) or TN_OK if the barrier completed.
+ * 1000 <= limit_ns <= 1e9.  Synchronises the stream; no GPU fault, no hang.
+ */
+tn_status tn_selftest_bounded_wait(uint64_t limit_ns, void* stream);
+
+/*
+ * Measured FP32 fused multiply-add throughput of the current device (the
+ * roofline of the complex64 CUDA-core path: 4 FMAs per complex
+ * multiply-add): *tflops = 2 flops per FMA / time, from CUDA events around
+ * 8 independent FMA chains per thread over 8 CTAs of 256 threads per SM.
+ */
+tn_status tn_selftest_fp32_peak(double* tflops, void* stream);
 
 /*
  * Index permutation of a tensor with power-of-two dimensions (paper Sec. III:

@@ -16,6 +16,8 @@ import numpy as np
 LIB_PATH = Path(__file__).resolve().parent / "_build" / "libtn.so"
 
 TN_OK = 0
+(TN_ERR_INVALID_ARG, TN_ERR_OOM, TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_UNSUPPORTED,
+ TN_ERR_NUMERIC) = 1, 2, 3, 4, 5, 6
 STATUS_NAMES = {0: "TN_OK", 1: "TN_ERR_INVALID_ARG", 2: "TN_ERR_OOM", 3: "TN_ERR_CUDA",
                 4: "TN_ERR_TIMEOUT", 5: "TN_ERR_UNSUPPORTED", 6: "TN_ERR_NUMERIC"}
 TN_PREC_C64, TN_PREC_BF16, TN_PREC_FP16 = 0, 1, 2
@@ -29,7 +31,7 @@ TN_FLAG_FINE_ACC = 0x20
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
            "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_plan_status",
-           "tn_permute", "tn_last_error", "tn_version")
+           "tn_permute", "tn_selftest_bounded_wait", "tn_selftest_fp32_peak", "tn_last_error", "tn_version")
 
 
 class TNError(RuntimeError):
@@ -92,6 +94,8 @@ def load() -> ctypes.CDLL:
     lib.tn_permute.argtypes = [vp, vp, i32, p_i32, i32, vp]
     lib.tn_selftest_gemm_tc.argtypes = [i64, i64, i64, i64, i32, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_double), vp]
+    lib.tn_selftest_bounded_wait.argtypes = [ctypes.c_uint64, vp]
+    lib.tn_selftest_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     for name in EXPORTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
     lib.tn_last_error.restype = ctypes.c_char_p
@@ -219,6 +223,17 @@ def tn_contract_slices_noalloc(plan: int, slice_ids, amps_ptr: int, accumulate: 
     _check(load().tn_contract_slices_noalloc(ctypes.c_void_p(plan), _p(ids, ctypes.c_int64), len(ids),
                                              ctypes.c_void_p(amps_ptr), int(accumulate),
                                              ctypes.c_void_p(stream)))
+
+
+def tn_selftest_bounded_wait(limit_ns: int, stream: int = 0) -> None:
+    """Raises TNError(TN_ERR_TIMEOUT) when the device wait gave up (the expected outcome)."""
+    _check(load().tn_selftest_bounded_wait(ctypes.c_uint64(int(limit_ns)), ctypes.c_void_p(stream)))
+
+
+def tn_selftest_fp32_peak(stream: int = 0) -> float:
+    out = ctypes.c_double()
+    _check(load().tn_selftest_fp32_peak(ctypes.byref(out), ctypes.c_void_p(stream)))
+    return out.value
 
 
 def tn_selftest_gemm_tc(nbt: int, M: int, N: int, K: int, prec: int, seed: int = 1, stream: int = 0) -> float:

@@ -1,5 +1,6 @@
 // The C ABI declared in include/tn.h.  Validation happens before any device
 // work; no C++ exception crosses the boundary.
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -66,9 +67,16 @@ static void* thread_scratch() {
   return p;
 }
 
+// TN_FAULT=<what>: host-side fault injection, checked before any device work
+static bool fault_injected(const char* what) {
+  const char* v = getenv("TN_FAULT");
+  return v && strcmp(v, what) == 0;
+}
+
 static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
                          size_t ws_bytes, cudaStream_t s, std::vector<LaunchRecord>* rec = nullptr) {
   TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
+  TN_CHECK(!fault_injected("stream"), TN_ERR_CUDA, "injected stream failure (TN_FAULT=stream)");
   TN_CHECK(amps != nullptr, TN_ERR_INVALID_ARG, "amps is null");
   TN_CHECK(n >= 0, TN_ERR_INVALID_ARG, "n_slices < 0");
   TN_CHECK(n == 0 || ids != nullptr, TN_ERR_INVALID_ARG, "slice_ids is null");
@@ -106,6 +114,8 @@ tn_status tn_plan_create(const tn_network_desc* net, const tn_tree_desc* tree, c
                          void* stream, tn_plan_t* out) {
   return guarded([&] {
     TN_CHECK(out != nullptr, TN_ERR_INVALID_ARG, "out is null");
+    TN_CHECK(!fault_injected("alloc"), TN_ERR_OOM, "injected allocation failure (TN_FAULT=alloc)");
+    TN_CHECK(!fault_injected("invalid_plan"), TN_ERR_INVALID_ARG, "injected invalid plan (TN_FAULT=invalid_plan)");
     auto p = build_plan(net, tree, opt, (cudaStream_t)stream);
     auto* h = new tn_plan_s{std::move(p)};
     *out = h;
@@ -165,6 +175,7 @@ tn_status tn_contract_slices_batched(const tn_plan_t* plans, int32_t n_plans, co
   return guarded([&] {
     TN_CHECK(n_plans >= 0, TN_ERR_INVALID_ARG, "n_plans < 0");
     TN_CHECK(n_plans == 0 || (plans && slice_ids && n_slices && amps), TN_ERR_INVALID_ARG, "null array");
+    TN_CHECK(!fault_injected("stream"), TN_ERR_CUDA, "injected stream failure (TN_FAULT=stream)");
     // validate every plan's arguments before queuing any work
     for (int32_t i = 0; i < n_plans; ++i) {
       TN_CHECK(plans[i] != nullptr, TN_ERR_INVALID_ARG, "plan is null");
@@ -267,6 +278,27 @@ tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, i
     if (r.stop) cudaEventDestroy(r.stop);
   }
   return st;
+}
+
+tn_status tn_selftest_bounded_wait(uint64_t limit_ns, void* stream) {
+  bool timed_out = false;
+  tn_status st = guarded([&] {
+    TN_CHECK(limit_ns >= 1000 && limit_ns <= 1000000000ull, TN_ERR_INVALID_ARG, "limit_ns out of range");
+    timed_out = selftest_bounded_wait(limit_ns, (cudaStream_t)stream);
+  });
+  if (st != TN_OK) return st;
+  if (timed_out) {
+    set_error("bounded wait gave up (expected)");
+    return TN_ERR_TIMEOUT;
+  }
+  return TN_OK;
+}
+
+tn_status tn_selftest_fp32_peak(double* tflops, void* stream) {
+  return guarded([&] {
+    TN_CHECK(tflops != nullptr, TN_ERR_INVALID_ARG, "tflops is null");
+    *tflops = selftest_fp32_peak((cudaStream_t)stream);
+  });
 }
 
 tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int32_t prec, uint64_t seed,

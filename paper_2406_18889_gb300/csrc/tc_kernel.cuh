@@ -74,17 +74,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// true when the phase with `parity` has completed; false on abort or timeout
-__device__ bool wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+// true when the phase with `parity` has completed; false on abort or after
+// limit_ns nanoseconds (then *err is raised)
+__device__ bool wait_bounded_ns(uint64_t* bar, uint32_t parity, int* err, uint64_t limit_ns) {
   const uint64_t t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     if (*(volatile int*)err) return false;
-    if (gtimer() - t0 > kWaitNs) {
+    if (gtimer() - t0 > limit_ns) {
       atomicExch(err, 1);
       return false;
     }
   }
   return true;
+}
+__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  return wait_bounded_ns(bar, parity, err, kWaitNs);
 }
 __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
                                             int z) {

@@ -208,6 +208,10 @@ void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Run
                      int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr,
                      float bscale = 1.0f);
 Runs single_run(int64_t extent, int64_t stride);
+// true when a wait on a barrier nothing completes gave up after limit_ns and raised its flag
+bool selftest_bounded_wait(uint64_t limit_ns, cudaStream_t s);
+// measured FP32 FMA throughput of the device (TFLOP/s, 2 flops per FMA)
+double selftest_fp32_peak(cudaStream_t s);
 RunDecode decode_of(const Runs& bt, const Runs& m, const Runs& n);
 int64_t expanded_b_bytes(int64_t nbt, int64_t N, int64_t K);
 double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,

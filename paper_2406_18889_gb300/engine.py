@@ -6,6 +6,7 @@ ABI (``binding``).
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
 
@@ -48,6 +49,7 @@ class Plan:
                                        tree.sliced_edges, PREC[prec], flags, max_slice_batch,
                                        mem_cap_bytes, s.cuda_stream)
         self.info = B.tn_plan_query(self.handle)
+        self.max_slice_batch = max_slice_batch
         self.G = tn.n_blocks
         self.J = 1
         for e in tn.open_edges:
@@ -84,6 +86,43 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def contract_checkpointed(plan: "Plan", slice_ids, path: str, chunk: Optional[int] = None, out=None,
+                          on_chunk=None):
+    """Sum the given slices in chunks, saving (ids, number finished, FP64 partial
+    sum) to the .npz file `path` after every chunk; a checkpoint already at
+    `path` for the same slice list is resumed from where it stopped.  Chunks are
+    processed in order and each adds into the FP64 sum, so a resumed run gives
+    the same bits as an uninterrupted one.  `on_chunk(i, n_done)` is called
+    after chunk i is saved (progress; an exception there leaves a valid
+    checkpoint behind)."""
+    torch = _torch()
+    ids = np.ascontiguousarray(np.asarray(slice_ids, dtype=np.int64))
+    chunk = int(chunk or plan.max_slice_batch)
+    if out is None:
+        out = torch.empty((plan.G, plan.J), dtype=torch.complex128, device="cuda")
+    done = 0
+    if os.path.exists(path):
+        ck = np.load(path)
+        if not np.array_equal(ck["ids"], ids):
+            raise ValueError(f"checkpoint {path} belongs to another slice list")
+        done = int(ck["done"])
+        out.copy_(torch.as_tensor(ck["amps"], device=out.device))
+    i = done // chunk
+    while done < len(ids):
+        part = ids[done:done + chunk]
+        plan.contract(part, out=out, accumulate=done > 0)
+        done += len(part)
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, ids=ids, done=np.int64(done), amps=out.cpu().numpy())
+        os.replace(tmp, path)
+        if on_chunk is not None:
+            on_chunk(i, done)
+        i += 1
+    if len(ids) == 0:
+        plan.contract([], out=out)
+    return out
 
 
 def topk(amps, k: int, inv_f: float, block_base, open_bit_pos, global_mode: bool = False, stream=None):

@@ -194,3 +194,15 @@ def test_tensor_core_steps_carry_the_flops(lib, bench_plan_steps):
     per_batch = (k & 4) == 0
     tc = (k & 8) > 0
     assert cost[per_batch & tc].sum() >= 0.99 * cost[per_batch].sum()
+
+
+@pytest.mark.parametrize("what,status", [("alloc", 2), ("invalid_plan", 1)])
+def test_injected_plan_faults(lib, prep, monkeypatch, what, status):
+    # host-side fault injection fails the call before any device work
+    monkeypatch.setenv("TN_FAULT", what)
+    with pytest.raises(lib.TNError) as ei:
+        _create(lib, prep)
+    assert ei.value.status == status
+    assert "TN_FAULT" in lib.tn_last_error()
+    monkeypatch.delenv("TN_FAULT")
+    lib.tn_plan_destroy(_create(lib, prep))
