@@ -72,15 +72,28 @@ __global__ void __launch_bounds__(256) hist_kernel(const double2* __restrict__ a
   const unsigned long long pp = idx_mode ? st->idx_prefix : st->prefix;
   const unsigned long long T = st->prefix;
   const unsigned long long dmask = (1ull << width) - 1;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
-    const double p = prob(amps, x, tp.inv_f);
-    if (!idx_mode && flag && isnan(p)) atomicExch(flag, 1);
-    unsigned long long key = key_of(p);
-    if (idx_mode) {
-      if (key != T) continue;
-      key = (unsigned long long)full_index(base[x / tp.Bsz], x % tp.Bsz, tp);
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop; lanes with the same digit add once per warp (the digits
+  // of p crowd into a few exponent bins)
+  for (long long wb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); wb < n;
+       wb += (long long)gridDim.x * blockDim.x) {
+    const long long x = wb + lane;
+    bool match = false;
+    unsigned bin = 0xffffffffu;
+    if (x < n) {
+      const double p = prob(amps, x, tp.inv_f);
+      if (!idx_mode && flag && isnan(p)) atomicExch(flag, 1);
+      unsigned long long key = key_of(p);
+      bool take = true;
+      if (idx_mode) {
+        take = key == T;
+        if (take) key = (unsigned long long)full_index(base[x / tp.Bsz], x % tp.Bsz, tp);
+      }
+      match = take && (key & pm) == pp;
+      if (match) bin = (unsigned)((key >> shift) & dmask);
     }
-    if ((key & pm) == pp) atomicAdd(&h[(key >> shift) & dmask], 1u);
+    const unsigned same = __match_any_sync(0xffffffffu, bin);
+    if (match && lane == __ffs(same) - 1) atomicAdd(&h[bin], (unsigned)__popc(same));
   }
   __syncthreads();
   for (int b = threadIdx.x; b < kBins; b += blockDim.x)
