@@ -15,6 +15,13 @@ module uses a greedy rule with seeded random restarts:
   reduces the largest intermediate (then the total cost), up to the requested
   count or until the largest intermediate fits the cap.
 
+* recursive bisection (``partition_path``): for deep circuits greedy stems
+  grow wide; splitting the tensor graph into balanced halves with a small cut
+  (spectral bisection on the graph whose edge weights are the bonds' log2
+  dimensions, then Fiduccia-Mattheyses moves), recursively, and contracting
+  small parts greedily gives trees whose intermediates follow the cuts.
+  ``plan_tree(method="both")`` keeps the cheaper of the two searches.
+
 All sizes are log2 element counts (every edge dimension is a power of two).
 Costs are complex multiply-adds: a step costs the product of the dimensions of
 every edge of its two operands (batch x M x N x K).
@@ -211,28 +218,203 @@ SWEEP = [(1.0, 0.0), (2.0, 0.0), (1.0, 0.25), (1.5, 0.25), (2.0, 0.25), (2.0, 0.
          (3.0, 0.5), (2.0, 0.75)]
 
 
+# ------------------------------------------------------------ recursive bisection
+def _weighted_graph(leaves, lg, keep):
+    """Adjacency of the tensors: a bond shared by tensors i and j adds its log2
+    dimension to w(i, j) (a hyper-edge over m tensors adds lg / (m - 1) to each
+    pair); output edges do not join tensors."""
+    occ: Dict[int, List[int]] = {}
+    for i, s in enumerate(leaves):
+        for e in s:
+            occ.setdefault(e, []).append(i)
+    adj: List[Dict[int, float]] = [dict() for _ in leaves]
+    for e, ids in occ.items():
+        if len(ids) < 2 or e in keep:
+            continue
+        w = lg[e] / (len(ids) - 1)
+        for x in range(len(ids)):
+            for y in range(x + 1, len(ids)):
+                a, b = ids[x], ids[y]
+                adj[a][b] = adj[a].get(b, 0.0) + w
+                adj[b][a] = adj[b].get(a, 0.0) + w
+    return adj, occ
+
+
+def _bisect(V: List[int], adj, imbalance: float) -> np.ndarray:
+    """Side (False / True) of every vertex of V: connected components are dealt
+    out whole; a connected V is cut at the smallest-weight split, along its
+    Fiedler vector, whose larger side holds at most (1 + imbalance) / 2 of V."""
+    n = len(V)
+    pos = {v: i for i, v in enumerate(V)}
+    W = np.zeros((n, n))
+    for v in V:
+        i = pos[v]
+        for u, w in adj[v].items():
+            j = pos.get(u)
+            if j is not None:
+                W[i, j] = w
+    # components
+    comp = -np.ones(n, dtype=np.int64)
+    n_comp = 0
+    for s0 in range(n):
+        if comp[s0] >= 0:
+            continue
+        stack = [s0]
+        comp[s0] = n_comp
+        while stack:
+            x = stack.pop()
+            for j in np.nonzero(W[x])[0]:
+                if comp[j] < 0:
+                    comp[j] = n_comp
+                    stack.append(int(j))
+        n_comp += 1
+    side = np.zeros(n, dtype=bool)
+    if n_comp > 1:
+        sizes = np.bincount(comp, minlength=n_comp)
+        a = b = 0
+        for c in np.argsort(-sizes, kind="stable"):
+            if a <= b:
+                a += sizes[c]
+            else:
+                side[comp == c] = True
+                b += sizes[c]
+        return side
+    L = np.diag(W.sum(axis=1)) - W
+    _, vec = np.linalg.eigh(L)
+    order = np.argsort(vec[:, 1], kind="stable")
+    lo = max(1, int(math.floor(n * (1 - imbalance) / 2)))
+    hi = min(n - 1, int(math.ceil(n * (1 + imbalance) / 2)))
+    cut, best, best_k = 0.0, None, lo
+    to_b = np.zeros(n)
+    total = W.sum(axis=1)
+    for t in range(n - 1):
+        x = order[t]
+        cut += (total[x] - to_b[x]) - to_b[x]
+        to_b += W[:, x]
+        if lo <= t + 1 <= hi and (best is None or cut < best - 1e-9):
+            best, best_k = cut, t + 1
+    side[order[:best_k]] = True
+    return side
+
+
+def _refine(V: List[int], side: np.ndarray, adj, imbalance: float, passes: int = 3) -> np.ndarray:
+    """Fiduccia-Mattheyses passes: move the unlocked vertex of largest gain (cut
+    weight removed) within the balance window, keep the best prefix."""
+    n = len(V)
+    pos = {v: i for i, v in enumerate(V)}
+    nb = [[(pos[u], w) for u, w in adj[v].items() if u in pos] for v in V]
+    lo, hi = n * (1 - imbalance) / 2, n * (1 + imbalance) / 2
+    cur = sum(w for i in range(n) for j, w in nb[i] if j > i and side[i] != side[j])
+    for _ in range(passes):
+        gain = np.array([sum(w if side[i] != side[j] else -w for j, w in nb[i]) for i in range(n)])
+        locked = np.zeros(n, dtype=bool)
+        s = side.copy()
+        n_true = int(s.sum())
+        c, best_c, best_s = cur, cur, side.copy()
+        for _m in range(n):
+            cand = np.nonzero(~locked)[0]
+            ok = np.where(s[cand], n_true - 1 >= lo, n_true + 1 <= hi)
+            cand = cand[ok]
+            if cand.size == 0:
+                break
+            i = int(cand[np.argmax(gain[cand])])
+            c -= gain[i]
+            n_true += -1 if s[i] else 1
+            s[i] = not s[i]
+            locked[i] = True
+            for j, w in nb[i]:
+                gain[j] += -2.0 * w if s[i] == s[j] else 2.0 * w
+            gain[i] = -gain[i]
+            if c < best_c - 1e-9:
+                best_c, best_s = c, s.copy()
+        if best_c < cur - 1e-9:
+            cur, side = best_c, best_s
+        else:
+            break
+    return side
+
+
+def partition_path(leaves: Sequence[FrozenSet[int]], lg: Sequence[float], keep: FrozenSet[int],
+                   imbalance: float = 0.4, leaf_size: int = 12) -> List[Tuple[int, int]]:
+    """Contraction path by recursive bisection of the tensor graph; parts of at
+    most ``leaf_size`` tensors are contracted greedily (their edges leaving the
+    part are kept open)."""
+    adj, occ = _weighted_graph(leaves, lg, keep)
+
+    def inside(V):
+        Vs = sorted(V)
+        members = set(Vs)
+        sub_keep = set(keep)
+        for v in Vs:
+            for e in leaves[v]:
+                if any(u not in members for u in occ[e]):
+                    sub_keep.add(e)
+        nodes: List = list(Vs)
+        for (i, j) in greedy([leaves[v] for v in Vs], lg, frozenset(sub_keep)):
+            nodes.append((nodes[i], nodes[j]))
+        return nodes[-1]
+
+    def rec(V):
+        if len(V) <= leaf_size:
+            return inside(V)
+        side = _refine(V, _bisect(V, adj, imbalance), adj, imbalance)
+        A = [v for v, t in zip(V, side) if not t]
+        B = [v for v, t in zip(V, side) if t]
+        if not A or not B:
+            return inside(V)
+        return (rec(A), rec(B))
+
+    pairs: List[Tuple[int, int]] = []
+    nxt = [len(leaves)]
+
+    def emit(x):
+        if isinstance(x, int):
+            return x
+        a, b = emit(x[0]), emit(x[1])
+        pairs.append((a, b))
+        nxt[0] += 1
+        return nxt[0] - 1
+
+    emit(rec(list(range(len(leaves)))))
+    return pairs
+
+
+PARTITION_IMBALANCES = (0.2, 0.3, 0.4, 0.5)
+
+
 def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = None,
-              restarts: int = 4, seed: int = 0, sliced: Optional[Sequence[int]] = None) -> Tree:
-    """Search paths over the alpha/temperature sweep (``restarts`` seeds per noisy
-    setting), slice each (unless ``sliced`` is given), keep the cheapest total."""
+              restarts: int = 4, seed: int = 0, sliced: Optional[Sequence[int]] = None,
+              method: str = "greedy") -> Tree:
+    """Search paths -- the greedy alpha/temperature sweep (``restarts`` seeds per
+    noisy setting), recursive bisection at several balance windows, or both
+    (``method``) -- slice each (unless ``sliced`` is given), keep the cheapest
+    total."""
+    if method not in ("greedy", "partition", "both"):
+        raise ValueError("method must be greedy, partition or both")
     lg = log2dims(tn)
     keep = frozenset(tn.output_edges())
     leaves = [frozenset(e) for e in tn.leaf_edges]
+    candidates = []
+    if method in ("greedy", "both"):
+        for (alpha, T) in SWEEP:
+            for r in range(restarts if T > 0 else 1):
+                candidates.append(greedy(leaves, lg, keep, alpha, T, seed + 1000 * r + 7))
+    if method in ("partition", "both"):
+        for imb in PARTITION_IMBALANCES:
+            candidates.append(partition_path(leaves, lg, keep, imbalance=imb))
     best = None
-    for (alpha, T) in SWEEP:
-        for r in range(restarts if T > 0 else 1):
-            pairs = greedy(leaves, lg, keep, alpha, T, seed + 1000 * r + 7)
-            if sliced is None:
-                sl = choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced, cap_log2) \
-                    if (n_sliced or cap_log2 is not None) else []
-            else:
-                sl = list(sliced)
-            mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
-            if cap_log2 is not None and mx > cap_log2:
-                continue
-            key = (cost * 2.0 ** len(sl), mx)
-            if best is None or key < best[0]:
-                best = (key, pairs, sl, mx, cost, vcost)
+    for pairs in candidates:
+        if sliced is None:
+            sl = choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced, cap_log2) \
+                if (n_sliced or cap_log2 is not None) else []
+        else:
+            sl = list(sliced)
+        mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
+        if cap_log2 is not None and mx > cap_log2:
+            continue
+        key = (cost * 2.0 ** len(sl), mx)
+        if best is None or key < best[0]:
+            best = (key, pairs, sl, mx, cost, vcost)
     if best is None:
         raise ValueError("no path fits the memory cap")
     _, pairs, sl, mx, cost, vcost = best
