@@ -526,6 +526,58 @@ def run_uneven(args):
         p.close()
 
 
+def run_sycamore(args):
+    """The 53-qubit Sycamore-shaped circuit, 20 cycles (l = 10 open qubits, G = 16
+    blocks, k = 1 per block): a bisection-search plan under a 2^32-element cap,
+    a few seeded slices timed one by one, and the extrapolated time to 1e6
+    samples at the fidelity whose top-1 XEB is 0.002 (Eq. 4: F = 0.002 /
+    (H_1024 - 1); slices needed per block batch = F x 2^(sliced bonds))."""
+    import math
+    import torch
+    import workloads as W
+    from paper_2406_18889_gb300 import binding as B
+    from paper_2406_18889_gb300 import engine as E
+    from paper_2406_18889_gb300 import network as N
+    from paper_2406_18889_gb300 import pathfind as P
+    torch.cuda.set_device(0)
+    w = W.workload("sycamore53_d20", cycles=20, l=10, G=16)
+    tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    t0 = time.perf_counter()
+    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition")
+    plan_s = time.perf_counter() - t0
+    plan = E.Plan(tn, tree, prec=args.prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=1)
+    s = len(tree.sliced_edges)
+    ids = W.draw_slice_subset(1 << min(s, 62), 1 + args.steps, seed=20)
+    amps = plan.contract(ids[:1])  # warm-up: graph capture
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(1, 1 + args.steps):
+        plan.contract(ids[i:i + 1], out=amps, accumulate=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_slice = e0.elapsed_time(e1) / args.steps / 1e3
+    useful = plan.info["useful_flops_per_slice"]
+    F = 0.002 / (sum(1.0 / j for j in range(1, 1025)) - 1.0)
+    slices_per_batch = F * 2.0 ** s
+    batches = 1e6 / w.G
+    print(json.dumps({
+        "metric": "53-qubit 20-cycle sliced contraction: seconds per slice on 1 GB300", "value": t_slice,
+        "unit": "s/slice", "higher_is_better": False, "steps": args.steps, "dtype": args.prec,
+        "data": "synthetic", "config": {"workload": "53-qubit Sycamore-shaped diagonal grid, 20 cycles, l = 10, "
+                                                  "G = 16, k = 1 per block", "cap_log2": 32, "sliced_bonds": s,
+                                        "path": "recursive bisection"},
+        "useful_tflops": useful / t_slice / 1e12, "useful_flops_per_slice": useful,
+        "path_cost_complex_macs": tree.cost_per_slice * 2.0 ** s, "host_planning_s": plan_s,
+        "extrapolation_1e6_samples": {"fidelity_F": F, "slices_per_block_batch": slices_per_batch,
+                                      "block_batches": batches,
+                                      "seconds": slices_per_batch * batches * t_slice,
+                                      "note": "bounded by the path: its cost is ~1e10 x the paper's 1.85e21"}}),
+          flush=True)
+    plan.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,7 +593,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="run warm-up and timed steps only (for ncu launch lists)")
-    ap.add_argument("--workload", default="grid4x6_d14", choices=["grid4x6_d14", "uneven64"],
+    ap.add_argument("--workload", default="grid4x6_d14", choices=["grid4x6_d14", "uneven64", "sycamore53_d20"],
                     help="uneven64: the 64-circuit batch (4x4..4x7 grids, depth 10..16, 2^2..2^8 "
                          "slices, l = 8, G = 16) in one batched call, timed as total slices / call time")
     args = ap.parse_args(argv)
@@ -549,6 +601,8 @@ def main(argv=None):
         args.warmup = 3
     if args.workload == "uneven64":
         run_uneven(args)
+    elif args.workload == "sycamore53_d20":
+        run_sycamore(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -55,3 +55,32 @@ def test_sycamore_shaped_slices(case, prec):
         assert np.abs(ref[i]).max() < 1e-10  # deep below the fp16 range
         assert pp.relative_l2(got, ref[i]) <= tol, (prec, sid)
     plan.close()
+
+
+@pytest.mark.skipif(__import__("os").environ.get("TN_PAPER_SCALE") != "1",
+                    reason="20-cycle circuit: set TN_PAPER_SCALE=1")
+def test_sycamore_20_cycles_fp16_agrees_with_complex64():
+    # 53 qubits, 20 cycles: beyond the oracle's reach (a sub-network costs ~1e13
+    # complex MACs); parity is partial: the fp16 path against the complex64
+    # path on the same two full sub-networks, held to the reduced-precision bar
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_18889_gb300 import engine as E
+    from paper_2406_18889_gb300 import network as N
+    from paper_2406_18889_gb300 import pathfind as P
+    from paper_2406_18889_gb300 import binding as B
+    w = W.workload("sycamore53_d20", cycles=20, l=10, G=16)
+    tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition")
+    assert tree.log2_max_intermediate <= 32 and len(tree.sliced_edges) <= 62
+    ids = W.draw_slice_subset(1 << len(tree.sliced_edges), 2, seed=21)
+    out = {}
+    for prec in ("fp16", "c64"):
+        plan = E.Plan(tn, tree, prec=prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=1)
+        out[prec] = plan.contract(ids).cpu().numpy()
+        plan.close()
+    assert np.abs(out["c64"]).max() > 0
+    assert pp.relative_l2(out["fp16"], out["c64"]) <= 3e-3
