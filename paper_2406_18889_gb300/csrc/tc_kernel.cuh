@@ -34,6 +34,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "tn_internal.h"
@@ -599,10 +600,14 @@ void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap
                 const TcGemmParams& p, cudaStream_t s) {
   const size_t sm = smem_bytes<BN, STAGE>();
   auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2, F32OUT, SPLIT>;
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory opt-in is a per-device property of the function
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  TN_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(attr_set.load() & bit)) {
     TN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
+    attr_set.fetch_or(bit);
   }
   const int64_t n_m = (p.M + BM - 1) / BM, n_n = (2 * p.N + BN - 1) / BN;
   if (!C2) {
