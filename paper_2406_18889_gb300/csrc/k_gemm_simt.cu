@@ -81,10 +81,11 @@ template <int TM, int TN, int TK, int TY, int TX, class In, class Out>
 __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, bool hilo, int flags) {
   static_assert(TY * TX == 256, "256 threads");
   constexpr int RM = TM / TY, RN = TN / TX;
+  constexpr int LA = (TM * TK + 255) / 256, LB = (TN * TK + 255) / 256;  // loads per thread per k slice
   using TI = typename In::T;
   using TO = typename Out::T;
-  __shared__ float2 As[TK][TM + 1];
-  __shared__ float2 Bs[TK][TN + 1];
+  __shared__ float2 As[2][TK][TM + 1];
+  __shared__ float2 Bs[2][TK][TN + 1];
   __shared__ int64_t a_row[TM], b_col[TN], c_row[TM], c_col[TN];
   __shared__ int64_t a_kof[TK], b_kof[TK];
   const TI* __restrict__ A = (const TI*)p.A;
@@ -104,6 +105,26 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
     b_col[i] = n0 + i < p.N ? run_offset(p.b_n, n0 + i) : 0;
     c_col[i] = n0 + i < p.N ? run_offset(p.c_n, n0 + i) : 0;
   }
+  // k slices start at multiples of TK (a power of two), so a slice's contracted
+  // offsets are its start's offset plus this CTA-constant table (run offsets
+  // are linear over disjoint index bits)
+  if (tid < TK) a_kof[tid] = run_offset(p.a_k, tid);
+  if (tid >= 32 && tid < 32 + TK) b_kof[tid - 32] = run_offset(p.b_k, tid - 32);
+  __syncthreads();
+  // this thread's (row, k) and (k, col) slots of a slice, in the coalesced order
+  int a_mm[LA], a_kk[LA], b_nn[LB], b_kk[LB];
+#pragma unroll
+  for (int q = 0; q < LA; ++q) {
+    const int l = tid + q * 256;
+    a_mm[q] = a_kc ? l / TK : l % TM;
+    a_kk[q] = a_kc ? l % TK : l / TM;
+  }
+#pragma unroll
+  for (int q = 0; q < LB; ++q) {
+    const int l = tid + q * 256;
+    b_nn[q] = b_nc ? l % TN : l / TK;
+    b_kk[q] = b_nc ? l / TN : l % TK;
+  }
   for (int64_t bt = blockIdx.z; bt < p.nbt; bt += gridDim.z) {
     const TI* Ab = A + run_offset(p.a_bt, bt);
     const TI* Bb = Bm + run_offset(p.b_bt, bt);
@@ -112,52 +133,53 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
     for (int i = 0; i < RM; ++i)
 #pragma unroll
       for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    float2 ra[LA], rb[LB];
+    // operands of the slice starting at k0 into registers
+    auto fetch = [&](int64_t k0) {
+      const int64_t ab = run_offset(p.a_k, k0), bb = run_offset(p.b_k, k0);
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        ra[q] = make_float2(0.f, 0.f);
+        if (tid + q * 256 < TM * TK && m0 + a_mm[q] < p.M && k0 + a_kk[q] < p.K)
+          ra[q] = In::ld(Ab[a_row[a_mm[q]] + ab + a_kof[a_kk[q]]]);
+      }
+#pragma unroll
+      for (int q = 0; q < LB; ++q) {
+        rb[q] = make_float2(0.f, 0.f);
+        if (tid + q * 256 < TN * TK && n0 + b_nn[q] < p.N && k0 + b_kk[q] < p.K)
+          rb[q] = In::ld(Bb[bb + b_kof[b_kk[q]] + b_col[b_nn[q]]]);
+      }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q)
+        if (tid + q * 256 < TM * TK) As[buf][a_kk[q]][a_mm[q]] = ra[q];
+#pragma unroll
+      for (int q = 0; q < LB; ++q)
+        if (tid + q * 256 < TN * TK) Bs[buf][b_kk[q]][b_nn[q]] = rb[q];
+    };
+    __syncthreads();  // the previous batch entry's last slice is consumed
+    fetch(0);
+    stash(0);
+    int buf = 0;
     for (int64_t k0 = 0; k0 < p.K; k0 += TK) {
-      __syncthreads();  // previous slice consumed; offset tables written
-      if (tid < TK) a_kof[tid] = k0 + tid < p.K ? run_offset(p.a_k, k0 + tid) : 0;
-      if (tid >= 32 && tid < 32 + TK) b_kof[tid - 32] = k0 + tid - 32 < p.K ? run_offset(p.b_k, k0 + tid - 32) : 0;
-      __syncthreads();
-#pragma unroll
-      for (int l = tid; l < TM * TK; l += 256) {
-        int mm, kk;
-        if (a_kc) {
-          mm = l / TK;
-          kk = l % TK;
-        } else {
-          kk = l / TM;
-          mm = l % TM;
-        }
-        float2 v = make_float2(0.f, 0.f);
-        if (m0 + mm < p.M && k0 + kk < p.K) v = In::ld(Ab[a_row[mm] + a_kof[kk]]);
-        As[kk][mm] = v;
-      }
-#pragma unroll
-      for (int l = tid; l < TN * TK; l += 256) {
-        int nn, kk;
-        if (b_nc) {
-          kk = l / TN;
-          nn = l % TN;
-        } else {
-          nn = l / TK;
-          kk = l % TK;
-        }
-        float2 v = make_float2(0.f, 0.f);
-        if (n0 + nn < p.N && k0 + kk < p.K) v = In::ld(Bb[b_kof[kk] + b_col[nn]]);
-        Bs[kk][nn] = v;
-      }
-      __syncthreads();
+      __syncthreads();  // slice k0 is in As/Bs[buf]; the other buffer is free
+      const bool more = k0 + TK < p.K;
+      if (more) fetch(k0 + TK);  // global loads in flight during the multiply-adds
 #pragma unroll
       for (int kk = 0; kk < TK; ++kk) {
         float2 a[RM], b[RN];
 #pragma unroll
-        for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + i * TY];
+        for (int i = 0; i < RM; ++i) a[i] = As[buf][kk][ty + i * TY];
 #pragma unroll
-        for (int j = 0; j < RN; ++j) b[j] = Bs[kk][tx + j * TX];
+        for (int j = 0; j < RN; ++j) b[j] = Bs[buf][kk][tx + j * TX];
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
           for (int j = 0; j < RN; ++j) cmac(acc[i][j], a[i], b[j]);
       }
+      if (more) stash(buf ^ 1);
+      buf ^= 1;
     }
     const int64_t cb = run_offset(p.c_bt, bt);
 #pragma unroll
