@@ -84,12 +84,15 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
            "two-CTA tensor-core form: 16-bit output needs tile width 256");
   TN_CHECK(p.acc_split >= 0 && !(p.cluster2 && p.acc_split), TN_ERR_UNSUPPORTED,
            "chunked accumulation runs on single CTAs");
+  TN_CHECK(p.m_halves == 0 || p.m_halves == 1 ||
+               (p.m_halves == 2 && bn == 256 && !p.cluster2 && !p.acc_split),
+           TN_ERR_UNSUPPORTED, "256-row tiles: tile width 256, single CTAs, one accumulator per tile");
   {
     // stage the epilogue when n is the output's more contiguous index
     const int64_t big = int64_t(1) << 62;
     const int64_t sn = p.c_n.n > 0 ? p.c_n.st[0] : big, sm = p.c_m.n > 0 ? p.c_m.st[0] : big;
     // only for write-heavy tiles (up to four k tiles); deeper tiles hide the per-row stores
-    p.stage_n = (sn < sm && 2 * p.K <= 4 * BK) ? 1 : 0;
+    p.stage_n = (sn < sm && 2 * p.K <= 4 * BK && p.m_halves != 2) ? 1 : 0;
   }
   {
     // offsets inside a tile are at most those of its all-ones row and column indices
@@ -349,6 +352,14 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
     p.acc_split = 2;
     launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
     diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
+    // and 256-row tiles (two m halves sharing each B tile; tile width 256)
+    if (p.bn == 256) {
+      TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
+      p.acc_split = 0;
+      p.m_halves = 2;
+      launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
+      diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
+    }
     unsigned h[2] = {0, 0};
     TN_CUDA(cudaMemcpyAsync(h, mx, 8, cudaMemcpyDeviceToHost, s));
     TN_CUDA(cudaStreamSynchronize(s));

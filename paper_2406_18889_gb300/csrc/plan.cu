@@ -540,6 +540,9 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     // single CTAs then
     tp.acc_split = (P.flags & TN_FLAG_FINE_ACC) ? 1 : S.hilo ? 4 : 0;
     tp.cluster2 = !tp.acc_split && (P.flags & TN_FLAG_TC_PAIR) && tp.bn == 256 ? 1 : 0;
+    // K-heavy steps: 256-row tiles load each B tile once for two 128-row MMAs
+    // (the expanded B dominates the bytes a tile brings into shared memory)
+    tp.m_halves = (!tp.acc_split && !tp.cluster2 && tp.bn == 256 && r.M >= 256 && r.K >= 256) ? 2 : 1;
     const char* a_hi = X.base(r.a_node);
     R.begin(5, flops, bytes);
     launch_gemm_tc(a_hi, S.hilo ? a_hi + NA.elems * 4 : nullptr, r.a_bt, r.a_m, bx, bx_lo, tp,

@@ -144,15 +144,15 @@ constexpr size_t kStageBytes = kEpiWarps * 32 * kStagePitch * 8 + kEpiWarps * 32
 
 // ring depth: as many stages as fit in 227 KB of shared memory next to the
 // barriers, the column-offset table and (STAGE) the epilogue staging, at most 8
-template <int BN, bool STAGE = false>
+template <int BN, bool STAGE = false, int MH = 1>
 __host__ __device__ constexpr int stages_for() {
   constexpr long budget = 232448 - 1024 - 256 - (long)BN / 2 * 12 - (STAGE ? (long)kStageBytes : 0L) - 512;
-  constexpr long per = (long)(BM + BN) * BK * 2;
+  constexpr long per = (long)(MH * BM + BN) * BK * 2;
   return budget / per > 8 ? 8 : (int)(budget / per);
 }
-template <int BN, bool STAGE>
+template <int BN, bool STAGE, int MH = 1>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)stages_for<BN, STAGE>() * (BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 12 +
+  return 1024 + (size_t)stages_for<BN, STAGE, MH>() * (MH * BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 12 +
          (STAGE ? kStageBytes : 0);
 }
 
@@ -209,6 +209,21 @@ __device__ __forceinline__ void store_el(char* Cb, char* C2b, int64_t o, float r
   }
 }
 
+// 32 consecutive accumulator columns of this warp's TMEM lane quarter
+__device__ __forceinline__ void tmem_ld32_h(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 16 consecutive accumulator columns of this warp's TMEM lane quarter
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
@@ -235,16 +250,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // so every SM reads a third less from L2 per k step.  A stage is refilled only
 // after both CTAs' MMAs released it (their commits arrive on both CTAs'
 // `empty` barriers).
-template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT>
+// MH: m halves per tile.  MH = 2 gives a CTA 256 rows (two 128-row MMAs per k
+// step sharing one B tile, so B is loaded once per 256 rows) and one TMEM
+// accumulator of 2 x BN columns instead of two alternating ones.
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT, int MH = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
                    TcGemmParams p) {
-  constexpr int S = stages_for<BN, STAGE>();
+  static_assert(MH == 1 || (MH == 2 && !STAGE && !C2 && !SPLIT), "two m halves: direct stores, single CTAs");
+  constexpr int S = stages_for<BN, STAGE, MH>();
+  constexpr int TBM = MH * BM;             // rows per tile
+  constexpr int NBUF = MH == 1 ? 2 : 1;    // TMEM accumulator buffers (TMEM holds 2 x BN columns)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sB = sA + S * BM * BK * 2;
+  uint8_t* sB = sA + S * TBM * BK * 2;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * BN * BK * 2);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;   // [2] MMA -> epilogue
@@ -258,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
   const int k_tiles = HILO ? 3 * k_tiles1 : k_tiles1;
-  const int64_t n_n = (2 * p.N + BN - 1) / BN, n_m = (p.M + BM - 1) / BM;
+  const int64_t n_n = (2 * p.N + BN - 1) / BN, n_m = (p.M + TBM - 1) / TBM;
   // work units: single tiles, or (C2) pairs of m tiles sharing an n tile
   const int64_t n_mu = C2 ? (n_m + 1) / 2 : n_m;
   const int64_t tiles = p.nbt * n_mu * n_n;
@@ -306,8 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const int pass = HILO ? kt / k_tiles1 : 0;
           const int kx = (kt - pass * k_tiles1) * BK;
-          mbar_expect_tx(&full[s], (uint32_t)((BM + BN) * BK * 2));
-          tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + s * BM * BK * 2, kx, m_tile * BM, bt);
+          mbar_expect_tx(&full[s], (uint32_t)((TBM + BN) * BK * 2));
+#pragma unroll
+          for (int h = 0; h < MH; ++h)
+            tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + (s * TBM + h * BM) * BK * 2, kx,
+                        m_tile * TBM + h * BM, bt);
           if (C2)
             tma_load_3d_mc(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2 + rank * (BN / 2) * BK * 2, kx,
                            n_tile * BN + rank * (BN / 2), bt, (uint16_t)0x3);
@@ -338,9 +362,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t t = unit0; t < tiles && !stop; t += ustride)
       for (int c0 = 0; c0 < k_tiles && !stop; c0 += kch, ++gu) {
         const int c1 = c0 + kch < k_tiles ? c0 + kch : k_tiles;
-        const int b = (int)(gu & 1);
-        const uint32_t u = (uint32_t)(gu >> 1);
-        if (gu >= 2 && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) {
+        const int b = NBUF == 2 ? (int)(gu & 1) : 0;
+        const uint32_t u = NBUF == 2 ? (uint32_t)(gu >> 1) : (uint32_t)gu;
+        if (gu >= NBUF && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) {
           stop = true;
           break;
         }
@@ -353,19 +377,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
+          const uint32_t a0 = smem_u32(sA + s * TBM * BK * 2);
           const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t ad = sw128_desc(a0 + kk * 32);
             const uint64_t bd = sw128_desc(b0 + kk * 32);
             const uint32_t acc = (kt > c0 || kk > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
+#pragma unroll
+            for (int h = 0; h < MH; ++h) {
+              const uint64_t ad = sw128_desc(a0 + h * BM * BK * 2 + kk * 32);
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr + h * BN),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                  : "memory");
+            }
           }
           if (C2)
             asm volatile(
@@ -386,8 +413,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       // before TMEM is freed: wait (bounded) for the last committed unit's MMAs
       if (gu > 0) {
         const int64_t last = gu - 1;
+        const int lb = NBUF == 2 ? (int)(last & 1) : 0;
+        const uint32_t lu = NBUF == 2 ? (uint32_t)(last >> 1) : (uint32_t)last;
         const uint64_t t0 = gtimer();
-        while (!mbar_try_wait(&tfull[last & 1], (uint32_t)((last >> 1) & 1)) && gtimer() - t0 < kWaitNs) {
+        while (!mbar_try_wait(&tfull[lb], lu & 1) && gtimer() - t0 < kWaitNs) {
         }
       }
     }
@@ -422,14 +451,55 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
       const int b = (int)(local & 1);
       const uint32_t u = (uint32_t)(local >> 1);
-      const int64_t nbase = (int64_t)n_tile * BN / 2, mbase = (int64_t)m_tile * BM;
+      const int64_t nbase = (int64_t)n_tile * BN / 2, mbase = (int64_t)m_tile * TBM;
       const int64_t tbase = run_offset(p.c_bt, bt) + run_offset(p.c_m, mbase) + run_offset(p.c_n, nbase);
       const int64_t row = tbase + m_rel;
       char* const Ct = Cb + tbase * ES;
       char* const C2t = HILO ? C2b + tbase * 4 : nullptr;
       const bool row_ok = mbase + quarter * 32 + lane < p.M;
       // the tile lies wholly inside M x N (a cluster's second tile may lie past M)
-      const bool whole = mbase + BM <= p.M && nbase + BN / 2 <= p.N;
+      const bool whole = mbase + TBM <= p.M && nbase + BN / 2 <= p.N;
+      if constexpr (MH == 2) {
+        // one accumulator (unit = tile); rows h * 128 + quarter * 32 + lane of the tile
+        const uint32_t uu = (uint32_t)local;
+        const bool ok = __all_sync(0xffffffffu, wait_bounded(&tfull[0], uu & 1, p.err));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t mr = run_offset(p.c_m, h * BM + quarter * 32 + lane);
+          const int64_t rowh = tbase + mr;
+          const uint32_t m32h = (uint32_t)mr;
+          const bool rowh_ok = mbase + h * BM + quarter * 32 + lane < p.M;
+#pragma unroll 1
+          for (int c = cgrp; c < kChunks && ok; c += kGroups) {
+            uint32_t v[32];
+            tmem_ld32_h(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * BN + c * 32), v);
+            const int j0 = c * 16;
+            if (whole && p.off32) {
+#pragma unroll
+              for (int j = 0; j < 16; j += 4) {
+                const uint4 nn = *reinterpret_cast<const uint4*>(n32 + j0 + j);
+                const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  store_el32<BF16, HILO, F32OUT>(Ct, C2t, m32h + o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
+                                                 __uint_as_float(v[2 * (j + q) + 1]) * p.scale);
+              }
+            } else if (rowh_ok) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                if (nbase + j0 + j >= p.N) break;
+                store_el<BF16, HILO, F32OUT>(Cb, C2b, rowh + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
+                                             __uint_as_float(v[2 * j + 1]) * p.scale);
+              }
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[0]);
+        continue;
+      }
       if constexpr (SPLIT) {
         // sum the tile's K chunks in FP32 registers, then store once
         constexpr int kMaxCh = (kChunks + kGroups - 1) / kGroups;
@@ -595,11 +665,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT = false>
+template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT = false, int MH = 1>
 void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
-  const size_t sm = smem_bytes<BN, STAGE>();
-  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2, F32OUT, SPLIT>;
+  const size_t sm = smem_bytes<BN, STAGE, MH>();
+  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2, F32OUT, SPLIT, MH>;
   // the shared-memory opt-in is a per-device property of the function
   static std::atomic<uint64_t> attr_set{0};
   int dev = 0;
@@ -609,7 +679,7 @@ void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap
     TN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set.fetch_or(bit);
   }
-  const int64_t n_m = (p.M + BM - 1) / BM, n_n = (2 * p.N + BN - 1) / BN;
+  const int64_t n_m = (p.M + MH * BM - 1) / (MH * BM), n_n = (2 * p.N + BN - 1) / BN;
   if (!C2) {
     const unsigned grid = (unsigned)std::min<int64_t>(n_m * n_n * p.nbt, 152);
     kern<<<grid, kThreads, sm, s>>>(ma, ma2, mb, mb2, p);
@@ -652,6 +722,16 @@ void launch_tc4(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap
 template <int BN, bool BF16, bool HILO>
 void launch_tc3(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
+  // 256-row tiles (two m halves sharing each B tile): single CTAs, direct stores
+  if constexpr (BN == 256) {
+    if (p.m_halves == 2) {
+      if (p.out_kind == 2)
+        launch_tc6<BN, BF16, HILO, false, false, true, false, 2>(ma, ma2, mb, mb2, p, s);
+      else
+        launch_tc6<BN, BF16, HILO, false, false, false, false, 2>(ma, ma2, mb, mb2, p, s);
+      return;
+    }
+  }
   // K accumulated in chunks: single CTAs, direct stores along m (no staging)
   if (p.acc_split) {
     if (p.out_kind == 2)
