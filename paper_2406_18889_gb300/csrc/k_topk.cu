@@ -14,7 +14,9 @@
 //  3. the chosen candidates are gathered (order of arrival) and bitonic-sorted
 //     into (p desc, index asc): shared-memory stages for strides below 2048,
 //     one launch per stride above.
-// All decisions stay on the device (no host round trip between passes).
+// After the first digit the candidates in its chosen bucket (usually few) are
+// compacted once and the remaining passes run over them; all other decisions
+// stay on the device (one host read of the bucket's size).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +29,7 @@ namespace {
 constexpr int kDigitBits = 12;
 constexpr int kBins = 1 << kDigitBits;
 constexpr int kLocal = 2048;  // elements sorted per CTA in shared memory
+constexpr unsigned long long kMaxCompact = 1ull << 26;  // candidates kept in the top digit's bucket
 
 struct SelState {
   unsigned long long prefix, mask;  // decided key bits
@@ -35,6 +38,14 @@ struct SelState {
   unsigned long long tie;           // 1: more candidates equal T than needed
   unsigned long long idx_prefix, idx_mask, idx_need;
   unsigned long long n_out;         // gathered so far
+  unsigned long long n_bucket;      // candidates in the digit chosen by the last pick
+  unsigned long long n_comp;        // compacted candidates
+};
+
+// a candidate of the threshold bucket: p's key and its position
+struct Comp {
+  unsigned long long key;
+  long long x;
 };
 
 struct Cand {
@@ -132,6 +143,7 @@ __global__ void __launch_bounds__(1024) pick_kernel(SelState* st, unsigned long 
       cum += cnt;
     }
     const unsigned long long dm = ((1ull << width) - 1) << shift;
+    st->n_bucket = cnt;
     if (idx_mode) {
       st->idx_prefix |= (unsigned long long)digit << shift;
       st->idx_mask |= dm;
@@ -168,6 +180,77 @@ __global__ void __launch_bounds__(256) gather_kernel(const double2* __restrict__
     if (key == T && tie && (unsigned long long)idx > I) continue;
     const unsigned long long slot = atomicAdd(&st->n_out, 1ull);
     if (slot < cap) out[slot] = Cand{p, idx};
+  }
+}
+
+// after the first digit: candidates above the chosen top digit go straight to
+// the output; those in it are compacted (key, position) for the later passes
+__global__ void __launch_bounds__(256) compact_kernel(const double2* __restrict__ amps, TopkParams tp,
+                                                      const int64_t* __restrict__ base, SelState* st,
+                                                      Cand* __restrict__ out, unsigned long long cap_out,
+                                                      Comp* __restrict__ comp, unsigned long long cap_comp,
+                                                      int shift) {
+  const long long n = tp.G * tp.Bsz;
+  const unsigned long long top = st->prefix >> shift;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const double p = prob(amps, x, tp.inv_f);
+    const unsigned long long key = key_of(p);
+    const unsigned long long d = key >> shift;
+    if (d > top) {
+      const unsigned long long slot = atomicAdd(&st->n_out, 1ull);
+      if (slot < cap_out) out[slot] = Cand{p, full_index(base[x / tp.Bsz], x % tp.Bsz, tp)};
+    } else if (d == top) {
+      const unsigned long long slot = atomicAdd(&st->n_comp, 1ull);
+      if (slot < cap_comp) comp[slot] = Comp{key, x};
+    }
+  }
+}
+
+// hist_kernel over the compacted candidates
+__global__ void __launch_bounds__(256) hist_comp_kernel(const Comp* __restrict__ comp, unsigned long long m,
+                                                        TopkParams tp, const int64_t* __restrict__ base,
+                                                        const SelState* st, unsigned long long* hist, int shift,
+                                                        int width, int idx_mode) {
+  __shared__ unsigned int h[kBins];
+  if (idx_mode && !st->tie) return;
+  for (int b = threadIdx.x; b < kBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const unsigned long long pm = idx_mode ? st->idx_mask : st->mask;
+  const unsigned long long pp = idx_mode ? st->idx_prefix : st->prefix;
+  const unsigned long long T = st->prefix;
+  const unsigned long long dmask = (1ull << width) - 1;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < m;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned long long key = comp[i].key;
+    if (idx_mode) {
+      if (key != T) continue;
+      const long long x = comp[i].x;
+      key = (unsigned long long)full_index(base[x / tp.Bsz], x % tp.Bsz, tp);
+    }
+    if ((key & pm) == pp) atomicAdd(&h[(key >> shift) & dmask], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kBins; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
+}
+
+// gather_kernel over the compacted candidates (those above the bucket are out already)
+__global__ void __launch_bounds__(256) gather_comp_kernel(const Comp* __restrict__ comp, unsigned long long m,
+                                                          const double2* __restrict__ amps, TopkParams tp,
+                                                          const int64_t* __restrict__ base, SelState* st,
+                                                          Cand* __restrict__ out, unsigned long long cap) {
+  const unsigned long long T = st->prefix;
+  const bool tie = st->tie != 0;
+  const unsigned long long I = st->idx_prefix;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < m;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = comp[i].key;
+    if (key < T) continue;
+    const long long x = comp[i].x;
+    const long long idx = full_index(base[x / tp.Bsz], x % tp.Bsz, tp);
+    if (key == T && tie && (unsigned long long)idx > I) continue;
+    const unsigned long long slot = atomicAdd(&st->n_out, 1ull);
+    if (slot < cap) out[slot] = Cand{prob(amps, x, tp.inv_f), idx};
   }
 }
 
@@ -250,6 +333,7 @@ void topk_global(const double2* amps, const TopkParams& tp, const int64_t* block
   SelState* st = reinterpret_cast<SelState*>(scratch);
   unsigned long long* hist = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(scratch) + 256);
   Cand* buf = reinterpret_cast<Cand*>(reinterpret_cast<char*>(hist) + hist_bytes);
+  Comp* comp = nullptr;
   try {
     TN_CUDA(cudaMemsetAsync(hist, 0, hist_bytes, s));
     init_state<<<1, 1, 0, s>>>(st, k);
@@ -257,13 +341,33 @@ void topk_global(const double2* amps, const TopkParams& tp, const int64_t* block
     const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 152 * 8);
     // digits of the 64-bit key from the top: 12, 12, 12, 12, 12, 4 bits
     const int shifts[6] = {52, 40, 28, 16, 4, 0}, widths[6] = {12, 12, 12, 12, 12, 4};
-    for (int mode = 0; mode < 2; ++mode)
-      for (int d = 0; d < 6; ++d) {
-        hist_kernel<<<grid, 256, 0, s>>>(amps, tp, block_base, st, hist, shifts[d], widths[d], mode,
-                                         mode == 0 ? d_flag : nullptr);
-        pick_kernel<<<1, 1024, 0, s>>>(st, hist, shifts[d], widths[d], mode, d == 5 ? 1 : 0);
-      }
-    gather_kernel<<<grid, 256, 0, s>>>(amps, tp, block_base, st, buf, P);
+    hist_kernel<<<grid, 256, 0, s>>>(amps, tp, block_base, st, hist, shifts[0], widths[0], 0, d_flag);
+    pick_kernel<<<1, 1024, 0, s>>>(st, hist, shifts[0], widths[0], 0, 0);
+    // the top digit's bucket usually holds few candidates: compact it once and
+    // run the remaining passes over the compacted set (else over everything)
+    unsigned long long n_bucket = 0;
+    TN_CUDA(cudaMemcpyAsync(&n_bucket, &st->n_bucket, sizeof(n_bucket), cudaMemcpyDeviceToHost, s));
+    TN_CUDA(cudaStreamSynchronize(s));
+    if (n_bucket <= kMaxCompact) {
+      TN_CUDA(cudaMalloc(&comp, sizeof(Comp) * std::max<unsigned long long>(n_bucket, 1)));
+      compact_kernel<<<grid, 256, 0, s>>>(amps, tp, block_base, st, buf, P, comp, n_bucket, shifts[0]);
+      const unsigned cgrid = (unsigned)std::min<unsigned long long>((n_bucket + 255) / 256 + 1, 152 * 8);
+      for (int mode = 0; mode < 2; ++mode)
+        for (int d = mode == 0 ? 1 : 0; d < 6; ++d) {
+          hist_comp_kernel<<<cgrid, 256, 0, s>>>(comp, n_bucket, tp, block_base, st, hist, shifts[d], widths[d],
+                                                 mode);
+          pick_kernel<<<1, 1024, 0, s>>>(st, hist, shifts[d], widths[d], mode, d == 5 ? 1 : 0);
+        }
+      gather_comp_kernel<<<cgrid, 256, 0, s>>>(comp, n_bucket, amps, tp, block_base, st, buf, P);
+    } else {
+      for (int mode = 0; mode < 2; ++mode)
+        for (int d = mode == 0 ? 1 : 0; d < 6; ++d) {
+          hist_kernel<<<grid, 256, 0, s>>>(amps, tp, block_base, st, hist, shifts[d], widths[d], mode,
+                                           mode == 0 ? d_flag : nullptr);
+          pick_kernel<<<1, 1024, 0, s>>>(st, hist, shifts[d], widths[d], mode, d == 5 ? 1 : 0);
+        }
+      gather_kernel<<<grid, 256, 0, s>>>(amps, tp, block_base, st, buf, P);
+    }
     pad_kernel<<<(unsigned)std::min<unsigned long long>((P + 255) / 256, 4096), 256, 0, s>>>(buf, k, P);
     const unsigned chunks = (unsigned)(P / kLocal);
     bitonic_local<<<chunks, 1024, 0, s>>>(buf, 0);
@@ -280,9 +384,11 @@ void topk_global(const double2* amps, const TopkParams& tp, const int64_t* block
   } catch (...) {
     cudaStreamSynchronize(s);
     cudaFree(scratch);
+    if (comp) cudaFree(comp);
     throw;
   }
   TN_CUDA(cudaFree(scratch));
+  if (comp) TN_CUDA(cudaFree(comp));
 }
 
 }  // namespace tn
