@@ -98,23 +98,31 @@ def rank_workload(rank: int):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of SM clock and throttle reasons, every 50 ms, kept only
+    where their timestamp falls inside a window marked with `timed()`."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.proc = None
         self.gpu = gpu_index
+        self.windows = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)  # let the sampler start before the first timed window
         except OSError:
             self.proc = None
         return self
+
+    def timed(self, t0: float, t1: float):
+        """Marks [t0, t1] (time.time() seconds) as a timed region."""
+        self.windows.append((t0, t1))
 
     def __exit__(self, *a):
         self.out = ""
@@ -126,22 +134,39 @@ class ClockSampler:
                 self.proc.kill()
                 self.out, _ = self.proc.communicate()
 
+    @staticmethod
+    def _epoch(stamp: str):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(stamp, fmt).timestamp()
+            except ValueError:
+                continue
+        return None
+
     def summary(self) -> dict:
         rows = []
         for line in (self.out or "").strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+                rows.append((self._epoch(parts[0]), float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        inside = [r for r in rows if r[0] is not None and any(a <= r[0] <= b for a, b in self.windows)]
+        note = "samples inside the timed regions"
+        if not inside:  # timed regions shorter than the sampling interval: nearest samples after the start
+            t0 = min((a for a, _ in self.windows), default=None)
+            after = [r for r in rows if r[0] is not None and t0 is not None and r[0] >= t0]
+            inside = after[:2] or rows[-2:]
+            note = "no sample inside the timed regions; the first samples after their start"
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
-        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1],
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for _, _, _, r in inside for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": inside[0][2],
+                "reasons": reasons, "samples": len(inside), "note": note}
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -199,7 +224,7 @@ KIND_NAMES = {0: "gemm_cuda_core", 1: "bit_permute", 2: "gather", 3: "accumulate
 # default configuration (fp16, slice batch 64, invariant subtrees hoisted), from
 # the ncu capture summarised in profiles/tc_gemm_grid4x6_d14_fp16_dram.md
 # (dram__bytes_read.sum + dram__bytes_write.sum of that launch)
-DOMINANT_TRAFFIC = {("fp16", 64, False, True): 2102178560}
+DOMINANT_TRAFFIC = {("fp16", 64, False, True): 2099230976}
 
 
 def fp32_peak_measured(B) -> tuple:
@@ -331,26 +356,28 @@ def run_ours(args):
         dist.barrier()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()  # evict L2 (129 MB) between steps; not inside the timed events
-            evs[i][0].record(stream)
-            step()
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-        if dist:
-            dist.barrier()
+    clk = ClockSampler(local).__enter__()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall0, t_win = time.perf_counter(), time.time()
+    for i in range(args.steps):
+        flush.zero_()  # evict L2 (129 MB) between steps; not inside the timed events
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk.timed(t_win, time.time())
+    if dist:
+        dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms = max_over_ranks(ms, dist, "cuda")
     slices = sum_over_ranks(float(S * args.steps), dist, "cuda")
     value = slices / (ms / 1e3)
 
     if args.only_timed:
+        clk.__exit__()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "slices/s",
                               "ms_per_step": ms / args.steps, "only_timed": True}), flush=True)
@@ -380,8 +407,11 @@ def run_ours(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        t_win = time.time()
         e2e_step()
         e2e_ms += 1e3 * (time.perf_counter() - t0)
+        clk.timed(t_win, time.time())
+    clk.__exit__()
     e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
 
     e2e_value = slices / (e2e_ms / 1e3)
@@ -581,7 +611,7 @@ def run_sycamore(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp16", choices=["c64", "bf16", "fp16"])

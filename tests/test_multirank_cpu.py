@@ -47,3 +47,31 @@ def test_two_gloo_ranks_partition_blocks():
     assert g0 == g1          # same circuit
     assert t0 == t1 == 2.0   # max over ranks
     assert n0 == n1 == 128.0  # slices summed over ranks
+
+
+def test_clock_samples_filtered_to_timed_regions():
+    """bench.py's clock record keeps only nvidia-smi samples whose timestamps fall
+    inside the marked timed regions; reasons are collected from those alone."""
+    import datetime
+    import bench
+    c = bench.ClockSampler(0)
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(dt_ms, mhz, thermal):
+        stamp = (base + datetime.timedelta(milliseconds=dt_ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return (f"{stamp}, {mhz}, 2070, 900.0, 0x0, Not Active, Not Active, "
+                f"{'Active' if thermal else 'Not Active'}, Not Active")
+
+    c.out = "\n".join([line(0, 1000, True), line(100, 2070, False), line(150, 2055, False),
+                       line(400, 900, True)])
+    t0 = base.timestamp()
+    c.timed(t0 + 0.05, t0 + 0.2)
+    s = c.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == (2070 + 2055) / 2 and s["reasons"] == []
+    c.timed(t0 + 0.39, t0 + 0.41)
+    s = c.summary()
+    assert s["samples"] == 3 and s["reasons"] == ["sw_thermal_slowdown"]
+    # no sample inside: the first ones after the region's start, and it says so
+    c.windows = [(t0 + 0.16, t0 + 0.17)]
+    s = c.summary()
+    assert s["samples"] == 1 and s["sm_mhz"] == 900 and "no sample" in s["note"]
