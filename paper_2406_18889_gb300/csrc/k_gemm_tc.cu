@@ -94,9 +94,10 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     // only for write-heavy tiles (up to four k tiles); deeper tiles hide the per-row stores
     p.stage_n = (sn < sm && 2 * p.K <= 4 * BK && p.m_halves != 2) ? 1 : 0;
   }
+  const int64_t tbm = (p.m_halves == 2 ? 2 : 1) * (int64_t)BM;  // rows per tile
   {
     // offsets inside a tile are at most those of its all-ones row and column indices
-    const int64_t local_max = run_offset(p.c_m, BM - 1) + run_offset(p.c_n, bn / 2 - 1);
+    const int64_t local_max = run_offset(p.c_m, tbm - 1) + run_offset(p.c_n, bn / 2 - 1);
     p.off32 = local_max < (int64_t(1) << 31) ? 1 : 0;
   }
   const uint64_t pitch = (uint64_t)((2 * p.K + BK - 1) / BK * BK);
@@ -291,6 +292,20 @@ __global__ void diff_kernel(const float2* a, const float2* b, int64_t n, unsigne
   atomicMax(max_diff, __float_as_uint(md));
   atomicMax(max_ref, __float_as_uint(mr));
 }
+// the same for a result stored [bt][n][m] (m contiguous) against b = [bt][m][n]
+__global__ void diff_t_kernel(const float2* a, const float2* b, int64_t nbt, int64_t M, int64_t N,
+                              unsigned* max_diff) {
+  float md = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbt * M * N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bt = i / (M * N), r = i - bt * M * N, m = r / N, n = r - m * N;
+    const float2 x = a[bt * M * N + n * M + m];
+    const float dx = x.x - b[i].x, dy = x.y - b[i].y;
+    md = fmaxf(md, sqrtf(dx * dx + dy * dy));
+    if (!(x.x == x.x) || !(x.y == x.y)) md = 3.0e38f;
+  }
+  atomicMax(max_diff, __float_as_uint(md));
+}
 }  // namespace
 
 double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
@@ -359,6 +374,19 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
       p.m_halves = 2;
       launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
       diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
+    }
+    // and an m-contiguous result ([bt][n][m], the direct epilogue's usual
+    // layout) under each tile form
+    p.c_m = single_run(M, 1);
+    p.c_n = single_run(N, M);
+    for (int v = 0; v < 3; ++v) {
+      if (v == 2 && p.bn != 256) break;
+      TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
+      p.cluster2 = v == 1;
+      p.acc_split = 0;
+      p.m_halves = v == 2 ? 2 : 1;
+      launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
+      diff_t_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt, M, N, mx);
     }
     unsigned h[2] = {0, 0};
     TN_CUDA(cudaMemcpyAsync(h, mx, 8, cudaMemcpyDeviceToHost, s));

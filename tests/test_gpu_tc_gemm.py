@@ -1,6 +1,8 @@
 """Tensor-core (tcgen05) GEMM self-test through the C ABI: the stacked-4M real
 lowering of a complex GEMM against a plain FP32 CUDA-core GEMM of the same
-16-bit inputs (both accumulate in FP32; only the summation order differs)."""
+16-bit inputs (both accumulate in FP32; only the summation order differs).
+Every shape runs each tile form (single CTA, two-CTA cluster, chunked
+accumulation, 256-row tiles) into an n-contiguous and an m-contiguous result."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -12,6 +14,8 @@ SHAPES = [  # (batch, M, N, K) in complex elements
     (2, 256, 128, 64),     # two M tiles, BN = 256
     (1, 130, 4, 4),        # tiny N and K (tile padding), ragged M
     (5, 96, 300, 260),     # several K stages (4-stage ring wraps), ragged N tile
+    (1, 1100, 600, 64),    # nine m tiles x five n tiles
+    (2, 520, 1030, 100),   # batched, ragged M, N and K across several tiles
 ]
 
 
