@@ -95,6 +95,9 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     p.stage_n = (sn < sm && 2 * p.K <= 4 * BK && p.m_halves != 2) ? 1 : 0;
   }
   const int64_t tbm = (p.m_halves == 2 ? 2 : 1) * (int64_t)BM;  // rows per tile
+  TN_CHECK(p.nbt * ((p.M + tbm - 1) / tbm) * ((2 * p.N + bn - 1) / bn) < (int64_t(1) << 31) &&
+               p.nbt < (int64_t(1) << 31) && p.M < (int64_t(1) << 31) && p.N < (int64_t(1) << 31),
+           TN_ERR_UNSUPPORTED, "tensor-core GEMM: tile count or an extent reaches 2^31");
   {
     // offsets inside a tile are at most those of its all-ones row and column indices
     const int64_t local_max = run_offset(p.c_m, tbm - 1) + run_offset(p.c_n, bn / 2 - 1);

@@ -157,6 +157,51 @@ __host__ __device__ constexpr size_t smem_bytes() {
 }
 
 
+// Coordinates of the tiles t0, t0 + step, t0 + 2 step, ... (t = (bt * n_mu + m)
+// * n_n + n).  Walking: one division when the walk starts, then a mixed-radix
+// add per tile instead of three 64-bit divisions.  Not walking (register-lean):
+// the divisions, per tile.
+template <bool kWalk>
+struct TileWalk {
+  int n, m, b;     // current tile
+  int dn, dm, db;  // the step in the same radix
+  int n_n, n_mu;
+  __device__ __forceinline__ TileWalk(int64_t t0, int64_t step, int64_t nn, int64_t nmu)
+      : n_n((int)nn), n_mu((int)nmu) {
+    n = (int)(t0 % nn);
+    m = (int)((t0 / nn) % nmu);
+    b = (int)(t0 / (nn * nmu));
+    dn = (int)(step % nn);
+    dm = (int)((step / nn) % nmu);
+    db = (int)(step / (nn * nmu));
+  }
+  __device__ __forceinline__ void next() {
+    n += dn;
+    const int cn = n >= n_n;
+    n -= cn ? n_n : 0;
+    m += dm + cn;
+    const int cm = m >= n_mu;
+    m -= cm ? n_mu : 0;
+    b += db + cm;
+  }
+  __device__ __forceinline__ void at(int64_t, int& n_tile, int& m_unit, int& bt) const {
+    n_tile = n;
+    m_unit = m;
+    bt = b;
+  }
+};
+template <>
+struct TileWalk<false> {
+  int64_t n_n, n_mu;
+  __device__ __forceinline__ TileWalk(int64_t, int64_t, int64_t nn, int64_t nmu) : n_n(nn), n_mu(nmu) {}
+  __device__ __forceinline__ void next() {}
+  __device__ __forceinline__ void at(int64_t t, int& n_tile, int& m_unit, int& bt) const {
+    n_tile = (int)(t % n_n);
+    m_unit = (int)((t / n_n) % n_mu);
+    bt = (int)(t / (n_n * n_mu));
+  }
+};
+
 // complex value -> one 32-bit word of two 16-bit reals
 template <bool BF16>
 __device__ __forceinline__ uint32_t pack16(float re, float im) {
@@ -315,9 +360,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int64_t g = 0;  // ring position over all of this CTA's k tiles
       bool stop = false;
-      for (int64_t t = unit0; t < tiles && !stop; t += ustride) {
-        const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
-        const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
+      TileWalk<true> w(unit0, ustride, n_n, n_mu);
+      for (int64_t t = unit0; t < tiles && !stop; t += ustride, w.next()) {
+        const int n_tile = w.n, bt = w.b;
+        const int m_tile = w.m * (C2 ? 2 : 1) + rank;
         for (int kt = 0; kt < k_tiles; ++kt, ++g) {
           const int s = (int)(g % S);
           const uint32_t use = (uint32_t)(g / S);
@@ -436,6 +482,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       n32[j] = (uint32_t)n_rel[j];  // used when p.off32: a tile's offsets fit in 32 bits
     }
     const int64_t m_rel = run_offset(p.c_m, quarter * 32 + lane);
+    // rows h * 128 + quarter * 32 + lane of a 256-row tile
+    const int64_t m_rel2[2] = {m_rel, MH == 2 ? run_offset(p.c_m, BM + quarter * 32 + lane) : 0};
+    // Tile base offsets.  Tile width 256: the output offset of bit `lane` of
+    // each tile-origin index, so that a tile's base offset is the sum over its
+    // origin's set bits (offsets are linear over disjoint index bits), reduced
+    // across the warp.  Otherwise (measured faster at width 128, and SPLIT is
+    // at its register limit): the runs walked per tile.
+    constexpr bool kBaseByBits = BN == 256 && !SPLIT;
+    const int64_t w_bt = kBaseByBits && lane < 31 ? run_offset(p.c_bt, int64_t(1) << lane) : 0;
+    const int64_t w_m = kBaseByBits && lane < 31 ? run_offset(p.c_m, int64_t(1) << lane) : 0;
+    const int64_t w_n = kBaseByBits && lane < 31 ? run_offset(p.c_n, int64_t(1) << lane) : 0;
     const uint32_t m32 = (uint32_t)m_rel;
     constexpr int ES = F32OUT ? 8 : 4;  // bytes per output element
     asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
@@ -446,13 +503,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t* rb = row_base + ew * 32;
     int64_t local = 0;
     int64_t gu = 0;  // SPLIT: accumulation units consumed
-    for (int64_t t = unit0; t < tiles; t += ustride, ++local) {
-      const int n_tile = (int)(t % n_n), bt = (int)(t / (n_n * n_mu));
-      const int m_tile = (int)((t / n_n) % n_mu) * (C2 ? 2 : 1) + rank;
+    TileWalk<!SPLIT> w(unit0, ustride, n_n, n_mu);
+    for (int64_t t = unit0; t < tiles; t += ustride, ++local, w.next()) {
+      int n_tile, m_unit, bt;
+      w.at(t, n_tile, m_unit, bt);
+      const int m_tile = m_unit * (C2 ? 2 : 1) + rank;
       const int b = (int)(local & 1);
       const uint32_t u = (uint32_t)(local >> 1);
       const int64_t nbase = (int64_t)n_tile * BN / 2, mbase = (int64_t)m_tile * TBM;
-      const int64_t tbase = run_offset(p.c_bt, bt) + run_offset(p.c_m, mbase) + run_offset(p.c_n, nbase);
+      int64_t tbase;
+      if constexpr (!kBaseByBits) {
+        tbase = run_offset(p.c_bt, bt) + run_offset(p.c_m, mbase) + run_offset(p.c_n, nbase);
+      } else {
+        tbase = (((uint32_t)bt >> lane) & 1u ? w_bt : 0) + (((uint32_t)mbase >> lane) & 1u ? w_m : 0) +
+                (((uint32_t)nbase >> lane) & 1u ? w_n : 0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tbase += __shfl_xor_sync(0xffffffffu, tbase, o);
+      }
       const int64_t row = tbase + m_rel;
       char* const Ct = Cb + tbase * ES;
       char* const C2t = HILO ? C2b + tbase * 4 : nullptr;
@@ -466,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int64_t mr = run_offset(p.c_m, h * BM + quarter * 32 + lane);
+          const int64_t mr = m_rel2[h];
           const int64_t rowh = tbase + mr;
           const uint32_t m32h = (uint32_t)mr;
           const bool rowh_ok = mbase + h * BM + quarter * 32 + lane < p.M;
