@@ -388,18 +388,39 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
   const int64_t ntiles = int64_t(1) << (p.nbits - p.P);
   const int n_q = (1 << p.P) / V;
   const int na_n = KC << p.na, nb_n = KC << p.nb;
+  // A, B and destination offsets of a tile's origin, double-buffered: warp 0
+  // forms the next tile's while the block stages this one (lanes take the
+  // tile index bits, then a warp reduction)
+  __shared__ int64_t tile_base[2][3];
+  const int lane = threadIdx.x & 31;
+  auto bases = [&](int64_t t, int slot) {
+    int64_t a = 0, b = 0, o = 0;
+    for (int j = p.P + lane; j < p.nbits; j += 32)
+      if ((t >> (j - p.P)) & 1) {
+        a += p.a_w[j];
+        b += p.b_w[j];
+        o += p.o_w[j];
+      }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, s);
+      b += __shfl_xor_sync(0xffffffffu, b, s);
+      o += __shfl_xor_sync(0xffffffffu, o, s);
+    }
+    if (lane == 0) {
+      tile_base[slot][0] = a;
+      tile_base[slot][1] = b;
+      tile_base[slot][2] = o;
+    }
+  };
+  if (threadIdx.x < 32 && (int64_t)blockIdx.x < ntiles) bases(blockIdx.x, 0);
   __syncthreads();
   const uint32_t sel_t = sel_lo[threadIdx.x];
   const int64_t off_t = off_lo[threadIdx.x];
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int64_t a0 = 0, b0 = 0, o0 = 0;
-    for (int j = p.P; j < p.nbits; ++j)
-      if ((t >> (j - p.P)) & 1) {
-        a0 += p.a_w[j];
-        b0 += p.b_w[j];
-        o0 += p.o_w[j];
-      }
-    __syncthreads();  // the previous tile's staged entries consumed
+  int it = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    __syncthreads();  // the previous tile's staged entries consumed; this tile's bases visible
+    const int64_t a0 = tile_base[it & 1][0], b0 = tile_base[it & 1][1], o0 = tile_base[it & 1][2];
     for (int i = threadIdx.x; i < na_n; i += blockDim.x) {
       const int u = i >> lgK;
       int64_t o = a0 + p.ak[i & (KC - 1)];
@@ -414,8 +435,10 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
         if ((u >> b) & 1) o += p.b_wt[b];
       Bs[i] = p.B[o];
     }
+    if (threadIdx.x < 32 && t + gridDim.x < ntiles) bases(t + gridDim.x, (it + 1) & 1);
     __syncthreads();
     const int64_t ot = o0 + off_t;
+#pragma unroll 2
     for (int q = threadIdx.x; q < n_q; q += blockDim.x) {
       const int h = q >> 8;
       const uint32_t sel = sel_t | sel_hi[h];

@@ -523,6 +523,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = tbase + m_rel;
       char* const Ct = Cb + tbase * ES;
       char* const C2t = HILO ? C2b + tbase * 4 : nullptr;
+      // this lane's row of the tile (32-bit offsets: p.off32 keeps every
+      // in-tile offset below 2^31, so row + column never wraps)
+      char* const Ctm = Ct + (size_t)m32 * ES;
+      char* const C2tm = HILO ? C2t + (size_t)m32 * 4 : nullptr;
       const bool row_ok = mbase + quarter * 32 + lane < p.M;
       // the tile lies wholly inside M x N (a cluster's second tile may lie past M)
       const bool whole = mbase + TBM <= p.M && nbase + BN / 2 <= p.N;
@@ -536,6 +540,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int64_t mr = m_rel2[h];
           const int64_t rowh = tbase + mr;
           const uint32_t m32h = (uint32_t)mr;
+          char* const Cth = Ct + (size_t)m32h * ES;
+          char* const C2th = HILO ? C2t + (size_t)m32h * 4 : nullptr;
           const bool rowh_ok = mbase + h * BM + quarter * 32 + lane < p.M;
 #pragma unroll 1
           for (int c = cgrp; c < kChunks && ok; c += kGroups) {
@@ -549,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                  store_el32<BF16, HILO, F32OUT>(Ct, C2t, m32h + o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
+                  store_el32<BF16, HILO, F32OUT>(Cth, C2th, o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
                                                  __uint_as_float(v[2 * (j + q) + 1]) * p.scale);
               }
             } else if (rowh_ok) {
@@ -699,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              store_el32<BF16, HILO, F32OUT>(Ct, C2t, m32 + o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
+              store_el32<BF16, HILO, F32OUT>(Ctm, C2tm, o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
                                              __uint_as_float(v[2 * (j + q) + 1]) * p.scale);
           }
         } else if (whole) {
