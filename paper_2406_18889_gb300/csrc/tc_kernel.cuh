@@ -410,6 +410,68 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int c1 = c0 + kch < k_tiles ? c0 + kch : k_tiles;
         const int b = NBUF == 2 ? (int)(gu & 1) : 0;
         const uint32_t u = NBUF == 2 ? (uint32_t)(gu >> 1) : (uint32_t)gu;
+        if constexpr (MH == 2) {
+          // 256-row tiles: the two TMEM halves (columns h * BN, rows h * 128 of
+          // the tile) come back separately (tempty[h]).  The tile's half-0 MMAs
+          // start once half 0 is drained; its half-1 MMAs wait, over at most
+          // the S staged k tiles, until half 1 is drained too, and each stage is
+          // released after both halves have used it.
+          auto mma_half = [&](int s, int h, bool acc_in) {
+            const uint32_t a0 = smem_u32(sA + s * TBM * BK * 2) + h * BM * BK * 2;
+            const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t acc = (acc_in || kk > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(h * BN)),
+                  "l"(sw128_desc(a0 + kk * 32)), "l"(sw128_desc(b0 + kk * 32)), "r"(idesc), "r"(acc)
+                  : "memory");
+            }
+          };
+          auto release = [&](int s) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+          };
+          if (gu >= 1 && !wait_bounded(&tempty[0], (u & 1) ^ 1, p.err)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          bool h1 = gu == 0;  // half 1 free
+          const int64_t g0 = g;
+          for (int kt = c0; kt < c1; ++kt, ++g) {
+            const int s = (int)(g % S);
+            if (!wait_bounded(&full[s], (uint32_t)((g / S) & 1), p.err)) {
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            mma_half(s, 0, kt > c0);
+            if (h1) {
+              mma_half(s, 1, kt > c0);
+              release(s);
+              continue;
+            }
+            if (kt + 1 < c1 && g - g0 + 1 < S) continue;  // defer half 1 while stages remain
+            if (!wait_bounded(&tempty[1], (u & 1) ^ 1, p.err)) {
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            h1 = true;
+            for (int64_t j = g0; j <= g; ++j) {
+              mma_half((int)(j % S), 1, j > g0);
+              release((int)(j % S));
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&tfull[0]))
+                       : "memory");
+          continue;
+        }
         if (gu >= NBUF && !wait_bounded(&tempty[b], (u & 1) ^ 1, p.err)) {
           stop = true;
           break;
@@ -567,10 +629,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           }
+          // hand this half's TMEM columns back: the next tile's MMAs into them
+          // may start while the other half is still being read
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[h]);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[0]);
         continue;
       }
       if constexpr (SPLIT) {
