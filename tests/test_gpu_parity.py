@@ -62,6 +62,37 @@ def test_grid4x6_all_slices(E, sv_grid4x6, batch):
     assert err <= C64_TOL, err
 
 
+@pytest.mark.parametrize("prec,tol", [("c64", C64_TOL), ("fp16", 3e-3)])
+def test_grid4x6_whole_state_vector(E, sv_grid4x6, prec, tol):
+    """The 24-qubit, 14-cycle circuit with all 2^14 closed bitstrings as blocks:
+    the 64 slices' blocks then hold every amplitude of the state vector."""
+    import torch
+    from paper_2406_18889_gb300 import binding as B
+    w0, psi = sv_grid4x6
+    w = W.workload("grid4x6_d14", G=1 << 14)
+    assert all(a.qubits == b.qubits and np.array_equal(a.matrix, b.matrix)
+               for a, b in zip(w.circuit.ops, w0.circuit.ops))
+    prep = E.prepare(w)
+    plan = E.Plan(prep.tn, prep.tree, prec=prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=16)
+    amps = plan.contract()
+    got = amps.cpu().numpy()
+    assert got.shape == (1 << 14, 1 << 10)
+    ref, _ = _sv_blocks(w, psi)
+    err = pp.relative_l2(got, ref)
+    assert err <= tol, err
+    # the blocks partition the state vector: total probability 1 (unit norm)
+    assert abs(float(np.sum(np.abs(got) ** 2)) - 1.0) <= 2 * tol
+    if prec == "c64":
+        # global top-k over all 2^24 strings, bit-exact on the oracle's amplitudes
+        base = torch.as_tensor(w.block_base(), device="cuda")
+        gi, gp = E.topk(torch.as_tensor(ref, device="cuda"), 1000, 1.0, base, w.open_bit_pos(), global_mode=True)
+        ri, rp = pp.topk_global(ref, 1000, 1.0, w.block_base(), w.open_bit_pos())
+        assert np.array_equal(gi.cpu().numpy(), ri) and np.array_equal(gp.cpu().numpy(), rp)
+        # and they are the 1000 most probable strings of the state vector itself
+        q = pp.probabilities(psi.reshape(1, -1), 1.0).reshape(-1)
+        assert np.array_equal(np.sort(ri), np.sort(np.argsort(-q, kind="stable")[:1000]))
+
+
 @pytest.mark.parametrize("prec", ["c64", "fp16"])
 def test_hoisted_invariant_subtrees(E, sv_grid4x6, prec):
     # slice-independent subtrees contracted once at plan creation give the same sum
