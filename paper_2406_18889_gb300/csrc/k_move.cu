@@ -229,33 +229,53 @@ void launch_gather_leaves(const GatherLeaf* d_table, int n_leaves, int64_t max_r
 
 // ------------------------------------------------------------ accumulate
 // amps[g][j] = (accumulate ? amps[g][j] : 0) + sum_{b < n_valid} root[b][g][j]
-// in FP64, b ascending (the cross-slice sum of paper Sec. III slicing).
+// in FP64 (the cross-slice sum of paper Sec. III slicing), in a fixed order:
+// four threads per output each sum a contiguous quarter of the batch in batch
+// order, then the four partial sums are added in quarter order.  (GB300's
+// FP64 rate is low; four threads per output hide the latency of the add chains.)
 namespace {
-__global__ void accumulate_kernel(const float2* __restrict__ root, int64_t sb, int64_t sg, int64_t sj,
-                                  int64_t G, int64_t J, const int32_t* __restrict__ n_valid,
-                                  double2* __restrict__ amps, int accumulate, double scale) {
-  int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (x >= G * J) return;
-  int64_t g = x / J, j = x % J;
+constexpr int kAccParts = 4;
+constexpr int kAccOut = 64;  // outputs per 256-thread block
+__global__ void __launch_bounds__(kAccParts * kAccOut)
+    accumulate_kernel(const float2* __restrict__ root, int64_t sb, int64_t sg, int64_t sj, int64_t G, int64_t J,
+                      const int32_t* __restrict__ n_valid, double2* __restrict__ amps, int accumulate,
+                      double scale) {
+  __shared__ double2 part[kAccParts][kAccOut];
+  const int q = threadIdx.x / kAccOut, o = threadIdx.x % kAccOut;  // a warp: one quarter, 32 outputs
+  const int64_t x = blockIdx.x * (int64_t)kAccOut + o;
   const int nv = *n_valid;
   double re = 0.0, im = 0.0;
-  const float2* p = root + g * sg + j * sj;
-  // loads issued eight at a time (independent), summed in batch order
-  int b = 0;
-  for (; b + 8 <= nv; b += 8) {
-    float2 v[8];
+  if (x < G * J) {
+    const int64_t g = x / J, j = x % J;
+    const float2* p = root + g * sg + j * sj;
+    const int b1 = (int)((int64_t)nv * (q + 1) / kAccParts);
+    int b = (int)((int64_t)nv * q / kAccParts);
+    // loads issued eight at a time (independent), summed in batch order
+    for (; b + 8 <= b1; b += 8) {
+      float2 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = p[(b + u) * sb];
+      for (int u = 0; u < 8; ++u) v[u] = p[(b + u) * sb];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      re += (double)v[u].x;
-      im += (double)v[u].y;
+      for (int u = 0; u < 8; ++u) {
+        re += (double)v[u].x;
+        im += (double)v[u].y;
+      }
+    }
+    for (; b < b1; ++b) {
+      const float2 v = p[b * sb];
+      re += (double)v.x;
+      im += (double)v.y;
     }
   }
-  for (; b < nv; ++b) {
-    const float2 v = p[b * sb];
-    re += (double)v.x;
-    im += (double)v.y;
+  part[q][o] = make_double2(re, im);
+  __syncthreads();
+  if (q != 0 || x >= G * J) return;
+  re = part[0][o].x;
+  im = part[0][o].y;
+#pragma unroll
+  for (int r = 1; r < kAccParts; ++r) {
+    re += part[r][o].x;
+    im += part[r][o].y;
   }
   re *= scale;  // power of two: exact
   im *= scale;
@@ -277,8 +297,8 @@ void launch_accumulate_c64(const void* root, int64_t sb, int64_t sg, int64_t sj,
                            double scale) {
   (void)B;
   int64_t n = G * J;
-  accumulate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)root, sb, sg, sj, G, J,
-                                                                 d_n_valid, (double2*)amps, accumulate, scale);
+  accumulate_kernel<<<(unsigned)((n + kAccOut - 1) / kAccOut), kAccParts * kAccOut, 0, s>>>(
+      (const float2*)root, sb, sg, sj, G, J, d_n_valid, (double2*)amps, accumulate, scale);
 }
 
 // ------------------------------------------------------------ amax

@@ -22,9 +22,13 @@ struct Key {
   long long idx;
 };
 
-// a is ordered before b
+// a is ordered before b: p descending, then index ascending.  Every p is a
+// non-negative double or the -1 sentinel, and such values order exactly as
+// their bit patterns read as signed 64-bit integers, so the comparison runs
+// on the integer pipe (a NaN p has already raised the numeric flag).
 __device__ __forceinline__ bool before(const Key& a, const Key& b) {
-  return a.p > b.p || (a.p == b.p && a.idx < b.idx);
+  const long long pa = __double_as_longlong(a.p), pb = __double_as_longlong(b.p);
+  return pa > pb || (pa == pb && a.idx < b.idx);
 }
 
 __device__ __forceinline__ long long full_index(long long base, long long j, const TopkParams& tp) {
