@@ -420,3 +420,48 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     _, pairs, sl, mx, cost, vcost = best
     return Tree(pairs=pairs, sliced_edges=list(sl), log2_max_intermediate=mx,
                 cost_per_slice=cost, cost_variant_per_slice=vcost, n_leaves=len(leaves))
+
+
+# ------------------------------------------------------------ memory vs complexity
+def memory_cap_sweep(tn: TensorNetwork, caps_log2: Sequence[float], method: str = "partition",
+                     max_sliced: int = 62, restarts: int = 1, seed: int = 0) -> List[dict]:
+    """Time complexity against the memory cap (paper Sec. III: a larger cap on
+    the largest intermediate means fewer sliced bonds and less total work).
+
+    Each candidate path (recursive bisection at every balance window, the greedy
+    sweep, or both) is found once -- it does not depend on the cap -- and then
+    sliced greedily down to every cap.  Returns one entry per cap, ascending:
+    ``cap_log2``, ``n_sliced``, ``cost_per_slice`` and ``total`` (complex
+    multiply-adds over all slices) of the cheapest total found, or only
+    ``cap_log2`` when no candidate fits within ``max_sliced`` sliced bonds."""
+    if method not in ("greedy", "partition", "both"):
+        raise ValueError("method must be greedy, partition or both")
+    lg = log2dims(tn)
+    keep = frozenset(tn.output_edges())
+    leaves = [frozenset(e) for e in tn.leaf_edges]
+    candidates = []
+    if method in ("partition", "both"):
+        for imb in PARTITION_IMBALANCES:
+            candidates.append(("bisection %.1f" % imb, partition_path(leaves, lg, keep, imbalance=imb)))
+    if method in ("greedy", "both"):
+        for (alpha, T) in SWEEP:
+            for r in range(restarts if T > 0 else 1):
+                candidates.append(("greedy %.2g/%.2g" % (alpha, T),
+                                   greedy(leaves, lg, keep, alpha, T, seed + 1000 * r + 7)))
+    out = []
+    for cap in sorted(caps_log2):
+        best = None
+        for name, pairs in candidates:
+            try:
+                sl = choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), 0, cap)
+            except ValueError:
+                continue
+            if len(sl) > max_sliced:
+                continue
+            mx, cost, _ = tree_stats(leaves, pairs, lg, keep, sl)
+            total = cost * 2.0 ** len(sl)
+            if best is None or total < best["total"]:
+                best = dict(cap_log2=cap, n_sliced=len(sl), cost_per_slice=cost, total=total,
+                            log2_max_intermediate=mx, path=name)
+        out.append(best if best is not None else dict(cap_log2=cap))
+    return out
