@@ -196,12 +196,50 @@ tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64
 tn_status tn_plan_status(tn_plan_t plan, void* stream);
 
 /*
+ * Per-step launch-form tuning of the tensor-core steps (paper Sec. III: each
+ * step's contraction kernel is chosen by timing the candidates).  Every
+ * tensor-core step that runs per batch tries each of its launch forms on one
+ * batch of the given slices and keeps the fastest.  The forms are: tile width
+ * (the widest for the step's N, or half of it), and at width 256 also 256-row
+ * tiles and two-CTA pairs (neither with split-precision chunked accumulation).
+ * Each form gets `reps` profiled passes, and the minimum event time per step
+ * decides.  Every form computes each output with the same MMAs over K in the
+ * same order, so tuning changes speed, not results.  The plan's captured batch
+ * graph is dropped and rebuilt on the next call.
+ *   plan      : created without TN_FLAG_PLAN_ONLY; a complex64 plan has no
+ *               tensor-core steps (nothing is tuned, TN_OK).
+ *   slice_ids : host [n_slices], 1 <= n_slices <= the plan's slice batch.
+ *   amps, workspace, ws_bytes, stream : as for tn_contract_slices (amps is
+ *               overwritten with the sum over the slices).
+ *   reps      : 1..64 timed passes per form.
+ *   forms     : host [3 * n_steps] (n_steps from tn_plan_steps) or NULL: per
+ *               step the chosen (tile width, row halves, pair); zeros for
+ *               steps that are not tuned.
+ * Errors: INVALID_ARG before any device work; CUDA_ERROR; TIMEOUT (a bounded
+ * device wait gave up).  On an error the plan keeps its previous forms.
+ * Synchronises `stream`.
+ */
+tn_status tn_plan_autotune(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices, void* amps,
+                           void* workspace, size_t ws_bytes, void* stream, int32_t reps, int32_t* forms);
+
+/*
+ * Set the launch forms of the tensor-core steps, e.g. those tn_plan_autotune
+ * returned, read back from a cache.  forms: host [3 * n_steps] with n_steps
+ * the plan's step count; per step (0, 0, 0) selects the default form, anything
+ * else must be one of the forms tn_plan_autotune may try for that step; steps
+ * that are not tuned take (0, 0, 0).  Validated in full before anything changes
+ * (INVALID_ARG).  Host-only: also valid on a TN_FLAG_PLAN_ONLY plan.
+ */
+tn_status tn_plan_set_tuning(tn_plan_t plan, const int32_t* forms, int32_t n_steps);
+
+/*
  * Contract the sub-networks `slice_ids[0..n_slices)` (host array; each id in
  * [0, 2^n_sliced), duplicates allowed and counted twice) and add them into
  * amps.  amps: device complex128 [G][2^l] (G = block edge dimension or 1);
  * accumulate = 0 overwrites amps with the sum, 1 adds to it.  Each slice is
- * computed in the plan's precision and summed across slices in FP64, in slice
- * order within a batch and batch by batch (deterministic).  workspace: device,
+ * computed in the plan's precision and summed across slices in FP64 in a fixed
+ * order: within a batch, four contiguous quarters of the batch each summed in
+ * slice order, then the quarters in order; batch by batch (deterministic).  workspace: device,
  * >= workspace_bytes of tn_plan_query, 256-byte aligned.  n_slices = 0 with
  * accumulate = 0 zeroes amps.
  */

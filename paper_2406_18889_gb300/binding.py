@@ -31,7 +31,8 @@ TN_FLAG_FINE_ACC = 0x20
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
            "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_plan_status",
-           "tn_permute", "tn_selftest_bounded_wait", "tn_selftest_fp32_peak", "tn_last_error", "tn_version")
+           "tn_permute", "tn_selftest_bounded_wait", "tn_selftest_fp32_peak", "tn_plan_autotune",
+           "tn_plan_set_tuning", "tn_last_error", "tn_version")
 
 
 class TNError(RuntimeError):
@@ -96,6 +97,8 @@ def load() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_double), vp]
     lib.tn_selftest_bounded_wait.argtypes = [ctypes.c_uint64, vp]
     lib.tn_selftest_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+    lib.tn_plan_autotune.argtypes = [vp, p_i64, i64, vp, vp, u64, vp, i32, p_i32]
+    lib.tn_plan_set_tuning.argtypes = [vp, p_i32, i32]
     for name in EXPORTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
     lib.tn_last_error.restype = ctypes.c_char_p
@@ -159,6 +162,25 @@ def tn_plan_steps(plan: int) -> dict:
                                 _p(nn, ctypes.c_int64), _p(k, ctypes.c_int64), _p(kinds, ctypes.c_int32),
                                 ctypes.byref(n)))
     return dict(batch=b, m=m, n=nn, k=k, kinds=kinds)
+
+
+def tn_plan_autotune(plan: int, slice_ids, amps_ptr: int, ws_ptr: int, ws_bytes: int, stream: int = 0,
+                     reps: int = 3) -> np.ndarray:
+    """Tunes the tensor-core steps' launch forms; returns int32 [n_steps, 3]
+    (tile width, row halves, pair; zeros for steps that are not tuned)."""
+    ids = _i64(slice_ids)
+    n = ctypes.c_int32()
+    _check(load().tn_plan_steps(ctypes.c_void_p(plan), 0, None, None, None, None, None, ctypes.byref(n)))
+    forms = np.zeros((n.value, 3), np.int32)
+    _check(load().tn_plan_autotune(ctypes.c_void_p(plan), _p(ids, ctypes.c_int64), len(ids),
+                                   ctypes.c_void_p(amps_ptr), ctypes.c_void_p(ws_ptr), int(ws_bytes),
+                                   ctypes.c_void_p(stream), int(reps), _p(forms, ctypes.c_int32)))
+    return forms
+
+
+def tn_plan_set_tuning(plan: int, forms) -> None:
+    f = np.ascontiguousarray(np.asarray(forms, dtype=np.int32).reshape(-1, 3))
+    _check(load().tn_plan_set_tuning(ctypes.c_void_p(plan), _p(f, ctypes.c_int32), f.shape[0]))
 
 
 def tn_contract_slices(plan: int, slice_ids, amps_ptr: int, accumulate: int, ws_ptr: int, ws_bytes: int,

@@ -161,6 +161,122 @@ tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64
   });
 }
 
+tn_status tn_plan_autotune(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices, void* amps,
+                           void* workspace, size_t ws_bytes, void* stream, int32_t reps, int32_t* forms) {
+  std::vector<LaunchRecord> rec;
+  auto free_rec = [&] {
+    for (auto& r : rec) {
+      if (r.start) cudaEventDestroy(r.start);
+      if (r.stop) cudaEventDestroy(r.stop);
+    }
+    rec.clear();
+  };
+  std::vector<TcForm> saved;
+  Plan* Pp = nullptr;
+  tn_status st = guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    Plan& P = *plan->p;
+    Pp = &P;
+    TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
+    TN_CHECK(n_slices >= 1 && n_slices <= P.B, TN_ERR_INVALID_ARG, "n_slices must be 1 .. the slice batch");
+    TN_CHECK(reps >= 1 && reps <= 64, TN_ERR_INVALID_ARG, "reps must be 1 .. 64");
+    const size_t T = P.steps.size();
+    for (size_t t = 0; t < T; ++t) saved.push_back({P.steps[t].tc_bn, P.steps[t].tc_mh, P.steps[t].tc_c2});
+    // the tuned steps in launch order (the order of their profiling records)
+    std::vector<size_t> tuned;
+    std::vector<std::vector<TcForm>> cand;
+    size_t most = 0;
+    for (size_t t = 0; t < T; ++t) {
+      std::vector<TcForm> f = tc_step_forms(P, t);
+      if (f.empty()) continue;
+      tuned.push_back(t);
+      most = std::max(most, f.size());
+      cand.push_back(std::move(f));
+    }
+    std::vector<float> best(tuned.size(), 3.0e38f);
+    std::vector<TcForm> pick(tuned.size());
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t c = 0; c < most; ++c) {
+      for (size_t i = 0; i < tuned.size(); ++i) {
+        const TcForm& f = cand[i][std::min(c, cand[i].size() - 1)];
+        Step& S = P.steps[tuned[i]];
+        S.tc_bn = f.bn;
+        S.tc_mh = f.mh;
+        S.tc_c2 = f.c2;
+      }
+      for (int r = 0; r < reps; ++r) {
+        contract_one(P, slice_ids, n_slices, amps, 0, workspace, ws_bytes, s, &rec);
+        TN_CUDA(cudaStreamSynchronize(s));
+        int h_err = 0;
+        TN_CUDA(cudaMemcpy(&h_err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        TN_CHECK(h_err == 0, TN_ERR_TIMEOUT, "a bounded device wait timed out");
+        size_t i = 0;
+        for (const LaunchRecord& L : rec) {
+          if (L.kind != 5) continue;
+          TN_CHECK(i < tuned.size(), TN_ERR_INVALID_ARG, "internal: tensor-core launch count");
+          float ms = 0.f;
+          TN_CUDA(cudaEventElapsedTime(&ms, L.start, L.stop));
+          if (ms < best[i]) {
+            best[i] = ms;
+            pick[i] = cand[i][std::min(c, cand[i].size() - 1)];
+          }
+          ++i;
+        }
+        TN_CHECK(i == tuned.size(), TN_ERR_INVALID_ARG, "internal: tensor-core launch count");
+        free_rec();
+      }
+    }
+    for (size_t i = 0; i < tuned.size(); ++i) {
+      Step& S = P.steps[tuned[i]];
+      S.tc_bn = pick[i].bn;
+      S.tc_mh = pick[i].mh;
+      S.tc_c2 = pick[i].c2;
+    }
+    drop_graph(P);
+    if (forms) {
+      for (size_t t = 0; t < T; ++t) {
+        forms[3 * t] = P.steps[t].tc_bn;
+        forms[3 * t + 1] = P.steps[t].tc_mh;
+        forms[3 * t + 2] = P.steps[t].tc_c2;
+      }
+    }
+  });
+  free_rec();
+  if (st != TN_OK && Pp && saved.size() == Pp->steps.size()) {
+    // keep the forms the plan had before the call
+    for (size_t t = 0; t < saved.size(); ++t) {
+      Pp->steps[t].tc_bn = saved[t].bn;
+      Pp->steps[t].tc_mh = saved[t].mh;
+      Pp->steps[t].tc_c2 = saved[t].c2;
+    }
+    drop_graph(*Pp);
+  }
+  return st;
+}
+
+tn_status tn_plan_set_tuning(tn_plan_t plan, const int32_t* forms, int32_t n_steps) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    Plan& P = *plan->p;
+    TN_CHECK(forms != nullptr, TN_ERR_INVALID_ARG, "forms is null");
+    TN_CHECK(n_steps == (int32_t)P.steps.size(), TN_ERR_INVALID_ARG, "n_steps differs from the plan's step count");
+    for (int32_t t = 0; t < n_steps; ++t) {
+      const int32_t bn = forms[3 * t], mh = forms[3 * t + 1], c2 = forms[3 * t + 2];
+      if (bn == 0 && mh == 0 && c2 == 0) continue;
+      bool ok = false;
+      for (const TcForm& f : tc_step_forms(P, (size_t)t)) ok = ok || (f.bn == bn && f.mh == mh && f.c2 == c2);
+      TN_CHECK(ok, TN_ERR_INVALID_ARG, "step " + std::to_string(t) + ": not a launch form of this step");
+    }
+    for (int32_t t = 0; t < n_steps; ++t) {
+      Step& S = P.steps[t];
+      S.tc_bn = forms[3 * t];
+      S.tc_mh = forms[3 * t + 1];
+      S.tc_c2 = forms[3 * t + 2];
+    }
+    drop_graph(P);
+  });
+}
+
 tn_status tn_contract_slices(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices, void* amps,
                              int accumulate, void* workspace, size_t ws_bytes, void* stream) {
   return guarded([&] {

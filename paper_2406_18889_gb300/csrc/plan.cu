@@ -334,6 +334,45 @@ TcRoles tc_roles(const Step& S, bool* ok_out = nullptr) {
   return r;
 }
 
+// split products also accumulate K in chunks (the tensor cores' own
+// accumulation error grows with K): 4 k tiles, or 1 with TN_FLAG_FINE_ACC;
+// single CTAs then
+int tc_acc_split(const Plan& P, const Step& S) { return (P.flags & TN_FLAG_FINE_ACC) ? 1 : S.hilo ? 4 : 0; }
+// The default launch form: the widest tile for N; two-CTA pairs with
+// TN_FLAG_TC_PAIR; 256-row tiles for K-heavy steps (they load each B tile once
+// for two 128-row MMAs, and the expanded B dominates the bytes a tile brings
+// into shared memory).
+TcForm tc_default_form(const Plan& P, const Step& S, const TcRoles& r) {
+  TcForm f{tc_gemm_bn(r.N), 1, 0};
+  const bool acc = tc_acc_split(P, S) != 0;
+  f.c2 = !acc && (P.flags & TN_FLAG_TC_PAIR) && f.bn == 256 ? 1 : 0;
+  f.mh = (!acc && !f.c2 && f.bn == 256 && r.M >= 256 && r.K >= 256) ? 2 : 1;
+  return f;
+}
+// Every form the tuner may try (the default first): the widest tile for N or
+// half of it; at width 256 also 256-row tiles (M >= 256) and two-CTA pairs,
+// neither with chunked accumulation -- the forms the launcher accepts.
+std::vector<TcForm> tc_forms(const Plan& P, const Step& S) {
+  const TcRoles r = tc_roles(S);
+  std::vector<TcForm> out{tc_default_form(P, S, r)};
+  auto add = [&](TcForm f) {
+    for (const TcForm& g : out)
+      if (g.bn == f.bn && g.mh == f.mh && g.c2 == f.c2) return;
+    out.push_back(f);
+  };
+  const bool acc = tc_acc_split(P, S) != 0;
+  const int bn0 = tc_gemm_bn(r.N);
+  for (int bn : {bn0, bn0 / 2}) {
+    if (bn < 32) continue;
+    add({bn, 1, 0});
+    if (bn == 256 && !acc) {
+      if (r.M >= 256) add({bn, 2, 0});
+      add({bn, 1, 1});
+    }
+  }
+  return out;
+}
+
 MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>& leaf_src_layout,
                     bool micro) {
   MemPlan M;
@@ -534,15 +573,11 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     tp.out_hilo = out_hilo ? 1 : 0;
     tp.scale = scale;
     tp.err = P.d_err;
-    tp.bn = tc_gemm_bn(r.N);
-    // split products also accumulate K in chunks (the tensor cores' own
-    // accumulation error grows with K): 4 k tiles, or 1 with TN_FLAG_FINE_ACC;
-    // single CTAs then
-    tp.acc_split = (P.flags & TN_FLAG_FINE_ACC) ? 1 : S.hilo ? 4 : 0;
-    tp.cluster2 = !tp.acc_split && (P.flags & TN_FLAG_TC_PAIR) && tp.bn == 256 ? 1 : 0;
-    // K-heavy steps: 256-row tiles load each B tile once for two 128-row MMAs
-    // (the expanded B dominates the bytes a tile brings into shared memory)
-    tp.m_halves = (!tp.acc_split && !tp.cluster2 && tp.bn == 256 && r.M >= 256 && r.K >= 256) ? 2 : 1;
+    tp.acc_split = tc_acc_split(P, S);
+    const TcForm f = S.tc_bn ? TcForm{S.tc_bn, S.tc_mh, S.tc_c2} : tc_default_form(P, S, r);
+    tp.bn = f.bn;
+    tp.m_halves = f.mh;
+    tp.cluster2 = f.c2;
     const char* a_hi = X.base(r.a_node);
     R.begin(5, flops, bytes);
     launch_gemm_tc(a_hi, S.hilo ? a_hi + NA.elems * 4 : nullptr, r.a_bt, r.a_m, bx, bx_lo, tp,
@@ -1077,6 +1112,20 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
   TN_CHECK(h_err == 0, TN_ERR_TIMEOUT, "a bounded device wait timed out during plan creation");
   TN_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
   return Pp;
+}
+
+// ---------------------------------------------------------------- tuning
+std::vector<TcForm> tc_step_forms(const Plan& P, size_t t) {
+  const Step& S = P.steps[t];
+  if (!S.tc || S.hoisted || P.mem.c64) return {};
+  return tc_forms(P, S);
+}
+
+void drop_graph(Plan& P) {
+  if (P.graph) cudaGraphExecDestroy(P.graph);
+  P.graph = nullptr;
+  P.graph_ws = P.graph_amps = nullptr;
+  P.graph_acc = -1;
 }
 
 // ---------------------------------------------------------------- execute

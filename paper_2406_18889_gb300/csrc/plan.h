@@ -26,6 +26,12 @@ struct Node {
   bool hilo = false;        // 16-bit value followed by its 16-bit rounding residual
 };
 
+// Launch form of a tensor-core step: tile width in real columns, 128-row
+// halves per tile, two-CTA pair.
+struct TcForm {
+  int bn, mh, c2;
+};
+
 struct Step {
   int a = -1, b = -1, c = -1;          // node ids: operands and result
   std::vector<int> bt, m, n, k;        // ordered index groups
@@ -42,6 +48,7 @@ struct Step {
   bool fuse_expand = false;            // writes its result as the consumer's expanded operand
   bool b_fused = false;                // tensor-core step whose expanded operand its producer wrote
   bool micro = false;                  // small per-batch step run inside the fused small-step launch
+  int tc_bn = 0, tc_mh = 0, tc_c2 = 0;  // tuned tensor-core launch form (tc_bn 0: the default heuristics)
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network
 };
@@ -116,6 +123,12 @@ struct LaunchRecord {
   double flops, bytes;
   cudaEvent_t start, stop;
 };
+
+// The launch forms the tuner may try for step t (the default first); empty
+// unless t is a tensor-core step that runs per batch.
+std::vector<TcForm> tc_step_forms(const Plan& P, size_t t);
+// Forget the captured batch graph (its kernels' launch forms changed).
+void drop_graph(Plan& P);
 
 // Queue one batch (n_valid <= B slice ids already in d_slice_ids) into amps.
 // With `rec`, launches directly and brackets every kernel with an event pair.

@@ -49,6 +49,7 @@ class Plan:
                                        tree.sliced_edges, PREC[prec], flags, max_slice_batch,
                                        mem_cap_bytes, s.cuda_stream)
         self.info = B.tn_plan_query(self.handle)
+        self.prec, self.flags = prec, flags
         self.max_slice_batch = max_slice_batch
         self.G = tn.n_blocks
         self.J = 1
@@ -75,6 +76,52 @@ class Plan:
         B.tn_contract_slices(self.handle, slice_ids, out.data_ptr(), int(accumulate),
                              self.workspace.data_ptr(), self.workspace.numel(), s.cuda_stream)
         return out
+
+    def autotune(self, slice_ids: Optional[Sequence[int]] = None, reps: int = 3, cache: Optional[str] = None,
+                 stream=None) -> np.ndarray:
+        """Launch forms of the tensor-core steps (tile width, row halves, pair),
+        timed on one batch of slices (the first ``max_slice_batch`` of
+        ``slice_ids``, default the first slices) by ``tn_plan_autotune``.  With
+        ``cache`` (a JSON file of forms keyed by precision, flags and step shape),
+        forms found there are set without timing, and newly tuned ones are added
+        to the file.  Returns int32 [n_steps, 3] (zeros: step not tuned)."""
+        import json
+        torch = _torch()
+        st = self.steps()
+        kinds = st["kinds"]
+        keys = [f"{self.prec}/{self.flags}/{st['batch'][t]}x{st['m'][t]}x{st['n'][t]}x{st['k'][t]}/{kinds[t]}"
+                for t in range(len(kinds))]
+        tuned = [t for t in range(len(kinds)) if (kinds[t] & 8) and not (kinds[t] & 4)]
+        known = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                known = json.load(fh)
+        if tuned and all(keys[t] in known for t in tuned):
+            forms = np.zeros((len(kinds), 3), np.int32)
+            for t in tuned:
+                forms[t] = known[keys[t]]
+            try:
+                B.tn_plan_set_tuning(self.handle, forms)
+                return forms
+            except B.TNError:
+                pass  # a stale entry: tune again
+        if slice_ids is None:
+            slice_ids = np.arange(min(self.max_slice_batch, self.n_slices_total), dtype=np.int64)
+        ids = np.asarray(slice_ids, dtype=np.int64)[: self.max_slice_batch]
+        if self.workspace is None:
+            raise ValueError("plan created without a workspace")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        out = torch.empty((self.G, self.J), dtype=torch.complex128, device="cuda")
+        forms = B.tn_plan_autotune(self.handle, ids, out.data_ptr(), self.workspace.data_ptr(),
+                                   self.workspace.numel(), s.cuda_stream, reps)
+        if cache and tuned:
+            for t in tuned:
+                known[keys[t]] = [int(x) for x in forms[t]]
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(known, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return forms
 
     def close(self):
         if getattr(self, "handle", None):

@@ -28,6 +28,10 @@ def test_exports_every_declared_symbol(lib):
     for name in declared:
         assert hasattr(L, name), name
     assert set(lib.EXPORTS) == declared
+    # every entry point with arguments has its C types declared (64-bit sizes and
+    # pointers would otherwise be passed as C ints)
+    for name in declared - {"tn_last_error", "tn_version"}:
+        assert getattr(L, name).argtypes is not None, name
     assert "sm_103a" in lib.tn_version()
 
 
@@ -206,3 +210,45 @@ def test_injected_plan_faults(lib, prep, monkeypatch, what, status):
     assert "TN_FAULT" in lib.tn_last_error()
     monkeypatch.delenv("TN_FAULT")
     lib.tn_plan_destroy(_create(lib, prep))
+
+
+def test_tuning_forms_validated_before_any_change(lib):
+    # per-step launch forms of the tensor-core steps (no device work: plan-only)
+    from paper_2406_18889_gb300 import engine as E
+    w = W.workload("grid4x6_d14")
+    prep = E.prepare(w)
+    h = _create(lib, prep, flags=lib.TN_FLAG_PLAN_ONLY | lib.TN_FLAG_HOIST_INVARIANT, prec=2, max_slice_batch=64)
+    try:
+        k = lib.tn_plan_steps(h)["kinds"]
+        tuned = np.where(((k & 8) > 0) & ((k & 4) == 0))[0]
+        other = np.where((k & 8) == 0)[0]
+        assert len(tuned) >= 1 and len(other) >= 1
+        zeros = np.zeros((len(k), 3), np.int32)
+        lib.tn_plan_set_tuning(h, zeros)  # every step at its default form
+        candidates = [(256, 1, 0), (256, 2, 0), (256, 1, 1), (128, 1, 0), (64, 1, 0), (32, 1, 0)]
+        for t in tuned:
+            accepted = []
+            for f in candidates:
+                forms = zeros.copy()
+                forms[t] = f
+                try:
+                    lib.tn_plan_set_tuning(h, forms)
+                    accepted.append(f)
+                except lib.TNError as e:
+                    assert e.status == 1
+            # the widest tile for N and half of it at least; pairs and 256-row tiles only at width 256
+            assert len(accepted) >= 2
+            if (256, 1, 1) in accepted or (256, 2, 0) in accepted:
+                assert (256, 1, 0) in accepted
+        for bad_step, bad in ((tuned[0], (999, 1, 0)), (tuned[0], (256, 3, 0)), (other[0], (256, 1, 0))):
+            forms = zeros.copy()
+            forms[bad_step] = bad
+            with pytest.raises(lib.TNError) as ei:
+                lib.tn_plan_set_tuning(h, forms)
+            assert ei.value.status == 1
+        with pytest.raises(lib.TNError):
+            lib.tn_plan_set_tuning(h, zeros[:-1])  # step count differs
+        with pytest.raises(lib.TNError):  # timing needs a device plan
+            lib.tn_plan_autotune(h, [0], 1 << 20, 1 << 20, 1 << 30, 0, 1)
+    finally:
+        lib.tn_plan_destroy(h)
