@@ -21,7 +21,9 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls queue work on it and return without synchronising,
  *     except where a function says it synchronises.
- *   - A plan is immutable after creation and may be shared by host threads;
+ *   - A plan is immutable after creation, except for the tensor-core launch
+ *     forms that tn_plan_autotune and tn_plan_set_tuning set (no other call
+ *     may run on the plan meanwhile), and may be shared by host threads;
  *     concurrent calls must use distinct workspaces and output buffers.
  *   - Complex numbers are interleaved (re, im); complex64 = 2 x float,
  *     complex128 = 2 x double.
