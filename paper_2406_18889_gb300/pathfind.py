@@ -21,6 +21,14 @@ module uses a greedy rule with seeded random restarts:
   dimensions, then Fiduccia-Mattheyses moves), recursively, and contracting
   small parts greedily gives trees whose intermediates follow the cuts.
   ``plan_tree(method="both")`` keeps the cheaper of the two searches.
+* subtree reconfiguration (``reconfigure``): a tensor's edges after contraction
+  depend only on which leaves it holds, so the subtree between any node and a
+  frontier of up to 8 of its descendants can be re-contracted in the cheapest
+  order, found exactly by dynamic programming over frontier subsets; and
+  slicing interleaved with it (``slice_and_reconfigure``: a few bonds sliced at
+  a time, the rest of the network reconfigured in between, sliced bonds given
+  back while the cap allows).  ``plan_tree(refine=True)`` and
+  ``memory_cap_sweep(refine=True)`` add these trees to the candidates.
 
 All sizes are log2 element counts (every edge dimension is a power of two).
 Costs are complex multiply-adds: a step costs the product of the dimensions of
@@ -384,11 +392,14 @@ PARTITION_IMBALANCES = (0.2, 0.3, 0.4, 0.5)
 
 def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = None,
               restarts: int = 4, seed: int = 0, sliced: Optional[Sequence[int]] = None,
-              method: str = "greedy") -> Tree:
+              method: str = "greedy", refine: bool = False, groups: Sequence[int] = (2, 4)) -> Tree:
     """Search paths -- the greedy alpha/temperature sweep (``restarts`` seeds per
     noisy setting), recursive bisection at several balance windows, or both
     (``method``) -- slice each (unless ``sliced`` is given), keep the cheapest
-    total."""
+    total.  ``refine``: every candidate is also re-optimised by subtree
+    reconfiguration -- with a cap, slicing interleaved with reconfiguration
+    (``slice_and_reconfigure``, each group size in ``groups``); otherwise the
+    network without its sliced bonds is reconfigured."""
     if method not in ("greedy", "partition", "both"):
         raise ValueError("method must be greedy, partition or both")
     lg = log2dims(tn)
@@ -402,13 +413,24 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     if method in ("partition", "both"):
         for imb in PARTITION_IMBALANCES:
             candidates.append(partition_path(leaves, lg, keep, imbalance=imb))
-    best = None
+    sliced_cands = []
     for pairs in candidates:
         if sliced is None:
             sl = choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced, cap_log2) \
                 if (n_sliced or cap_log2 is not None) else []
         else:
             sl = list(sliced)
+        sliced_cands.append((pairs, sl))
+        if refine:
+            if sliced is None and cap_log2 is not None and not n_sliced:
+                for g in groups:
+                    sliced_cands.append(slice_and_reconfigure(leaves, pairs, lg, keep, len(tn.edge_dim),
+                                                              cap_log2, group=g))
+            else:
+                stripped = [frozenset(x - set(sl)) for x in leaves]
+                sliced_cands.append((reconfigure(stripped, pairs, lg, keep, cap_log2=cap_log2), list(sl)))
+    best = None
+    for pairs, sl in sliced_cands:
         mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
         if cap_log2 is not None and mx > cap_log2:
             continue
@@ -424,7 +446,8 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
 
 # ------------------------------------------------------------ memory vs complexity
 def memory_cap_sweep(tn: TensorNetwork, caps_log2: Sequence[float], method: str = "partition",
-                     max_sliced: int = 62, restarts: int = 1, seed: int = 0) -> List[dict]:
+                     max_sliced: int = 62, restarts: int = 1, seed: int = 0, refine: bool = False,
+                     groups: Sequence[int] = (2, 4)) -> List[dict]:
     """Time complexity against the memory cap (paper Sec. III: a larger cap on
     the largest intermediate means fewer sliced bonds and less total work).
 
@@ -433,7 +456,9 @@ def memory_cap_sweep(tn: TensorNetwork, caps_log2: Sequence[float], method: str 
     sliced greedily down to every cap.  Returns one entry per cap, ascending:
     ``cap_log2``, ``n_sliced``, ``cost_per_slice`` and ``total`` (complex
     multiply-adds over all slices) of the cheapest total found, or only
-    ``cap_log2`` when no candidate fits within ``max_sliced`` sliced bonds."""
+    ``cap_log2`` when no candidate fits within ``max_sliced`` sliced bonds.
+    ``refine``: each candidate is also sliced with interleaved subtree
+    reconfiguration (``slice_and_reconfigure``, every group size in ``groups``)."""
     if method not in ("greedy", "partition", "both"):
         raise ValueError("method must be greedy, partition or both")
     lg = log2dims(tn)
@@ -452,16 +477,208 @@ def memory_cap_sweep(tn: TensorNetwork, caps_log2: Sequence[float], method: str 
     for cap in sorted(caps_log2):
         best = None
         for name, pairs in candidates:
+            trees = []
             try:
-                sl = choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), 0, cap)
+                trees.append((name, pairs, choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), 0, cap)))
             except ValueError:
-                continue
-            if len(sl) > max_sliced:
-                continue
-            mx, cost, _ = tree_stats(leaves, pairs, lg, keep, sl)
-            total = cost * 2.0 ** len(sl)
-            if best is None or total < best["total"]:
-                best = dict(cap_log2=cap, n_sliced=len(sl), cost_per_slice=cost, total=total,
-                            log2_max_intermediate=mx, path=name)
+                pass
+            if refine:
+                for g in groups:
+                    try:
+                        p2, sl2 = slice_and_reconfigure(leaves, pairs, lg, keep, len(tn.edge_dim), cap, group=g)
+                    except ValueError:
+                        continue
+                    trees.append((f"{name} + reconfiguration (groups of {g})", p2, sl2))
+            for label, p2, sl in trees:
+                if len(sl) > max_sliced:
+                    continue
+                mx, cost, _ = tree_stats(leaves, p2, lg, keep, sl)
+                total = cost * 2.0 ** len(sl)
+                if best is None or total < best["total"]:
+                    best = dict(cap_log2=cap, n_sliced=len(sl), cost_per_slice=cost, total=total,
+                                log2_max_intermediate=mx, path=label, pairs=p2, sliced=list(sl))
         out.append(best if best is not None else dict(cap_log2=cap))
     return out
+
+
+# ------------------------------------------------------------ subtree reconfiguration
+def reconfigure(leaves: Sequence[FrozenSet[int]], pairs, lg: Sequence[float], keep: FrozenSet[int],
+                cap_log2: Optional[float] = None, size: int = 8, sweeps: int = 3):
+    """Local re-optimisation of a contraction tree (the path stays a tree over the
+    same leaves with the same output).
+
+    A tensor's edges after contraction depend only on which leaves it holds, so
+    any subtree can be re-contracted freely between its root and a frontier of
+    its descendants.  For every node, a frontier of up to ``size`` tensors is
+    grown by expanding the most expensive step inside it; the cheapest order
+    of contracting the frontier back into the node is found exactly by dynamic
+    programming over frontier subsets (a subset's result keeps the edges that
+    also occur outside it), and replaces the subtree when cheaper with every
+    new intermediate within ``cap_log2``.  Sweeps repeat while the cost falls.
+    Costs as in ``tree_stats``: per step, the product of the dimensions of all
+    edges of both operands.  Returns the new SSA pairs."""
+    L = len(leaves)
+    nodes = replay(leaves, pairs, keep)
+    ordinary = 0
+    special = []
+    for s in nodes:
+        for e in s:
+            if lg[e] == 1.0:
+                ordinary |= 1 << e
+    for e in {e for s in nodes for e in s}:
+        if lg[e] != 1.0:
+            special.append((1 << e, lg[e]))
+
+    def weight(m: int) -> float:
+        w = float((m & ordinary).bit_count())
+        for bit, v in special:
+            if m & bit:
+                w += v
+        return w
+
+    mask = [0] * len(nodes)
+    for i, s in enumerate(nodes):
+        m = 0
+        for e in s:
+            m |= 1 << e
+        mask[i] = m
+    child: Dict[int, Tuple[int, int]] = {L + t: (a, b) for t, (a, b) in enumerate(pairs)}
+    root = L + len(pairs) - 1 if pairs else 0
+    nxt = len(nodes)
+
+    def step_cost(v: int) -> float:
+        a, b = child[v]
+        return 2.0 ** weight(mask[a] | mask[b])
+
+    def try_node(v: int) -> bool:
+        nonlocal nxt
+        frontier = list(child[v])
+        inner = [v]
+        while len(frontier) < size:
+            cand = [f for f in frontier if f in child]
+            if not cand:
+                break
+            f = max(cand, key=step_cost)
+            frontier.remove(f)
+            frontier.extend(child[f])
+            inner.append(f)
+        k = len(frontier)
+        if k < 3:
+            return False
+        current = sum(step_cost(u) for u in inner)
+        fm = [mask[f] for f in frontier]
+        full = (1 << k) - 1
+        union = [0] * (full + 1)
+        for S in range(1, full + 1):
+            low = S & -S
+            union[S] = union[S ^ low] | fm[low.bit_length() - 1]
+        out = [0] * (full + 1)
+        for S in range(1, full + 1):
+            out[S] = union[S] & (union[full ^ S] | mask[v])
+        wout = [weight(out[S]) for S in range(full + 1)]
+        best = [0.0] * (full + 1)
+        split = [0] * (full + 1)
+        for S in range(1, full + 1):
+            if S & (S - 1) == 0:
+                continue
+            if S != full and cap_log2 is not None and wout[S] > cap_log2 + 1e-9:
+                best[S] = math.inf
+                continue
+            low = S & -S
+            bc, bs = math.inf, 0
+            sub = (S - 1) & S
+            while sub:
+                if sub & low:
+                    rest = S ^ sub
+                    c = best[sub] + best[rest]
+                    if c < bc:
+                        c += 2.0 ** weight(out[sub] | out[rest])
+                        if c < bc:
+                            bc, bs = c, sub
+                sub = (sub - 1) & S
+            best[S], split[S] = bc, bs
+        if not best[full] < current * (1 - 1e-9):
+            return False
+        for u in inner[1:]:
+            del child[u]
+
+        def build(S: int) -> int:
+            nonlocal nxt
+            if S & (S - 1) == 0:
+                return frontier[S.bit_length() - 1]
+            a, b = build(split[S]), build(S ^ split[S])
+            if S == full:
+                child[v] = (a, b)
+                return v
+            u = nxt
+            nxt += 1
+            mask.append(out[S])
+            child[u] = (a, b)
+            return u
+
+        build(full)
+        return True
+
+    for _ in range(sweeps):
+        changed = False
+        for v in sorted(child.keys()):
+            if v in child and try_node(v):
+                changed = True
+        if not changed:
+            break
+    # back to SSA pairs, children before parents
+    ssa: Dict[int, int] = {i: i for i in range(L)}
+    out_pairs: List[Tuple[int, int]] = []
+    stack = [(root, False)]
+    while stack:
+        v, done = stack.pop()
+        if v < L:
+            continue
+        if done:
+            a, b = child[v]
+            ssa[v] = L + len(out_pairs)
+            out_pairs.append((ssa[a], ssa[b]))
+        else:
+            stack.append((v, True))
+            a, b = child[v]
+            stack.append((b, False))
+            stack.append((a, False))
+    return out_pairs
+
+
+def refine_sliced(leaves, pairs, lg, keep, sliced, cap_log2: Optional[float] = None, rounds: int = 2,
+                  size: int = 8):
+    """Reconfigure a sliced tree on the network with its sliced bonds removed,
+    then restore sliced bonds (last chosen first) while the largest
+    intermediate still fits the cap -- restoring one never raises the total
+    (per-slice cost at most doubles while the slice count halves).  Returns
+    (pairs, sliced)."""
+    sl = list(sliced)
+    for _ in range(rounds):
+        stripped = [frozenset(x - set(sl)) for x in leaves]
+        pairs = reconfigure(stripped, pairs, lg, keep, cap_log2=cap_log2, size=size)
+        for e in list(reversed(sl)):
+            trial = [x for x in sl if x != e]
+            mx, _, _ = tree_stats(leaves, pairs, lg, keep, trial)
+            if cap_log2 is None or mx <= cap_log2 + 1e-9:
+                sl = trial
+    return pairs, sl
+
+
+def slice_and_reconfigure(leaves, pairs, lg, keep, n_edges: int, cap_log2: float, group: int = 4,
+                          size: int = 8):
+    """Slicing interleaved with reconfiguration: bonds are sliced ``group`` at a
+    time (greedy, as ``choose_slices``) and the network without them is
+    reconfigured after each group, until the largest intermediate fits the cap;
+    then ``refine_sliced``.  Returns (pairs, sliced)."""
+    sl: List[int] = []
+    pairs = reconfigure(leaves, pairs, lg, keep, size=size)
+    while True:
+        mx, _, _ = tree_stats(leaves, pairs, lg, keep, sl)
+        if mx <= cap_log2 + 1e-9:
+            break
+        stripped = [frozenset(x - set(sl)) for x in leaves]
+        sl += choose_slices(stripped, pairs, lg, keep, n_edges, n_sliced=group)
+        stripped = [frozenset(x - set(sl)) for x in leaves]
+        pairs = reconfigure(stripped, pairs, lg, keep, size=size)
+    return refine_sliced(leaves, pairs, lg, keep, sl, cap_log2=cap_log2, size=size)
