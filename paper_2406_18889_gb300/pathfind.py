@@ -666,19 +666,24 @@ def refine_sliced(leaves, pairs, lg, keep, sliced, cap_log2: Optional[float] = N
 
 
 def slice_and_reconfigure(leaves, pairs, lg, keep, n_edges: int, cap_log2: float, group: int = 4,
-                          size: int = 8):
+                          size: int = 8, max_sliced: int = 62):
     """Slicing interleaved with reconfiguration: bonds are sliced ``group`` at a
     time (greedy, as ``choose_slices``) and the network without them is
     reconfigured after each group, until the largest intermediate fits the cap;
-    then ``refine_sliced``.  Returns (pairs, sliced)."""
+    then ``refine_sliced``.  Returns (pairs, sliced); ValueError once more than
+    ``max_sliced`` bonds would be needed."""
     sl: List[int] = []
     pairs = reconfigure(leaves, pairs, lg, keep, size=size)
     while True:
         mx, _, _ = tree_stats(leaves, pairs, lg, keep, sl)
         if mx <= cap_log2 + 1e-9:
             break
+        if len(sl) >= max_sliced:
+            raise ValueError("no tree within the cap with at most max_sliced sliced bonds")
         stripped = [frozenset(x - set(sl)) for x in leaves]
         sl += choose_slices(stripped, pairs, lg, keep, n_edges, n_sliced=group)
         stripped = [frozenset(x - set(sl)) for x in leaves]
+        # uncapped in between: a tree may grow before slicing takes it back
+        # under the cap (capping it here was measured to give worse trees)
         pairs = reconfigure(stripped, pairs, lg, keep, size=size)
     return refine_sliced(leaves, pairs, lg, keep, sl, cap_log2=cap_log2, size=size)
