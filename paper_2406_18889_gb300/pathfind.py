@@ -399,7 +399,8 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     total.  ``refine``: every candidate is also re-optimised by subtree
     reconfiguration -- with a cap, slicing interleaved with reconfiguration
     (``slice_and_reconfigure``, each group size in ``groups``); otherwise the
-    network without its sliced bonds is reconfigured."""
+    network without its sliced bonds is reconfigured, its intermediates kept
+    within the cap or, without one, within the unrefined tree's largest."""
     if method not in ("greedy", "partition", "both"):
         raise ValueError("method must be greedy, partition or both")
     lg = log2dims(tn)
@@ -427,8 +428,12 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
                     sliced_cands.append(slice_and_reconfigure(leaves, pairs, lg, keep, len(tn.edge_dim),
                                                               cap_log2, group=g))
             else:
+                # a fixed slice set: reconfigure within the cap, or within the
+                # tree's own largest intermediate when there is no cap
+                mx0, _, _ = tree_stats(leaves, pairs, lg, keep, sl)
                 stripped = [frozenset(x - set(sl)) for x in leaves]
-                sliced_cands.append((reconfigure(stripped, pairs, lg, keep, cap_log2=cap_log2), list(sl)))
+                lim = cap_log2 if cap_log2 is not None else mx0
+                sliced_cands.append((reconfigure(stripped, pairs, lg, keep, cap_log2=lim), list(sl)))
     best = None
     for pairs, sl in sliced_cands:
         mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
@@ -456,8 +461,9 @@ def memory_cap_sweep(tn: TensorNetwork, caps_log2: Sequence[float], method: str 
     sliced greedily down to every cap.  Returns one entry per cap, ascending:
     ``cap_log2``, ``n_sliced``, ``cost_per_slice`` and ``total`` (complex
     multiply-adds over all slices) of the cheapest total found, or only
-    ``cap_log2`` when no candidate fits within ``max_sliced`` sliced bonds.
-    ``refine``: each candidate is also sliced with interleaved subtree
+    ``cap_log2`` when no candidate fits within ``max_sliced`` sliced bonds.  A
+    tree found for a smaller cap also fits a larger one and is carried forward,
+    so totals never rise with the cap.  ``refine``: each candidate is also sliced with interleaved subtree
     reconfiguration (``slice_and_reconfigure``, every group size in ``groups``)."""
     if method not in ("greedy", "partition", "both"):
         raise ValueError("method must be greedy, partition or both")
@@ -497,6 +503,11 @@ def memory_cap_sweep(tn: TensorNetwork, caps_log2: Sequence[float], method: str 
                 if best is None or total < best["total"]:
                     best = dict(cap_log2=cap, n_sliced=len(sl), cost_per_slice=cost, total=total,
                                 log2_max_intermediate=mx, path=label, pairs=p2, sliced=list(sl))
+        # a tree within a smaller cap fits this one too
+        prev = next((r for r in reversed(out) if "total" in r), None)
+        if prev is not None and (best is None or prev["total"] < best["total"]):
+            best = dict(prev, cap_log2=cap, path=prev["path"] + f" (found for cap 2^{prev['cap_log2']:g})"
+                        if "found for cap" not in prev["path"] else prev["path"])
         out.append(best if best is not None else dict(cap_log2=cap))
     return out
 

@@ -104,3 +104,15 @@ def test_slicing_with_reconfiguration_fits_the_cap(grid24):
     t1 = P.plan_tree(tn, cap_log2=cap, method="partition", refine=True)
     assert t1.log2_max_intermediate <= cap
     assert t1.cost_per_slice * 2.0 ** len(t1.sliced_edges) <= t0.cost_per_slice * 2.0 ** len(t0.sliced_edges)
+
+
+def test_refined_plan_for_the_24_qubit_workload():
+    # the same workload (6 sliced bonds, 64 slices): the refined search needs
+    # less work per slice than the plain greedy tree, with no larger intermediate
+    from paper_2406_18889_gb300 import engine as E
+    w = W.workload("grid4x6_d14")
+    plain = E.prepare(w, restarts=1).tree
+    refined = E.prepare(w, restarts=1, refine=True).tree
+    assert len(refined.sliced_edges) == len(plain.sliced_edges) == 6
+    assert refined.cost_per_slice < plain.cost_per_slice
+    assert refined.log2_max_intermediate <= plain.log2_max_intermediate
