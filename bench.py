@@ -185,10 +185,10 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def sliced_wires():
+def sliced_wires(refine: bool = False):
     from paper_2406_18889_gb300 import engine as E
     w = rank_workload(0)
-    prep = E.prepare(w)
+    prep = E.prepare(w, refine=refine)
     return w, prep, [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
 
 
@@ -196,7 +196,7 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    w, prep, wires = sliced_wires()
+    w, prep, wires = sliced_wires(args.refine_path)
     sample = "1 slice of 64 per step, oracle O2 (naive FP64 einsum contractor, numpy matmul)"
     for s in range(args.warmup):
         oracle_slices_per_s(w, wires, [s % 64])
@@ -329,7 +329,7 @@ def run_ours(args):
     from paper_2406_18889_gb300 import engine as E
 
     w = rank_workload(rank)
-    prep = E.prepare(w)
+    prep = E.prepare(w, refine=args.refine_path)
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
     plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
     S = plan.n_slices_total
@@ -467,7 +467,7 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        _, _, wires = sliced_wires()
+        _, _, wires = sliced_wires(args.refine_path)
         v = oracle_slices_per_s(rank_workload(0), wires, [0, 1])
         cpu = {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
                "sample": "2 of the 64 slices, oracle O2 (naive FP64 einsum contractor, numpy matmul)"}
@@ -480,6 +480,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
                    "hoist_invariant": not args.no_hoist, "autotune": bool(args.autotune),
+                   "path": "greedy + subtree reconfiguration" if args.refine_path else "greedy",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"{world} independent block sets (one per GPU)"},
         "useful_tflops": value * useful_per_slice / 1e12,
@@ -517,7 +518,7 @@ def run_uneven(args):
     torch.cuda.set_device(0)
     ws = W.configs.uneven_batch(64)
     t0 = time.perf_counter()
-    preps = [E.prepare(w, restarts=1) for w in ws]
+    preps = [E.prepare(w, restarts=1, refine=args.refine_path) for w in ws]
     plan_s = time.perf_counter() - t0
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
     # slice batch at most 16: at 64 the largest (28-qubit) circuit alone needs a 164 GB workspace
@@ -575,7 +576,7 @@ def run_sycamore(args):
     w = W.workload("sycamore53_d20", cycles=20, l=10, G=16)
     tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
     t0 = time.perf_counter()
-    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition")
+    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition", refine=args.refine_path)
     plan_s = time.perf_counter() - t0
     plan = E.Plan(tn, tree, prec=args.prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=1)
     s = len(tree.sliced_edges)
@@ -621,6 +622,8 @@ def main(argv=None):
     ap.add_argument("--no-c64", action="store_true", help="skip timing the complex64 path alongside")
     ap.add_argument("--no-hoist", action="store_true",
                     help="recompute slice-independent subtrees in every batch instead of once per plan")
+    ap.add_argument("--refine-path", action="store_true",
+                    help="plan with subtree reconfiguration (less work per slice; same slices and outputs)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the tensor-core steps' launch forms on one batch first and keep the fastest")
     ap.add_argument("--batch", type=int, default=64)
