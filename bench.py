@@ -188,7 +188,7 @@ def host_cores() -> int:
 def sliced_wires(refine: bool = False):
     from paper_2406_18889_gb300 import engine as E
     w = rank_workload(0)
-    prep = E.prepare(w, refine=refine)
+    prep = E.prepare(w, refine=refine, method="both" if refine else "greedy")
     return w, prep, [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
 
 
@@ -329,7 +329,7 @@ def run_ours(args):
     from paper_2406_18889_gb300 import engine as E
 
     w = rank_workload(rank)
-    prep = E.prepare(w, refine=args.refine_path)
+    prep = E.prepare(w, refine=args.refine_path, method="both" if args.refine_path else "greedy")
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
     plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
     S = plan.n_slices_total
@@ -480,7 +480,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
                    "hoist_invariant": not args.no_hoist, "autotune": bool(args.autotune),
-                   "path": "greedy + subtree reconfiguration" if args.refine_path else "greedy",
+                   "path": "greedy and bisection + subtree reconfiguration" if args.refine_path else "greedy",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"{world} independent block sets (one per GPU)"},
         "useful_tflops": value * useful_per_slice / 1e12,
@@ -518,7 +518,8 @@ def run_uneven(args):
     torch.cuda.set_device(0)
     ws = W.configs.uneven_batch(64)
     t0 = time.perf_counter()
-    preps = [E.prepare(w, restarts=1, refine=args.refine_path) for w in ws]
+    preps = [E.prepare(w, restarts=1, refine=args.refine_path, method="both" if args.refine_path else "greedy")
+             for w in ws]
     plan_s = time.perf_counter() - t0
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
     # slice batch at most 16: at 64 the largest (28-qubit) circuit alone needs a 164 GB workspace

@@ -434,6 +434,11 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
                 stripped = [frozenset(x - set(sl)) for x in leaves]
                 lim = cap_log2 if cap_log2 is not None else mx0
                 sliced_cands.append((reconfigure(stripped, pairs, lg, keep, cap_log2=lim), list(sl)))
+                if sliced is None and n_sliced:
+                    # or the given number of bonds chosen a few at a time, with
+                    # reconfiguration in between
+                    p2, sl2 = slice_count_and_reconfigure(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced)
+                    sliced_cands.append((p2, sl2))
     best = None
     for pairs, sl in sliced_cands:
         mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
@@ -655,6 +660,23 @@ def reconfigure(leaves: Sequence[FrozenSet[int]], pairs, lg: Sequence[float], ke
             stack.append((b, False))
             stack.append((a, False))
     return out_pairs
+
+
+def slice_count_and_reconfigure(leaves, pairs, lg, keep, n_edges: int, n_sliced: int, group: int = 2,
+                                size: int = 8):
+    """A fixed number of sliced bonds, chosen ``group`` at a time with the
+    network reconfigured in between; no intermediate ever grows past the
+    largest one of the tree so far.  Returns (pairs, sliced)."""
+    mx, _, _ = tree_stats(leaves, pairs, lg, keep)
+    pairs = reconfigure(leaves, pairs, lg, keep, cap_log2=mx, size=size)
+    sl: List[int] = []
+    while len(sl) < n_sliced:
+        stripped = [frozenset(x - set(sl)) for x in leaves]
+        sl += choose_slices(stripped, pairs, lg, keep, n_edges, n_sliced=min(group, n_sliced - len(sl)))
+        stripped = [frozenset(x - set(sl)) for x in leaves]
+        mx, _, _ = tree_stats(leaves, pairs, lg, keep, sl)
+        pairs = reconfigure(stripped, pairs, lg, keep, cap_log2=mx, size=size)
+    return pairs, sl
 
 
 def refine_sliced(leaves, pairs, lg, keep, sliced, cap_log2: Optional[float] = None, rounds: int = 2,
