@@ -188,7 +188,7 @@ def host_cores() -> int:
 def sliced_wires(refine: bool = False):
     from paper_2406_18889_gb300 import engine as E
     w = rank_workload(0)
-    prep = E.prepare(w, refine=refine, method="both" if refine else "greedy")
+    prep = E.prepare(w, refine=refine, method="both" if refine else "greedy", workers=host_cores() if refine else 0)
     return w, prep, [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
 
 
@@ -329,7 +329,8 @@ def run_ours(args):
     from paper_2406_18889_gb300 import engine as E
 
     w = rank_workload(rank)
-    prep = E.prepare(w, refine=args.refine_path, method="both" if args.refine_path else "greedy")
+    prep = E.prepare(w, refine=args.refine_path, method="both" if args.refine_path else "greedy",
+                     workers=host_cores() if args.refine_path else 0)
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
     plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
     S = plan.n_slices_total
@@ -518,8 +519,8 @@ def run_uneven(args):
     torch.cuda.set_device(0)
     ws = W.configs.uneven_batch(64)
     t0 = time.perf_counter()
-    preps = [E.prepare(w, restarts=1, refine=args.refine_path, method="both" if args.refine_path else "greedy")
-             for w in ws]
+    preps = [E.prepare(w, restarts=1, refine=args.refine_path, method="both" if args.refine_path else "greedy",
+                       workers=host_cores() if args.refine_path else 0) for w in ws]
     plan_s = time.perf_counter() - t0
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
     # slice batch at most 16: at 64 the largest (28-qubit) circuit alone needs a 164 GB workspace
@@ -577,7 +578,8 @@ def run_sycamore(args):
     w = W.workload("sycamore53_d20", cycles=20, l=10, G=16)
     tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
     t0 = time.perf_counter()
-    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition", refine=args.refine_path)
+    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition", refine=args.refine_path,
+                       workers=host_cores() if args.refine_path else 0)
     plan_s = time.perf_counter() - t0
     plan = E.Plan(tn, tree, prec=args.prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=1)
     s = len(tree.sliced_edges)

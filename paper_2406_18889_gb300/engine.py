@@ -202,14 +202,16 @@ class Prepared:
 
 
 def prepare(workload, n_sliced: Optional[int] = None, restarts: int = 4, seed: int = 0,
-            sliced_wires: Optional[Sequence] = None, method: str = "greedy", refine: bool = False) -> Prepared:
+            sliced_wires: Optional[Sequence] = None, method: str = "greedy", refine: bool = False,
+            workers: int = 0) -> Prepared:
     """Network + contraction tree of a workload (host planning, once per circuit).
-    ``method`` / ``refine`` select the path search (``pathfind.plan_tree``)."""
+    ``method`` / ``refine`` / ``workers`` select the path search (``pathfind.plan_tree``)."""
     tn = circuit_network(workload.circuit, workload.open_qubits, workload.closed_qubits,
                          workload.closed_bits)
     sliced = None
     if sliced_wires is not None:
         sliced = [tn.edge_of_wire[tuple(w)] for w in sliced_wires]
     s = workload.n_sliced if n_sliced is None else n_sliced
-    tree = plan_tree(tn, n_sliced=s, restarts=restarts, seed=seed, sliced=sliced, method=method, refine=refine)
+    tree = plan_tree(tn, n_sliced=s, restarts=restarts, seed=seed, sliced=sliced, method=method, refine=refine,
+                     workers=workers)
     return Prepared(tn, tree)

@@ -390,9 +390,42 @@ def partition_path(leaves: Sequence[FrozenSet[int]], lg: Sequence[float], keep: 
 PARTITION_IMBALANCES = (0.2, 0.3, 0.4, 0.5)
 
 
+def _candidate_trees(job):
+    """Slicing (and with ``refine`` the refined trees) of one candidate path:
+    a list of (pairs, sliced).  Top level, so that a process pool can run it."""
+    leaves, pairs, lg, keep, n_edges, n_sliced, cap_log2, sliced, refine, groups = job
+    if sliced is None:
+        sl = choose_slices(leaves, pairs, lg, keep, n_edges, n_sliced, cap_log2) \
+            if (n_sliced or cap_log2 is not None) else []
+    else:
+        sl = list(sliced)
+    out = [(pairs, sl)]
+    if not refine:
+        return out
+    if sliced is None and cap_log2 is not None and not n_sliced:
+        for g in groups:
+            try:
+                out.append(slice_and_reconfigure(leaves, pairs, lg, keep, n_edges, cap_log2, group=g))
+            except ValueError:
+                pass
+        return out
+    # a fixed slice set: reconfigure within the cap, or within the tree's own
+    # largest intermediate when there is no cap
+    mx0, _, _ = tree_stats(leaves, pairs, lg, keep, sl)
+    stripped = [frozenset(x - set(sl)) for x in leaves]
+    lim = cap_log2 if cap_log2 is not None else mx0
+    out.append((reconfigure(stripped, pairs, lg, keep, cap_log2=lim), list(sl)))
+    if sliced is None and n_sliced:
+        # or the given number of bonds chosen a few at a time, with
+        # reconfiguration in between
+        out.append(slice_count_and_reconfigure(leaves, pairs, lg, keep, n_edges, n_sliced))
+    return out
+
+
 def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = None,
               restarts: int = 4, seed: int = 0, sliced: Optional[Sequence[int]] = None,
-              method: str = "greedy", refine: bool = False, groups: Sequence[int] = (2, 4)) -> Tree:
+              method: str = "greedy", refine: bool = False, groups: Sequence[int] = (2, 4),
+              workers: int = 0) -> Tree:
     """Search paths -- the greedy alpha/temperature sweep (``restarts`` seeds per
     noisy setting), recursive bisection at several balance windows, or both
     (``method``) -- slice each (unless ``sliced`` is given), keep the cheapest
@@ -400,7 +433,9 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     reconfiguration -- with a cap, slicing interleaved with reconfiguration
     (``slice_and_reconfigure``, each group size in ``groups``); otherwise the
     network without its sliced bonds is reconfigured, its intermediates kept
-    within the cap or, without one, within the unrefined tree's largest."""
+    within the cap or, without one, within the unrefined tree's largest.
+    ``workers`` > 1 slices and refines the candidates in that many processes
+    (started with spawn); the result does not depend on it."""
     if method not in ("greedy", "partition", "both"):
         raise ValueError("method must be greedy, partition or both")
     lg = log2dims(tn)
@@ -414,39 +449,25 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     if method in ("partition", "both"):
         for imb in PARTITION_IMBALANCES:
             candidates.append(partition_path(leaves, lg, keep, imbalance=imb))
-    sliced_cands = []
-    for pairs in candidates:
-        if sliced is None:
-            sl = choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced, cap_log2) \
-                if (n_sliced or cap_log2 is not None) else []
-        else:
-            sl = list(sliced)
-        sliced_cands.append((pairs, sl))
-        if refine:
-            if sliced is None and cap_log2 is not None and not n_sliced:
-                for g in groups:
-                    sliced_cands.append(slice_and_reconfigure(leaves, pairs, lg, keep, len(tn.edge_dim),
-                                                              cap_log2, group=g))
-            else:
-                # a fixed slice set: reconfigure within the cap, or within the
-                # tree's own largest intermediate when there is no cap
-                mx0, _, _ = tree_stats(leaves, pairs, lg, keep, sl)
-                stripped = [frozenset(x - set(sl)) for x in leaves]
-                lim = cap_log2 if cap_log2 is not None else mx0
-                sliced_cands.append((reconfigure(stripped, pairs, lg, keep, cap_log2=lim), list(sl)))
-                if sliced is None and n_sliced:
-                    # or the given number of bonds chosen a few at a time, with
-                    # reconfiguration in between
-                    p2, sl2 = slice_count_and_reconfigure(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced)
-                    sliced_cands.append((p2, sl2))
+    jobs = [(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced, cap_log2,
+             None if sliced is None else list(sliced), refine, tuple(groups)) for pairs in candidates]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=min(workers, len(jobs)),
+                                 mp_context=multiprocessing.get_context("spawn")) as ex:
+            results = list(ex.map(_candidate_trees, jobs))
+    else:
+        results = [_candidate_trees(j) for j in jobs]
     best = None
-    for pairs, sl in sliced_cands:
-        mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
-        if cap_log2 is not None and mx > cap_log2:
-            continue
-        key = (cost * 2.0 ** len(sl), mx)
-        if best is None or key < best[0]:
-            best = (key, pairs, sl, mx, cost, vcost)
+    for trees in results:
+        for pairs, sl in trees:
+            mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
+            if cap_log2 is not None and mx > cap_log2:
+                continue
+            key = (cost * 2.0 ** len(sl), mx)
+            if best is None or key < best[0]:
+                best = (key, pairs, sl, mx, cost, vcost)
     if best is None:
         raise ValueError("no path fits the memory cap")
     _, pairs, sl, mx, cost, vcost = best
