@@ -112,7 +112,21 @@ def test_refined_plan_for_the_24_qubit_workload():
     from paper_2406_18889_gb300 import engine as E
     w = W.workload("grid4x6_d14")
     plain = E.prepare(w, restarts=1).tree
-    refined = E.prepare(w, restarts=1, refine=True).tree
+    prep = E.prepare(w, restarts=1, refine=True)
+    refined = prep.tree
     assert len(refined.sliced_edges) == len(plain.sliced_edges) == 6
     assert refined.cost_per_slice < plain.cost_per_slice
     assert refined.log2_max_intermediate <= plain.log2_max_intermediate
+    # the library plans the refined tree (host-only planning: layouts,
+    # tensor-core roles, memory map), with the planner's cost model
+    from paper_2406_18889_gb300 import build as Bd
+    Bd.build()
+    from paper_2406_18889_gb300 import binding as B
+    rank, edges, data = E.flatten_network(prep.tn)
+    for prec in (0, 2):
+        h = B.tn_plan_create(rank, edges, prep.tn.edge_dim, data, prep.tn.open_edges, prep.tn.block_edge,
+                             np.asarray(prep.tree.pairs, dtype=np.int32).reshape(-1), prep.tree.sliced_edges,
+                             prec, B.TN_FLAG_PLAN_ONLY | B.TN_FLAG_HOIST_INVARIANT, 64, 0, 0)
+        q = B.tn_plan_query(h)
+        B.tn_plan_destroy(h)
+        assert q["useful_flops_per_slice"] == pytest.approx(8 * prep.tree.cost_per_slice, rel=1e-9)
