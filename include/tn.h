@@ -68,14 +68,15 @@ typedef enum {
                                         contraction calls on the plan fail (for inspection) */
 #define TN_FLAG_HILO 0x8u            /* reduced precision: every tensor-core step multiplies
                                         split-precision operands (hi + lo, three passes) */
-#define TN_FLAG_TC_PAIR 0x10u        /* reduced precision: tensor-core steps with 256-column tiles
-                                        run as two-CTA clusters that share each B tile (TMA
-                                        multicast), halving B's reads from L2 (not combined with
-                                        chunked accumulation) */
 #define TN_FLAG_FINE_ACC 0x20u       /* reduced precision: tensor-core steps accumulate K one k tile
                                         (64 real products) at a time, summed in FP32 registers;
                                         with TN_FLAG_HILO the result has complex64 accuracy (without
                                         it, TN_FLAG_HILO accumulates 4 k tiles at a time) */
+#define TN_FLAG_HILO_AUTO 0x40u      /* reduced precision: split-precision (hi + lo) products only on
+                                        the tensor-core steps whose 16-bit rounding moves the
+                                        calibration batch's amplitudes most, until their relative L2
+                                        against a complex64 pass is within hilo_tol (selection at
+                                        tn_plan_create, see tn_plan_precision) */
 
 typedef struct tn_plan_s* tn_plan_t;
 
@@ -130,15 +131,33 @@ typedef struct {
  * prec            : arithmetic of the per-slice contractions (tn_precision).
  * flags           : TN_FLAG_* bits.
  * max_slice_batch : slices contracted together per launch sequence (power of
- *                   two, 1..65536); the workspace scales with it.
+ *                   two, 1..65536); the workspace scales with it.  0 = chosen
+ *                   from memory: the largest power of two, at most the number
+ *                   of slices and 65536, whose device memory (plan memory plus
+ *                   workspace, and the complex64 calibration pass of a
+ *                   reduced-precision plan) fits mem_cap_bytes, or half of the
+ *                   device's free memory at creation when mem_cap_bytes = 0
+ *                   (a TN_FLAG_PLAN_ONLY plan then needs mem_cap_bytes > 0);
+ *                   1 if none fits (then TN_ERR_OOM when the workspace exceeds
+ *                   mem_cap_bytes).  tn_plan_slice_batch reports the choice.
  * mem_cap_bytes   : reject the plan (TN_ERR_OOM) if the workspace exceeds this
  *                   (0 = no cap).
+ * hilo_steps      : NULL, or host [n_steps] of 0/1: 1 asks for a split-precision
+ *                   (hi + lo) product on that step; it takes effect on the
+ *                   tensor-core steps of a reduced-precision plan and is
+ *                   ignored elsewhere.  NULL: TN_FLAG_HILO decides for every
+ *                   step (or TN_FLAG_HILO_AUTO selects them).  Not combined
+ *                   with TN_FLAG_HILO or TN_FLAG_HILO_AUTO.
+ * hilo_tol        : TN_FLAG_HILO_AUTO's target relative L2 (0 < hilo_tol < 1;
+ *                   0 selects 3e-3).
  */
 typedef struct {
   int32_t prec;
   uint32_t flags;
   int32_t max_slice_batch;
   int64_t mem_cap_bytes;
+  const uint8_t* hilo_steps;
+  double hilo_tol;
 } tn_plan_options;
 
 /*
@@ -154,7 +173,8 @@ typedef struct {
  * expanded; with TN_FLAG_HILO both are split into hi + lo 16-bit parts.  Every
  * other tensor, the small steps (CUDA cores, FP32) and the root stay in
  * complex64.  e is fixed at creation by one complex64 calibration batch
- * (slice ids 0..B-1) as the exponent of the tensor's largest component.
+ * (B seeded pseudo-random slice ids, splitmix64) as the exponent of the
+ * tensor's largest component.
  * Creation temporarily needs a complex64 workspace for the calibration.
  * Synchronises `stream`.  *out is set only on success; destroy with
  * tn_plan_destroy.
@@ -163,6 +183,28 @@ tn_status tn_plan_create(const tn_network_desc* net, const tn_tree_desc* tree,
                          const tn_plan_options* opt, void* stream, tn_plan_t* out);
 
 tn_status tn_plan_destroy(tn_plan_t plan);
+
+/* The plan's slice batch (max_slice_batch as given, or as chosen when it was
+ * 0; 1 for a network without sliced edges). */
+tn_status tn_plan_slice_batch(tn_plan_t plan, int32_t* batch);
+
+/*
+ * Precision record of a reduced-precision plan (spec: split-precision
+ * products on the contractions whose error measurably moves the result).
+ * With TN_FLAG_HILO_AUTO, tn_plan_create contracts the calibration slices
+ * (the plan's seeded calibration batch) once in complex64 and, in the plan's
+ * 16-bit precision, with every candidate placement it tries: no split; each
+ * tensor-core step alone left unsplit (all others split) to size each step's
+ * share of the error; then the steps with the largest shares split first
+ * until the relative L2 of the calibration amplitudes is at most hilo_tol.
+ *   rel_l2_chosen : relative L2 of the calibration amplitudes with the chosen
+ *                   placement (-1 when no selection ran);
+ *   rel_l2_none   : the same with no split product (-1 when not measured);
+ *   n_tc_steps    : tensor-core steps; n_hilo_steps: of those, split.
+ * Any output pointer may be NULL.
+ */
+tn_status tn_plan_precision(tn_plan_t plan, double* rel_l2_chosen, double* rel_l2_none, int32_t* n_tc_steps,
+                            int32_t* n_hilo_steps);
 
 /*
  * Cost model of one slice (paper Table I conventions):
@@ -203,7 +245,7 @@ tn_status tn_plan_status(tn_plan_t plan, void* stream);
  * tensor-core step that runs per batch tries each of its launch forms on one
  * batch of the given slices and keeps the fastest.  The forms are: tile width
  * (the widest for the step's N, or half of it), and at width 256 also 256-row
- * tiles and two-CTA pairs (neither with split-precision chunked accumulation).
+ * tiles (not with split-precision chunked accumulation).
  * Each form gets `reps` profiled passes, and the minimum event time per step
  * decides.  Every form computes each output with the same MMAs over K in the
  * same order, so tuning changes speed, not results.  The plan's captured batch
@@ -214,9 +256,9 @@ tn_status tn_plan_status(tn_plan_t plan, void* stream);
  *   amps, workspace, ws_bytes, stream : as for tn_contract_slices (amps is
  *               overwritten with the sum over the slices).
  *   reps      : 1..64 timed passes per form.
- *   forms     : host [3 * n_steps] (n_steps from tn_plan_steps) or NULL: per
- *               step the chosen (tile width, row halves, pair); zeros for
- *               steps that are not tuned.
+ *   forms     : host [2 * n_steps] (n_steps from tn_plan_steps) or NULL: per
+ *               step the chosen (tile width, row halves); zeros for steps
+ *               that are not tuned.
  * Errors: INVALID_ARG before any device work; CUDA_ERROR; TIMEOUT (a bounded
  * device wait gave up).  On an error the plan keeps its previous forms.
  * Synchronises `stream`.
@@ -226,10 +268,10 @@ tn_status tn_plan_autotune(tn_plan_t plan, const int64_t* slice_ids, int64_t n_s
 
 /*
  * Set the launch forms of the tensor-core steps, e.g. those tn_plan_autotune
- * returned, read back from a cache.  forms: host [3 * n_steps] with n_steps
- * the plan's step count; per step (0, 0, 0) selects the default form, anything
+ * returned, read back from a cache.  forms: host [2 * n_steps] with n_steps
+ * the plan's step count; per step (0, 0) selects the default form, anything
  * else must be one of the forms tn_plan_autotune may try for that step; steps
- * that are not tuned take (0, 0, 0).  Validated in full before anything changes
+ * that are not tuned take (0, 0).  Validated in full before anything changes
  * (INVALID_ARG).  Host-only: also valid on a TN_FLAG_PLAN_ONLY plan.
  */
 tn_status tn_plan_set_tuning(tn_plan_t plan, const int32_t* forms, int32_t n_steps);
@@ -243,7 +285,8 @@ tn_status tn_plan_set_tuning(tn_plan_t plan, const int32_t* forms, int32_t n_ste
  * order: within a batch, four contiguous quarters of the batch each summed in
  * slice order, then the quarters in order; batch by batch (deterministic).  workspace: device,
  * >= workspace_bytes of tn_plan_query, 256-byte aligned.  n_slices = 0 with
- * accumulate = 0 zeroes amps.
+ * accumulate = 0 zeroes amps.  The plan's device (current at tn_plan_create)
+ * must be current (TN_ERR_INVALID_ARG otherwise).
  */
 tn_status tn_contract_slices(tn_plan_t plan, const int64_t* slice_ids, int64_t n_slices,
                              void* amps, int accumulate, void* workspace, size_t ws_bytes,
@@ -323,7 +366,9 @@ tn_status tn_contract_slices_profile(tn_plan_t plan, const int64_t* slice_ids, i
  * keeps until the process exits.  A plan whose workspace_bytes
  * (tn_plan_query) exceeds it is rejected with TN_ERR_INVALID_ARG before any
  * work is queued; build such plans with a smaller max_slice_batch or use
- * tn_contract_slices.  The first call on each device looks up the array's
+ * tn_contract_slices.  The plan's device must be the current device (the
+ * array used is that device's); otherwise TN_ERR_INVALID_ARG.  Argument
+ * checks, TN_FAULT injection and batching are those of tn_contract_slices.  The first call on each device looks up the array's
  * device address (which also loads the library's device code on that device)
  * with that device current; make that first call before any stream capture.
  * Kernels are launched directly; no CUDA graph is built.  All calls share the
@@ -340,10 +385,11 @@ tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* slice_ids, i
  * Self-test of the tensor-core GEMM on this device: random complex operands
  * in fp16 (prec = TN_PREC_FP16) or bf16 (TN_PREC_BF16), A [nbt][M][K] and
  * B [nbt][K][N] (complex extents), multiplied by the tcgen05 kernel (after
- * expanding B to its real 2x2 form) in both of its forms -- one CTA per tile,
- * and two-CTA clusters sharing B tiles by TMA multicast -- and by a plain FP32
+ * expanding B to its real 2x2 form) in each of its tile forms -- one
+ * accumulator per tile, K accumulated in chunks, and (tile width 256) 256-row
+ * tiles; results stored n-contiguous and m-contiguous -- and by a plain FP32
  * CUDA-core reference from the same 16-bit inputs.  *max_rel_err = max over
- * both forms of max |C_tc - C_ref| / max |C_ref|.  Allocates and frees its own buffers; synchronises `stream`.
+ * the forms of max |C_tc - C_ref| / max |C_ref|.  Allocates and frees its own buffers; synchronises `stream`.
  * Returns TN_ERR_TIMEOUT if a bounded device wait gave up.
  */
 tn_status tn_selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, int32_t prec, uint64_t seed,

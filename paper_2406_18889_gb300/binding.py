@@ -25,14 +25,14 @@ TN_FLAG_HOIST_INVARIANT = 0x1
 TN_FLAG_NO_GRAPH = 0x2
 TN_FLAG_PLAN_ONLY = 0x4
 TN_FLAG_HILO = 0x8
-TN_FLAG_TC_PAIR = 0x10
 TN_FLAG_FINE_ACC = 0x20
+TN_FLAG_HILO_AUTO = 0x40
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
            "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_plan_status",
            "tn_permute", "tn_selftest_bounded_wait", "tn_selftest_fp32_peak", "tn_plan_autotune",
-           "tn_plan_set_tuning", "tn_last_error", "tn_version")
+           "tn_plan_set_tuning", "tn_plan_slice_batch", "tn_plan_precision", "tn_last_error", "tn_version")
 
 
 class TNError(RuntimeError):
@@ -58,7 +58,8 @@ class TreeDesc(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("max_slice_batch", ctypes.c_int32), ("mem_cap_bytes", ctypes.c_int64)]
+                ("max_slice_batch", ctypes.c_int32), ("mem_cap_bytes", ctypes.c_int64),
+                ("hilo_steps", ctypes.POINTER(ctypes.c_uint8)), ("hilo_tol", ctypes.c_double)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -99,6 +100,9 @@ def load() -> ctypes.CDLL:
     lib.tn_selftest_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     lib.tn_plan_autotune.argtypes = [vp, p_i64, i64, vp, vp, u64, vp, i32, p_i32]
     lib.tn_plan_set_tuning.argtypes = [vp, p_i32, i32]
+    lib.tn_plan_slice_batch.argtypes = [vp, p_i32]
+    p_f64 = ctypes.POINTER(ctypes.c_double)
+    lib.tn_plan_precision.argtypes = [vp, p_f64, p_f64, p_i32, p_i32]
     for name in EXPORTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
     lib.tn_last_error.restype = ctypes.c_char_p
@@ -126,7 +130,8 @@ def _p(arr: np.ndarray, ctype):
 
 def tn_plan_create(leaf_rank, leaf_edges, edge_dim, leaf_data, open_edges, block_edge: int,
                    pairs, sliced_edges, prec: int = TN_PREC_C64, flags: int = 0,
-                   max_slice_batch: int = 1, mem_cap_bytes: int = 0, stream: int = 0) -> int:
+                   max_slice_batch: int = 1, mem_cap_bytes: int = 0, stream: int = 0,
+                   hilo_steps=None, hilo_tol: float = 0.0) -> int:
     rank, edges, dims = _i32(leaf_rank), _i32(leaf_edges), _i64(edge_dim)
     data = np.ascontiguousarray(np.asarray(leaf_data, dtype=np.complex128))
     opens, pr, sl = _i32(open_edges), _i32(pairs).reshape(-1), _i32(sliced_edges)
@@ -134,7 +139,9 @@ def tn_plan_create(leaf_rank, leaf_edges, edge_dim, leaf_data, open_edges, block
                       _p(dims, ctypes.c_int64), data.ctypes.data, len(opens),
                       _p(opens, ctypes.c_int32), int(block_edge))
     tree = TreeDesc(len(pr) // 2, _p(pr, ctypes.c_int32), len(sl), _p(sl, ctypes.c_int32))
-    opt = PlanOptions(int(prec), int(flags), int(max_slice_batch), int(mem_cap_bytes))
+    hl = None if hilo_steps is None else np.ascontiguousarray(np.asarray(hilo_steps, dtype=np.uint8))
+    opt = PlanOptions(int(prec), int(flags), int(max_slice_batch), int(mem_cap_bytes),
+                      None if hl is None else _p(hl, ctypes.c_uint8), float(hilo_tol))
     out = ctypes.c_void_p()
     _check(load().tn_plan_create(ctypes.byref(net), ctypes.byref(tree), ctypes.byref(opt),
                                  ctypes.c_void_p(stream), ctypes.byref(out)))
@@ -143,6 +150,20 @@ def tn_plan_create(leaf_rank, leaf_edges, edge_dim, leaf_data, open_edges, block
 
 def tn_plan_destroy(plan: int) -> None:
     _check(load().tn_plan_destroy(ctypes.c_void_p(plan)))
+
+
+def tn_plan_slice_batch(plan: int) -> int:
+    b = ctypes.c_int32()
+    _check(load().tn_plan_slice_batch(ctypes.c_void_p(plan), ctypes.byref(b)))
+    return b.value
+
+
+def tn_plan_precision(plan: int) -> dict:
+    e1, e0 = ctypes.c_double(), ctypes.c_double()
+    ntc, nhl = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().tn_plan_precision(ctypes.c_void_p(plan), ctypes.byref(e1), ctypes.byref(e0), ctypes.byref(ntc),
+                                    ctypes.byref(nhl)))
+    return dict(rel_l2_chosen=e1.value, rel_l2_none=e0.value, n_tc_steps=ntc.value, n_hilo_steps=nhl.value)
 
 
 def tn_plan_query(plan: int) -> dict:
@@ -166,12 +187,12 @@ def tn_plan_steps(plan: int) -> dict:
 
 def tn_plan_autotune(plan: int, slice_ids, amps_ptr: int, ws_ptr: int, ws_bytes: int, stream: int = 0,
                      reps: int = 3) -> np.ndarray:
-    """Tunes the tensor-core steps' launch forms; returns int32 [n_steps, 3]
-    (tile width, row halves, pair; zeros for steps that are not tuned)."""
+    """Tunes the tensor-core steps' launch forms; returns int32 [n_steps, 2]
+    (tile width, row halves; zeros for steps that are not tuned)."""
     ids = _i64(slice_ids)
     n = ctypes.c_int32()
     _check(load().tn_plan_steps(ctypes.c_void_p(plan), 0, None, None, None, None, None, ctypes.byref(n)))
-    forms = np.zeros((n.value, 3), np.int32)
+    forms = np.zeros((n.value, 2), np.int32)
     _check(load().tn_plan_autotune(ctypes.c_void_p(plan), _p(ids, ctypes.c_int64), len(ids),
                                    ctypes.c_void_p(amps_ptr), ctypes.c_void_p(ws_ptr), int(ws_bytes),
                                    ctypes.c_void_p(stream), int(reps), _p(forms, ctypes.c_int32)))
@@ -179,7 +200,7 @@ def tn_plan_autotune(plan: int, slice_ids, amps_ptr: int, ws_ptr: int, ws_bytes:
 
 
 def tn_plan_set_tuning(plan: int, forms) -> None:
-    f = np.ascontiguousarray(np.asarray(forms, dtype=np.int32).reshape(-1, 3))
+    f = np.ascontiguousarray(np.asarray(forms, dtype=np.int32).reshape(-1, 2))
     _check(load().tn_plan_set_tuning(ctypes.c_void_p(plan), _p(f, ctypes.c_int32), f.shape[0]))
 
 

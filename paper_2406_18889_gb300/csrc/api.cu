@@ -73,10 +73,17 @@ static bool fault_injected(const char* what) {
   return v && strcmp(v, what) == 0;
 }
 
-static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
-                         size_t ws_bytes, cudaStream_t s, std::vector<LaunchRecord>* rec = nullptr) {
+void contract_checked(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
+                      size_t ws_bytes, cudaStream_t s, const BatchRunner& run) {
   TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
   TN_CHECK(!fault_injected("stream"), TN_ERR_CUDA, "injected stream failure (TN_FAULT=stream)");
+  {
+    int dev = -1;
+    TN_CUDA(cudaGetDevice(&dev));
+    TN_CHECK(dev == P.device, TN_ERR_INVALID_ARG,
+             "the plan lives on device " + std::to_string(P.device) + " but device " + std::to_string(dev) +
+                 " is current");
+  }
   TN_CHECK(amps != nullptr, TN_ERR_INVALID_ARG, "amps is null");
   TN_CHECK(n >= 0, TN_ERR_INVALID_ARG, "n_slices < 0");
   TN_CHECK(n == 0 || ids != nullptr, TN_ERR_INVALID_ARG, "slice_ids is null");
@@ -99,9 +106,15 @@ static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int
     int32_t nv = (int32_t)std::min<int64_t>(P.B, n - start);
     for (int b = 0; b < P.B; ++b) chunk[b] = ids[start + (b < nv ? b : 0)];
     launch_set_slice_ids(P.d_slice_ids, P.d_n_valid, chunk.data(), P.B, nv, s);
-    run_batch(P, ws, amps, start == 0 ? accumulate : 1, s, rec);
+    run(P, ws, amps, start == 0 ? accumulate : 1, s);
   }
   TN_CUDA(cudaGetLastError());
+}
+
+static void contract_one(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
+                         size_t ws_bytes, cudaStream_t s, std::vector<LaunchRecord>* rec = nullptr) {
+  contract_checked(P, ids, n, amps, accumulate, ws, ws_bytes, s,
+                   [rec](Plan& Q, void* w, void* a, int acc, cudaStream_t st) { run_batch(Q, w, a, acc, st, rec); });
 }
 
 }  // namespace tn
@@ -116,7 +129,7 @@ tn_status tn_plan_create(const tn_network_desc* net, const tn_tree_desc* tree, c
     TN_CHECK(out != nullptr, TN_ERR_INVALID_ARG, "out is null");
     TN_CHECK(!fault_injected("alloc"), TN_ERR_OOM, "injected allocation failure (TN_FAULT=alloc)");
     TN_CHECK(!fault_injected("invalid_plan"), TN_ERR_INVALID_ARG, "injected invalid plan (TN_FAULT=invalid_plan)");
-    auto p = build_plan(net, tree, opt, (cudaStream_t)stream);
+    auto p = create_plan(net, tree, opt, (cudaStream_t)stream);
     auto* h = new tn_plan_s{std::move(p)};
     *out = h;
   });
@@ -126,6 +139,30 @@ tn_status tn_plan_destroy(tn_plan_t plan) {
   return guarded([&] {
     TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
     delete plan;
+  });
+}
+
+tn_status tn_plan_slice_batch(tn_plan_t plan, int32_t* batch) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr && batch != nullptr, TN_ERR_INVALID_ARG, "null pointer");
+    *batch = plan->p->B;
+  });
+}
+
+tn_status tn_plan_precision(tn_plan_t plan, double* rel_l2_chosen, double* rel_l2_none, int32_t* n_tc_steps,
+                            int32_t* n_hilo_steps) {
+  return guarded([&] {
+    TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
+    const Plan& P = *plan->p;
+    int32_t tc = 0, hl = 0;
+    for (const Step& S : P.steps) {
+      tc += S.tc ? 1 : 0;
+      hl += (S.tc && S.hilo) ? 1 : 0;
+    }
+    if (rel_l2_chosen) *rel_l2_chosen = P.calib_err_chosen;
+    if (rel_l2_none) *rel_l2_none = P.calib_err_none;
+    if (n_tc_steps) *n_tc_steps = tc;
+    if (n_hilo_steps) *n_hilo_steps = hl;
   });
 }
 
@@ -181,7 +218,7 @@ tn_status tn_plan_autotune(tn_plan_t plan, const int64_t* slice_ids, int64_t n_s
     TN_CHECK(n_slices >= 1 && n_slices <= P.B, TN_ERR_INVALID_ARG, "n_slices must be 1 .. the slice batch");
     TN_CHECK(reps >= 1 && reps <= 64, TN_ERR_INVALID_ARG, "reps must be 1 .. 64");
     const size_t T = P.steps.size();
-    for (size_t t = 0; t < T; ++t) saved.push_back({P.steps[t].tc_bn, P.steps[t].tc_mh, P.steps[t].tc_c2});
+    for (size_t t = 0; t < T; ++t) saved.push_back({P.steps[t].tc_bn, P.steps[t].tc_mh});
     // the tuned steps in launch order (the order of their profiling records)
     std::vector<size_t> tuned;
     std::vector<std::vector<TcForm>> cand;
@@ -202,7 +239,6 @@ tn_status tn_plan_autotune(tn_plan_t plan, const int64_t* slice_ids, int64_t n_s
         Step& S = P.steps[tuned[i]];
         S.tc_bn = f.bn;
         S.tc_mh = f.mh;
-        S.tc_c2 = f.c2;
       }
       for (int r = 0; r < reps; ++r) {
         contract_one(P, slice_ids, n_slices, amps, 0, workspace, ws_bytes, s, &rec);
@@ -230,14 +266,12 @@ tn_status tn_plan_autotune(tn_plan_t plan, const int64_t* slice_ids, int64_t n_s
       Step& S = P.steps[tuned[i]];
       S.tc_bn = pick[i].bn;
       S.tc_mh = pick[i].mh;
-      S.tc_c2 = pick[i].c2;
     }
     drop_graph(P);
     if (forms) {
       for (size_t t = 0; t < T; ++t) {
-        forms[3 * t] = P.steps[t].tc_bn;
-        forms[3 * t + 1] = P.steps[t].tc_mh;
-        forms[3 * t + 2] = P.steps[t].tc_c2;
+        forms[2 * t] = P.steps[t].tc_bn;
+        forms[2 * t + 1] = P.steps[t].tc_mh;
       }
     }
   });
@@ -247,7 +281,6 @@ tn_status tn_plan_autotune(tn_plan_t plan, const int64_t* slice_ids, int64_t n_s
     for (size_t t = 0; t < saved.size(); ++t) {
       Pp->steps[t].tc_bn = saved[t].bn;
       Pp->steps[t].tc_mh = saved[t].mh;
-      Pp->steps[t].tc_c2 = saved[t].c2;
     }
     drop_graph(*Pp);
   }
@@ -261,17 +294,16 @@ tn_status tn_plan_set_tuning(tn_plan_t plan, const int32_t* forms, int32_t n_ste
     TN_CHECK(forms != nullptr, TN_ERR_INVALID_ARG, "forms is null");
     TN_CHECK(n_steps == (int32_t)P.steps.size(), TN_ERR_INVALID_ARG, "n_steps differs from the plan's step count");
     for (int32_t t = 0; t < n_steps; ++t) {
-      const int32_t bn = forms[3 * t], mh = forms[3 * t + 1], c2 = forms[3 * t + 2];
-      if (bn == 0 && mh == 0 && c2 == 0) continue;
+      const int32_t bn = forms[2 * t], mh = forms[2 * t + 1];
+      if (bn == 0 && mh == 0) continue;
       bool ok = false;
-      for (const TcForm& f : tc_step_forms(P, (size_t)t)) ok = ok || (f.bn == bn && f.mh == mh && f.c2 == c2);
+      for (const TcForm& f : tc_step_forms(P, (size_t)t)) ok = ok || (f.bn == bn && f.mh == mh);
       TN_CHECK(ok, TN_ERR_INVALID_ARG, "step " + std::to_string(t) + ": not a launch form of this step");
     }
     for (int32_t t = 0; t < n_steps; ++t) {
       Step& S = P.steps[t];
-      S.tc_bn = forms[3 * t];
-      S.tc_mh = forms[3 * t + 1];
-      S.tc_c2 = forms[3 * t + 2];
+      S.tc_bn = forms[2 * t];
+      S.tc_mh = forms[2 * t + 1];
     }
     drop_graph(P);
   });

@@ -80,13 +80,9 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
   TN_CHECK(p.out_kind == 2 || (p.out_kind == (bf16 ? 1 : 0) && (p.out_hilo != 0) == hilo), TN_ERR_UNSUPPORTED,
            "tensor-core output storage must match the operand precision");
   const int bn = p.bn;
-  TN_CHECK(!p.cluster2 || p.out_kind == 2 || bn == 256, TN_ERR_UNSUPPORTED,
-           "two-CTA tensor-core form: 16-bit output needs tile width 256");
-  TN_CHECK(p.acc_split >= 0 && !(p.cluster2 && p.acc_split), TN_ERR_UNSUPPORTED,
-           "chunked accumulation runs on single CTAs");
-  TN_CHECK(p.m_halves == 0 || p.m_halves == 1 ||
-               (p.m_halves == 2 && bn == 256 && !p.cluster2 && !p.acc_split),
-           TN_ERR_UNSUPPORTED, "256-row tiles: tile width 256, single CTAs, one accumulator per tile");
+  TN_CHECK(p.acc_split >= 0, TN_ERR_UNSUPPORTED, "negative accumulation chunk");
+  TN_CHECK(p.m_halves == 0 || p.m_halves == 1 || (p.m_halves == 2 && bn == 256 && !p.acc_split),
+           TN_ERR_UNSUPPORTED, "256-row tiles: tile width 256, one accumulator per tile");
   {
     // stage the epilogue when n is the output's more contiguous index
     const int64_t big = int64_t(1) << 62;
@@ -107,7 +103,7 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
   CUtensorMap ma, ma2, mb, mb2;
   const uint64_t a_row = (uint64_t)sa_m * 4, a_bt = p.nbt > 1 ? (uint64_t)sa_bt * 4 : a_row * (uint64_t)p.M;
   make_map(&ma, A, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row, (a_bt + 15) / 16 * 16, BM);
-  const uint32_t b_box = (uint32_t)(p.cluster2 ? bn / 2 : bn);
+  const uint32_t b_box = (uint32_t)bn;
   make_map(&mb, Bx, bf16, pitch, (uint64_t)(2 * p.N), (uint64_t)p.nbt, pitch * 2, pitch * 2 * 2 * p.N, b_box);
   if (hilo) {
     make_map(&ma2, A_lo, bf16, (uint64_t)(2 * p.K), (uint64_t)p.M, (uint64_t)p.nbt, a_row, (a_bt + 15) / 16 * 16,
@@ -350,9 +346,7 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
     p.scale = 1.0f;
     p.err = d_err;
     p.bn = tc_gemm_bn(N);
-    // both variants: one CTA per tile, and two-CTA clusters sharing B by multicast;
-    // the second overwrites the first, then is compared; the first is compared below
-    p.cluster2 = 0;
+    // one CTA per tile, K in one accumulator
     launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
     if (bf16)
       ref_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>((const __nv_bfloat162*)A, (const __nv_bfloat162*)B,
@@ -360,13 +354,8 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
     else
       ref_kernel<__half2><<<1024, 256, 0, s>>>((const __half2*)A, (const __half2*)B, (float2*)R, nbt, M, N, K);
     diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
+    // and K accumulated in chunks summed in FP32 registers
     TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
-    p.cluster2 = 1;
-    launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
-    diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
-    // and single CTAs accumulating K in chunks summed in FP32 registers
-    TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
-    p.cluster2 = 0;
     p.acc_split = 2;
     launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
     diff_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt * M * N, mx, mx + 1);
@@ -382,12 +371,11 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
     // layout) under each tile form
     p.c_m = single_run(M, 1);
     p.c_n = single_run(N, M);
-    for (int v = 0; v < 3; ++v) {
-      if (v == 2 && p.bn != 256) break;
+    for (int v = 0; v < 2; ++v) {
+      if (v == 1 && p.bn != 256) break;
       TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
-      p.cluster2 = v == 1;
       p.acc_split = 0;
-      p.m_halves = v == 2 ? 2 : 1;
+      p.m_halves = v == 1 ? 2 : 1;
       launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
       diff_t_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt, M, N, mx);
     }

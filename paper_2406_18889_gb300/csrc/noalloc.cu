@@ -48,7 +48,6 @@ void* static_workspace() {
 
 }  // namespace
 
-void run_batch_direct(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream);
 tn_status guarded_call(const std::function<void()>& f);
 
 }  // namespace tn
@@ -60,30 +59,23 @@ extern "C" tn_status tn_contract_slices_noalloc(tn_plan_t plan, const int64_t* s
     TN_CHECK(plan != nullptr, TN_ERR_INVALID_ARG, "plan is null");
     Plan& P = *plan->p;
     TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
-    TN_CHECK(amps != nullptr, TN_ERR_INVALID_ARG, "amps is null");
-    TN_CHECK(n_slices >= 0 && (n_slices == 0 || slice_ids), TN_ERR_INVALID_ARG, "bad slice list");
-    TN_CHECK(accumulate == 0 || accumulate == 1, TN_ERR_INVALID_ARG, "accumulate must be 0 or 1");
+    // the static array of the plan's device: that device must be current
+    int dev = -1;
+    TN_CUDA(cudaGetDevice(&dev));
+    TN_CHECK(dev == P.device, TN_ERR_INVALID_ARG,
+             "the plan lives on device " + std::to_string(P.device) + " but device " + std::to_string(dev) +
+                 " is current");
     TN_CHECK(P.mem.ws_bytes <= (int64_t)TN_STATIC_WORKSPACE_BYTES, TN_ERR_INVALID_ARG,
              "plan needs " + std::to_string(P.mem.ws_bytes) + " bytes of workspace; the static workspace holds " +
                  std::to_string((long long)TN_STATIC_WORKSPACE_BYTES) +
                  " (use tn_contract_slices or a smaller max_slice_batch)");
-    const int64_t S = int64_t(1) << P.sliced.size();
-    for (int64_t i = 0; i < n_slices; ++i)
-      TN_CHECK(slice_ids[i] >= 0 && slice_ids[i] < S, TN_ERR_INVALID_ARG, "slice id out of range");
-    cudaStream_t s = (cudaStream_t)stream;
     void* ws = static_workspace();
-    if (n_slices == 0) {
-      if (!accumulate) TN_CUDA(cudaMemsetAsync(amps, 0, (size_t)(P.G * P.J * 16), s));
-      return;
-    }
-    std::vector<int64_t> chunk(P.B);
-    for (int64_t start = 0; start < n_slices; start += P.B) {
-      int32_t nv = (int32_t)std::min<int64_t>(P.B, n_slices - start);
-      for (int b = 0; b < P.B; ++b) chunk[b] = slice_ids[start + (b < nv ? b : 0)];
-      // pageable host -> device: the runtime stages the source before returning
-      launch_set_slice_ids(P.d_slice_ids, P.d_n_valid, chunk.data(), P.B, nv, s);
-      run_batch_direct(P, ws, amps, start == 0 ? accumulate : 1, s);
-    }
-    TN_CUDA(cudaGetLastError());
+    // the same argument checks, fault injection and batching as tn_contract_slices;
+    // each batch's ids reach the device as kernel arguments (no staging copy),
+    // and the batch is launched directly (no graph is instantiated)
+    contract_checked(P, slice_ids, n_slices, amps, accumulate, ws, (size_t)TN_STATIC_WORKSPACE_BYTES,
+                     (cudaStream_t)stream, [](Plan& Q, void* w, void* a, int acc, cudaStream_t st) {
+                       run_batch_direct(Q, w, a, acc, st);
+                     });
   });
 }

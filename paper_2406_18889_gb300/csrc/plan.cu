@@ -338,37 +338,32 @@ TcRoles tc_roles(const Step& S, bool* ok_out = nullptr) {
 // accumulation error grows with K): 4 k tiles, or 1 with TN_FLAG_FINE_ACC;
 // single CTAs then
 int tc_acc_split(const Plan& P, const Step& S) { return (P.flags & TN_FLAG_FINE_ACC) ? 1 : S.hilo ? 4 : 0; }
-// The default launch form: the widest tile for N; two-CTA pairs with
-// TN_FLAG_TC_PAIR; 256-row tiles for K-heavy steps (they load each B tile once
-// for two 128-row MMAs, and the expanded B dominates the bytes a tile brings
-// into shared memory).
+// The default launch form: the widest tile for N; 256-row tiles for K-heavy
+// steps (they load each B tile once for two 128-row MMAs, and the expanded B
+// dominates the bytes a tile brings into shared memory).
 TcForm tc_default_form(const Plan& P, const Step& S, const TcRoles& r) {
-  TcForm f{tc_gemm_bn(r.N), 1, 0};
+  TcForm f{tc_gemm_bn(r.N), 1};
   const bool acc = tc_acc_split(P, S) != 0;
-  f.c2 = !acc && (P.flags & TN_FLAG_TC_PAIR) && f.bn == 256 ? 1 : 0;
-  f.mh = (!acc && !f.c2 && f.bn == 256 && r.M >= 256 && r.K >= 256) ? 2 : 1;
+  f.mh = (!acc && f.bn == 256 && r.M >= 256 && r.K >= 256) ? 2 : 1;
   return f;
 }
 // Every form the tuner may try (the default first): the widest tile for N or
-// half of it; at width 256 also 256-row tiles (M >= 256) and two-CTA pairs,
-// neither with chunked accumulation -- the forms the launcher accepts.
+// half of it; at width 256 also 256-row tiles (M >= 256, not with chunked
+// accumulation) -- the forms the launcher accepts.
 std::vector<TcForm> tc_forms(const Plan& P, const Step& S) {
   const TcRoles r = tc_roles(S);
   std::vector<TcForm> out{tc_default_form(P, S, r)};
   auto add = [&](TcForm f) {
     for (const TcForm& g : out)
-      if (g.bn == f.bn && g.mh == f.mh && g.c2 == f.c2) return;
+      if (g.bn == f.bn && g.mh == f.mh) return;
     out.push_back(f);
   };
   const bool acc = tc_acc_split(P, S) != 0;
   const int bn0 = tc_gemm_bn(r.N);
   for (int bn : {bn0, bn0 / 2}) {
     if (bn < 32) continue;
-    add({bn, 1, 0});
-    if (bn == 256 && !acc) {
-      if (r.M >= 256) add({bn, 2, 0});
-      add({bn, 1, 1});
-    }
+    add({bn, 1});
+    if (bn == 256 && !acc && r.M >= 256) add({bn, 2});
   }
   return out;
 }
@@ -574,10 +569,9 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     tp.scale = scale;
     tp.err = P.d_err;
     tp.acc_split = tc_acc_split(P, S);
-    const TcForm f = S.tc_bn ? TcForm{S.tc_bn, S.tc_mh, S.tc_c2} : tc_default_form(P, S, r);
+    const TcForm f = S.tc_bn ? TcForm{S.tc_bn, S.tc_mh} : tc_default_form(P, S, r);
     tp.bn = f.bn;
     tp.m_halves = f.mh;
-    tp.cluster2 = f.c2;
     const char* a_hi = X.base(r.a_node);
     R.begin(5, flops, bytes);
     launch_gemm_tc(a_hi, S.hilo ? a_hi + NA.elems * 4 : nullptr, r.a_bt, r.a_m, bx, bx_lo, tp,
@@ -660,8 +654,26 @@ void enqueue_batch_mem(const Plan& P, const MemPlan& M, char* pb, void* ws, void
 }  // namespace
 
 // ---------------------------------------------------------------- build
+std::vector<int64_t> calibration_ids(int B, int n_sliced) {
+  // seeded pseudo-random ids (splitmix64) spread over all sliced edges, so no
+  // sliced edge is pinned to one value across the sample
+  std::vector<int64_t> ids(B);
+  const uint64_t mask = n_sliced >= 63 ? ~0ull : (uint64_t(1) << n_sliced) - 1;
+  uint64_t z = 0x2406188890ull;
+  for (int b = 0; b < B; ++b) {
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    ids[b] = (int64_t)(x & mask);
+  }
+  return ids;
+}
+
 std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc* tree,
-                                 const tn_plan_options* opt, cudaStream_t stream) {
+                                 const tn_plan_options* opt, cudaStream_t stream,
+                                 const std::vector<char>* hilo_mask) {
   auto Pp = std::make_unique<Plan>();
   Plan& P = *Pp;
   TN_CHECK(net && tree && opt, TN_ERR_INVALID_ARG, "null descriptor");
@@ -857,7 +869,8 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       if (big && !ok && want != larger) ok = valid(larger);
       if (ok) {
         S.tc = true;
-        S.hilo = (P.flags & TN_FLAG_HILO) != 0;
+        const size_t t = &S - P.steps.data();
+        S.hilo = hilo_mask ? (t < hilo_mask->size() && (*hilo_mask)[t] != 0) : (P.flags & TN_FLAG_HILO) != 0;
       } else {
         S.tc_swap = larger;
       }
@@ -933,6 +946,10 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     P.peak_intermediate_bytes = std::max(P.peak_intermediate_bytes, per(S.c));
   }
   P.mem = plan_memory(P, P.skind == KIND_C64, leaf_src_layout, true);
+  if (P.skind != KIND_C64) {
+    const MemPlan Mc = plan_memory(P, true, leaf_src_layout, false);
+    P.calib_bytes = Mc.plan_bytes + Mc.ws_bytes + total_leaf_elems * 16;
+  }
   if (opt->mem_cap_bytes > 0)
     TN_CHECK(P.mem.ws_bytes <= opt->mem_cap_bytes, TN_ERR_OOM, "workspace exceeds mem_cap_bytes");
   {
@@ -945,24 +962,14 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
   if (P.flags & TN_FLAG_PLAN_ONLY) return Pp;
 
   // ------------------------------------------------------------ device setup
+  TN_CUDA(cudaGetDevice(&P.device));
   TN_CUDA(cudaMalloc(&P.d_slice_ids, sizeof(int64_t) * P.B));
   TN_CUDA(cudaMalloc(&P.d_n_valid, sizeof(int32_t)));
   TN_CUDA(cudaMalloc(&P.d_err, sizeof(int)));
   TN_CUDA(cudaMemsetAsync(P.d_err, 0, sizeof(int), stream));
   {
-    // calibration slices: seeded pseudo-random ids (splitmix64) spread over all sliced
-    // edges, so no sliced edge is pinned to one value across the sample
-    std::vector<int64_t> ids(P.B);
-    const int64_t S = int64_t(1) << P.sliced.size();
-    uint64_t z = 0x2406188890ull;
-    for (int b = 0; b < P.B; ++b) {
-      z += 0x9E3779B97F4A7C15ull;
-      uint64_t x = z;
-      x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-      x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-      x ^= x >> 31;
-      ids[b] = (int64_t)(x & (uint64_t)(S - 1));
-    }
+    // calibration slices
+    std::vector<int64_t> ids = calibration_ids(P.B, (int)P.sliced.size());
     int32_t nv = P.B;
     TN_CUDA(cudaMemcpyAsync(P.d_slice_ids, ids.data(), sizeof(int64_t) * P.B, cudaMemcpyHostToDevice, stream));
     TN_CUDA(cudaMemcpyAsync(P.d_n_valid, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, stream));
@@ -1012,7 +1019,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
   };
 
   if (P.skind != KIND_C64) {
-    // calibration: one complex64 batch (slice ids 0..B-1) records every tensor's
+    // calibration: one complex64 batch (the seeded slice ids above) records every tensor's
     // largest component; exponents make the stored maxima lie in [1/2, 1)
     MemPlan Mc = plan_memory(P, true, leaf_src_layout, false);
     char *cplan = nullptr, *cws = nullptr;

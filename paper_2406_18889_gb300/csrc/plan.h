@@ -2,6 +2,7 @@
 // memory layout, the workspace map and the per-step kernel parameters.
 #pragma once
 
+#include <functional>
 #include <map>
 #include <memory>
 #include <vector>
@@ -27,9 +28,9 @@ struct Node {
 };
 
 // Launch form of a tensor-core step: tile width in real columns, 128-row
-// halves per tile, two-CTA pair.
+// halves per tile.
 struct TcForm {
-  int bn, mh, c2;
+  int bn, mh;
 };
 
 struct Step {
@@ -48,7 +49,7 @@ struct Step {
   bool fuse_expand = false;            // writes its result as the consumer's expanded operand
   bool b_fused = false;                // tensor-core step whose expanded operand its producer wrote
   bool micro = false;                  // small per-batch step run inside the fused small-step launch
-  int tc_bn = 0, tc_mh = 0, tc_c2 = 0;  // tuned tensor-core launch form (tc_bn 0: the default heuristics)
+  int tc_bn = 0, tc_mh = 0;            // tuned tensor-core launch form (tc_bn 0: the default heuristics)
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network
 };
@@ -69,6 +70,7 @@ struct MemPlan {
 };
 
 struct Plan {
+  int device = -1;                      // CUDA device the plan lives on (-1: plan-only)
   // network
   int n_leaves = 0, n_edges = 0;
   std::vector<int64_t> dim;             // edge dims; index n_edges is the slice-batch edge
@@ -104,6 +106,9 @@ struct Plan {
   int64_t root_sb = 0, root_sg = 0, root_sj = 1;
   // statistics
   double useful_flops_per_slice = 0, algo_bytes_per_slice = 0, peak_intermediate_bytes = 0;
+  int64_t calib_bytes = 0;              // device memory of the complex64 calibration pass (reduced precision)
+  // split-precision selection (TN_FLAG_HILO_AUTO): calibration relative L2 errors, -1 = not measured
+  double calib_err_chosen = -1, calib_err_none = -1;
   // CUDA graph cache
   cudaGraphExec_t graph = nullptr;
   void* graph_ws = nullptr;
@@ -114,8 +119,17 @@ struct Plan {
   ~Plan();
 };
 
+// One plan for the given options; hilo_mask (per step, 1 = split product on a
+// tensor-core step) overrides TN_FLAG_HILO when given.  max_slice_batch >= 1.
 std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc* tree,
-                                 const tn_plan_options* opt, cudaStream_t stream);
+                                 const tn_plan_options* opt, cudaStream_t stream,
+                                 const std::vector<char>* hilo_mask = nullptr);
+// tn_plan_create: resolves max_slice_batch = 0 (from memory), hilo_steps and
+// TN_FLAG_HILO_AUTO (calibrated placement of split products), then builds.
+std::unique_ptr<Plan> create_plan(const tn_network_desc* net, const tn_tree_desc* tree,
+                                  const tn_plan_options* opt, cudaStream_t stream);
+// The seeded calibration slice ids of a plan with batch B over n_sliced edges.
+std::vector<int64_t> calibration_ids(int B, int n_sliced);
 
 // Per-launch profiling record (tn_contract_slices_profile).
 struct LaunchRecord {
@@ -134,5 +148,14 @@ void drop_graph(Plan& P);
 // With `rec`, launches directly and brackets every kernel with an event pair.
 void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream,
                std::vector<LaunchRecord>* rec = nullptr);
+// The same with direct launches only (no graph is built or replayed).
+void run_batch_direct(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t stream);
+
+// How one batch is queued once its slice ids are on the device.
+using BatchRunner = std::function<void(Plan&, void* ws, void* amps, int accumulate, cudaStream_t)>;
+// Validate a contraction call (before any device work), then queue its
+// batches: slice-id upload + run(...) per batch of up to P.B slices.
+void contract_checked(Plan& P, const int64_t* ids, int64_t n, void* amps, int accumulate, void* ws,
+                      size_t ws_bytes, cudaStream_t s, const BatchRunner& run);
 
 }  // namespace tn

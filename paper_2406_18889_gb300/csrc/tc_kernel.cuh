@@ -99,26 +99,6 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* ba
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
-// the same load delivered to every CTA of the cluster in `mask` (same smem
-// offset, each CTA's own mbarrier at the same offset)
-__device__ __forceinline__ void tma_load_3d_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (SBO), descriptor version 1 (tcgen05)
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -290,20 +270,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // then m tile, then batch).  The TMEM accumulator is double-buffered (2 x BN
 // columns): the MMA thread fills buffer (i & 1) for the CTA's i-th tile while
 // the epilogue drains the other; tfull/tempty hand the buffers back and forth.
-// C2: a cluster of two CTAs takes two adjacent m tiles of one n tile; each CTA
-// loads its own A tile and one half of the shared B tile, multicast to both,
-// so every SM reads a third less from L2 per k step.  A stage is refilled only
-// after both CTAs' MMAs released it (their commits arrive on both CTAs'
-// `empty` barriers).
 // MH: m halves per tile.  MH = 2 gives a CTA 256 rows (two 128-row MMAs per k
 // step sharing one B tile, so B is loaded once per 256 rows) and one TMEM
 // accumulator of 2 x BN columns instead of two alternating ones.
-template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT, int MH = 1>
+template <int BN, bool BF16, bool HILO, bool STAGE, bool F32OUT, bool SPLIT, int MH = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2,
                    TcGemmParams p) {
-  static_assert(MH == 1 || (MH == 2 && !STAGE && !C2 && !SPLIT), "two m halves: direct stores, single CTAs");
+  static_assert(MH == 1 || (MH == 2 && !STAGE && !SPLIT), "two m halves: direct stores");
   constexpr int S = stages_for<BN, STAGE, MH>();
   constexpr int TBM = MH * BM;             // rows per tile
   constexpr int NBUF = MH == 1 ? 2 : 1;    // TMEM accumulator buffers (TMEM holds 2 x BN columns)
@@ -325,23 +300,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int k_tiles1 = (int)((2 * p.K + BK - 1) / BK);
   const int k_tiles = HILO ? 3 * k_tiles1 : k_tiles1;
   const int64_t n_n = (2 * p.N + BN - 1) / BN, n_m = (p.M + TBM - 1) / TBM;
-  // work units: single tiles, or (C2) pairs of m tiles sharing an n tile
-  const int64_t n_mu = C2 ? (n_m + 1) / 2 : n_m;
+  const int64_t n_mu = n_m;
   const int64_t tiles = p.nbt * n_mu * n_n;
-  const int rank = C2 ? (int)cluster_rank() : 0;
-  const int64_t unit0 = C2 ? blockIdx.x / 2 : blockIdx.x;
-  const int64_t ustride = C2 ? gridDim.x / 2 : gridDim.x;
+  const int64_t unit0 = blockIdx.x;
+  const int64_t ustride = gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], C2 ? 2 : 1);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps);  // one arrival per epilogue warp
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
@@ -352,7 +324,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (C2) cluster_sync_all();  // the peer's barriers are initialised before any multicast
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -363,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       TileWalk<true> w(unit0, ustride, n_n, n_mu);
       for (int64_t t = unit0; t < tiles && !stop; t += ustride, w.next()) {
         const int n_tile = w.n, bt = w.b;
-        const int m_tile = w.m * (C2 ? 2 : 1) + rank;
+        const int m_tile = w.m;
         for (int kt = 0; kt < k_tiles; ++kt, ++g) {
           const int s = (int)(g % S);
           const uint32_t use = (uint32_t)(g / S);
@@ -378,11 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int h = 0; h < MH; ++h)
             tma_load_3d(pass == 2 ? &tmA2 : &tmA, &full[s], sA + (s * TBM + h * BM) * BK * 2, kx,
                         m_tile * TBM + h * BM, bt);
-          if (C2)
-            tma_load_3d_mc(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2 + rank * (BN / 2) * BK * 2, kx,
-                           n_tile * BN + rank * (BN / 2), bt, (uint16_t)0x3);
-          else
-            tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
+          tma_load_3d(pass == 1 ? &tmB2 : &tmB, &full[s], sB + s * BN * BK * 2, kx, n_tile * BN, bt);
         }
       }
       // drain: every issued load must have landed before the CTA can exit
@@ -502,16 +469,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                   : "memory");
             }
           }
-          if (C2)
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                    smem_u32(&empty[s])),
-                "h"((uint16_t)0x3)
-                : "memory");
-          else
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&empty[s]))
-                         : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty[s]))
+                       : "memory");
         }
         // tfull[b] completes when this unit's MMAs (and all earlier ones) finish
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -569,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t t = unit0; t < tiles; t += ustride, ++local, w.next()) {
       int n_tile, m_unit, bt;
       w.at(t, n_tile, m_unit, bt);
-      const int m_tile = m_unit * (C2 ? 2 : 1) + rank;
+      const int m_tile = m_unit;
       const int b = (int)(local & 1);
       const uint32_t u = (uint32_t)(local >> 1);
       const int64_t nbase = (int64_t)n_tile * BN / 2, mbase = (int64_t)m_tile * TBM;
@@ -590,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       char* const Ctm = Ct + (size_t)m32 * ES;
       char* const C2tm = HILO ? C2t + (size_t)m32 * 4 : nullptr;
       const bool row_ok = mbase + quarter * 32 + lane < p.M;
-      // the tile lies wholly inside M x N (a cluster's second tile may lie past M)
+      // the tile lies wholly inside M x N
       const bool whole = mbase + TBM <= p.M && nbase + BN / 2 <= p.N;
       if constexpr (MH == 2) {
         // one accumulator (unit = tile); rows h * 128 + quarter * 32 + lane of the tile
@@ -794,7 +754,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (C2) cluster_sync_all();  // no CTA leaves while its peer may still multicast into it
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
@@ -802,11 +761,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int BN, bool BF16, bool HILO, bool STAGE, bool C2, bool F32OUT, bool SPLIT = false, int MH = 1>
+template <int BN, bool BF16, bool HILO, bool STAGE, bool F32OUT, bool SPLIT = false, int MH = 1>
 void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
   const size_t sm = smem_bytes<BN, STAGE, MH>();
-  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, C2, F32OUT, SPLIT, MH>;
+  auto kern = tc_gemm_kernel<BN, BF16, HILO, STAGE, F32OUT, SPLIT, MH>;
   // the shared-memory opt-in is a per-device property of the function
   static std::atomic<uint64_t> attr_set{0};
   int dev = 0;
@@ -817,64 +776,36 @@ void launch_tc6(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap
     attr_set.fetch_or(bit);
   }
   const int64_t n_m = (p.M + MH * BM - 1) / (MH * BM), n_n = (2 * p.N + BN - 1) / BN;
-  if (!C2) {
-    const unsigned grid = (unsigned)std::min<int64_t>(n_m * n_n * p.nbt, 152);
-    kern<<<grid, kThreads, sm, s>>>(ma, ma2, mb, mb2, p);
-    return;
-  }
-  const int64_t pairs = ((n_m + 1) / 2) * n_n * p.nbt;
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(pairs, 76)));
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  TN_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, ma2, mb, mb2, p));
+  const unsigned grid = (unsigned)std::min<int64_t>(n_m * n_n * p.nbt, 152);
+  kern<<<grid, kThreads, sm, s>>>(ma, ma2, mb, mb2, p);
 }
-// the two-CTA cluster form: fp32 outputs at every width, 16-bit outputs at width 256
 template <int BN, bool BF16, bool HILO, bool STAGE>
 void launch_tc4(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
-  if (p.cluster2) {
-    if (p.out_kind == 2) {
-      launch_tc6<BN, BF16, HILO, STAGE, true, true>(ma, ma2, mb, mb2, p, s);
-      return;
-    }
-    if constexpr (BN == 256) {
-      launch_tc6<BN, BF16, HILO, STAGE, true, false>(ma, ma2, mb, mb2, p, s);
-      return;
-    }
-    fail(TN_ERR_UNSUPPORTED, "two-CTA tensor-core form: 16-bit output needs tile width 256");
-  } else if (p.out_kind == 2)
-    launch_tc6<BN, BF16, HILO, STAGE, false, true>(ma, ma2, mb, mb2, p, s);
+  if (p.out_kind == 2)
+    launch_tc6<BN, BF16, HILO, STAGE, true>(ma, ma2, mb, mb2, p, s);
   else
-    launch_tc6<BN, BF16, HILO, STAGE, false, false>(ma, ma2, mb, mb2, p, s);
+    launch_tc6<BN, BF16, HILO, STAGE, false>(ma, ma2, mb, mb2, p, s);
 }
 template <int BN, bool BF16, bool HILO>
 void launch_tc3(const CUtensorMap& ma, const CUtensorMap& ma2, const CUtensorMap& mb, const CUtensorMap& mb2,
                 const TcGemmParams& p, cudaStream_t s) {
-  // 256-row tiles (two m halves sharing each B tile): single CTAs, direct stores
+  // 256-row tiles (two m halves sharing each B tile): direct stores
   if constexpr (BN == 256) {
     if (p.m_halves == 2) {
       if (p.out_kind == 2)
-        launch_tc6<BN, BF16, HILO, false, false, true, false, 2>(ma, ma2, mb, mb2, p, s);
+        launch_tc6<BN, BF16, HILO, false, true, false, 2>(ma, ma2, mb, mb2, p, s);
       else
-        launch_tc6<BN, BF16, HILO, false, false, false, false, 2>(ma, ma2, mb, mb2, p, s);
+        launch_tc6<BN, BF16, HILO, false, false, false, 2>(ma, ma2, mb, mb2, p, s);
       return;
     }
   }
-  // K accumulated in chunks: single CTAs, direct stores along m (no staging)
+  // K accumulated in chunks: direct stores along m (no staging)
   if (p.acc_split) {
     if (p.out_kind == 2)
-      launch_tc6<BN, BF16, HILO, false, false, true, true>(ma, ma2, mb, mb2, p, s);
+      launch_tc6<BN, BF16, HILO, false, true, true>(ma, ma2, mb, mb2, p, s);
     else
-      launch_tc6<BN, BF16, HILO, false, false, false, true>(ma, ma2, mb, mb2, p, s);
+      launch_tc6<BN, BF16, HILO, false, false, true>(ma, ma2, mb, mb2, p, s);
     return;
   }
   if (p.stage_n)

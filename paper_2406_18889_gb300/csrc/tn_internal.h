@@ -122,7 +122,6 @@ struct TcGemmParams {
   int* err;                   // device flag raised when a bounded wait times out
   int bn;                     // real-column tile (32, 64, 128 or 256)
   int stage_n;                // write tiles out along n (n is the output's contiguous index)
-  int cluster2;               // two-CTA clusters sharing B tiles by TMA multicast
   int acc_split;              // > 0: accumulate K in chunks of this many k tiles, summed in FP32 registers
   int off32;                  // every offset inside a tile (from its base) fits in 32 bits (set by the launcher)
   int m_halves;               // 2: 256-row tiles, two 128-row MMAs sharing each B tile (tile width 256 only)

@@ -38,7 +38,11 @@ class Plan:
 
     def __init__(self, tn: TensorNetwork, tree: Tree, prec: str = "c64", flags: int = 0,
                  max_slice_batch: int = 64, mem_cap_bytes: int = 0, stream=None,
-                 own_workspace: bool = True):
+                 own_workspace: bool = True, hilo_steps=None, hilo_tol: float = 0.0):
+        """``max_slice_batch = 0`` lets the library choose the batch from the
+        memory budget; ``hilo_steps`` (per step 0/1) or ``flags`` with
+        ``TN_FLAG_HILO_AUTO`` (target ``hilo_tol``) place split-precision
+        products on chosen tensor-core steps."""
         torch = _torch()
         self.tn, self.tree = tn, tree
         self.n_slices_total = 1 << len(tree.sliced_edges)
@@ -47,10 +51,10 @@ class Plan:
         self.handle = B.tn_plan_create(rank, edges, tn.edge_dim, data, tn.open_edges, tn.block_edge,
                                        np.asarray(tree.pairs, dtype=np.int32).reshape(-1),
                                        tree.sliced_edges, PREC[prec], flags, max_slice_batch,
-                                       mem_cap_bytes, s.cuda_stream)
+                                       mem_cap_bytes, s.cuda_stream, hilo_steps=hilo_steps, hilo_tol=hilo_tol)
         self.info = B.tn_plan_query(self.handle)
         self.prec, self.flags = prec, flags
-        self.max_slice_batch = max_slice_batch
+        self.max_slice_batch = B.tn_plan_slice_batch(self.handle)
         self.G = tn.n_blocks
         self.J = 1
         for e in tn.open_edges:
@@ -61,6 +65,9 @@ class Plan:
 
     def steps(self) -> dict:
         return B.tn_plan_steps(self.handle)
+
+    def precision(self) -> dict:
+        return B.tn_plan_precision(self.handle)
 
     def contract(self, slice_ids: Optional[Sequence[int]] = None, out=None, accumulate: bool = False,
                  stream=None):
@@ -79,12 +86,12 @@ class Plan:
 
     def autotune(self, slice_ids: Optional[Sequence[int]] = None, reps: int = 3, cache: Optional[str] = None,
                  stream=None) -> np.ndarray:
-        """Launch forms of the tensor-core steps (tile width, row halves, pair),
+        """Launch forms of the tensor-core steps (tile width, row halves),
         timed on one batch of slices (the first ``max_slice_batch`` of
         ``slice_ids``, default the first slices) by ``tn_plan_autotune``.  With
         ``cache`` (a JSON file of forms keyed by precision, flags and step shape),
         forms found there are set without timing, and newly tuned ones are added
-        to the file.  Returns int32 [n_steps, 3] (zeros: step not tuned)."""
+        to the file.  Returns int32 [n_steps, 2] (zeros: step not tuned)."""
         import json
         torch = _torch()
         st = self.steps()
@@ -97,7 +104,7 @@ class Plan:
             with open(cache) as fh:
                 known = json.load(fh)
         if tuned and all(keys[t] in known for t in tuned):
-            forms = np.zeros((len(kinds), 3), np.int32)
+            forms = np.zeros((len(kinds), 2), np.int32)
             for t in tuned:
                 forms[t] = known[keys[t]]
             try:

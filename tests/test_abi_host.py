@@ -223,9 +223,9 @@ def test_tuning_forms_validated_before_any_change(lib):
         tuned = np.where(((k & 8) > 0) & ((k & 4) == 0))[0]
         other = np.where((k & 8) == 0)[0]
         assert len(tuned) >= 1 and len(other) >= 1
-        zeros = np.zeros((len(k), 3), np.int32)
+        zeros = np.zeros((len(k), 2), np.int32)
         lib.tn_plan_set_tuning(h, zeros)  # every step at its default form
-        candidates = [(256, 1, 0), (256, 2, 0), (256, 1, 1), (128, 1, 0), (64, 1, 0), (32, 1, 0)]
+        candidates = [(256, 1), (256, 2), (128, 1), (64, 1), (32, 1)]
         for t in tuned:
             accepted = []
             for f in candidates:
@@ -236,11 +236,11 @@ def test_tuning_forms_validated_before_any_change(lib):
                     accepted.append(f)
                 except lib.TNError as e:
                     assert e.status == 1
-            # the widest tile for N and half of it at least; pairs and 256-row tiles only at width 256
+            # the widest tile for N and half of it at least; 256-row tiles only at width 256
             assert len(accepted) >= 2
-            if (256, 1, 1) in accepted or (256, 2, 0) in accepted:
-                assert (256, 1, 0) in accepted
-        for bad_step, bad in ((tuned[0], (999, 1, 0)), (tuned[0], (256, 3, 0)), (other[0], (256, 1, 0))):
+            if (256, 2) in accepted:
+                assert (256, 1) in accepted
+        for bad_step, bad in ((tuned[0], (999, 1)), (tuned[0], (256, 3)), (other[0], (256, 1))):
             forms = zeros.copy()
             forms[bad_step] = bad
             with pytest.raises(lib.TNError) as ei:
@@ -252,3 +252,72 @@ def test_tuning_forms_validated_before_any_change(lib):
             lib.tn_plan_autotune(h, [0], 1 << 20, 1 << 20, 1 << 30, 0, 1)
     finally:
         lib.tn_plan_destroy(h)
+
+
+def test_slice_batch_chosen_from_memory_cap(lib):
+    # max_slice_batch = 0: the largest power of two whose memory fits the cap
+    from paper_2406_18889_gb300 import engine as E
+    w = W.workload("grid4x6_d14")
+    prep = E.prepare(w)
+    need = {}
+    for b in (1, 2, 4, 8, 16, 32, 64):
+        h = _create(lib, prep, prec=2, flags=lib.TN_FLAG_PLAN_ONLY | lib.TN_FLAG_HOIST_INVARIANT, max_slice_batch=b)
+        need[b] = lib.tn_plan_query(h)["workspace_bytes"]
+        lib.tn_plan_destroy(h)
+    assert all(need[b] <= need[2 * b] for b in (1, 2, 4, 8, 16, 32))
+    for cap, lo, hi in ((need[64] * 4, 64, 64), (need[16] * 1.02 + (1 << 30), 4, 16)):
+        h = _create(lib, prep, prec=2, flags=lib.TN_FLAG_PLAN_ONLY | lib.TN_FLAG_HOIST_INVARIANT,
+                    max_slice_batch=0, mem_cap_bytes=int(cap))
+        b = lib.tn_plan_slice_batch(h)
+        assert lo <= b <= hi and (b & (b - 1)) == 0, (cap, b)
+        assert lib.tn_plan_query(h)["workspace_bytes"] <= cap
+        lib.tn_plan_destroy(h)
+    # nothing fits: batch 1, rejected by the cap
+    with pytest.raises(lib.TNError) as ei:
+        _create(lib, prep, prec=2, flags=lib.TN_FLAG_PLAN_ONLY, max_slice_batch=0, mem_cap_bytes=1)
+    assert ei.value.status == 2
+    # never more than the number of slices (2^6)
+    h = _create(lib, prep, prec=0, flags=lib.TN_FLAG_PLAN_ONLY, max_slice_batch=0, mem_cap_bytes=1 << 50)
+    assert lib.tn_plan_slice_batch(h) == 64
+    lib.tn_plan_destroy(h)
+    # a plan-only plan has no device to ask for free memory
+    with pytest.raises(lib.TNError) as ei:
+        _create(lib, prep, prec=0, flags=lib.TN_FLAG_PLAN_ONLY, max_slice_batch=0)
+    assert ei.value.status == 1
+
+
+def test_hilo_steps_mask_places_split_products(lib):
+    from paper_2406_18889_gb300 import engine as E
+    w = W.workload("grid4x6_d14")
+    prep = E.prepare(w)
+    flags = lib.TN_FLAG_PLAN_ONLY | lib.TN_FLAG_HOIST_INVARIANT
+    h = _create(lib, prep, prec=1, flags=flags, max_slice_batch=64)
+    k0 = lib.tn_plan_steps(h)["kinds"]
+    ws0 = lib.tn_plan_query(h)["workspace_bytes"]
+    lib.tn_plan_destroy(h)
+    tc = np.where((k0 & 8) > 0)[0]
+    assert len(tc) >= 2 and not ((k0 & 16) > 0).any()
+    mask = np.zeros(len(k0), np.uint8)
+    mask[tc[::2]] = 1
+    mask[np.where((k0 & 8) == 0)[0][:3]] = 1  # ignored on CUDA-core steps
+    h = _create(lib, prep, prec=1, flags=flags, max_slice_batch=64, hilo_steps=mask)
+    k = lib.tn_plan_steps(h)["kinds"]
+    assert np.array_equal((k & 8) > 0, (k0 & 8) > 0)
+    assert np.array_equal(np.where((k & 16) > 0)[0], tc[::2])
+    assert lib.tn_plan_query(h)["workspace_bytes"] >= ws0
+    p = lib.tn_plan_precision(h)
+    assert p["n_tc_steps"] == len(tc) and p["n_hilo_steps"] == len(tc[::2]) and p["rel_l2_chosen"] == -1
+    lib.tn_plan_destroy(h)
+    # the mask does not combine with the global flags; entries are 0 or 1
+    for bad in (dict(flags=flags | lib.TN_FLAG_HILO, hilo_steps=mask),
+                dict(flags=flags | lib.TN_FLAG_HILO_AUTO, hilo_steps=mask),
+                dict(flags=flags | lib.TN_FLAG_HILO_AUTO | lib.TN_FLAG_HILO),
+                dict(flags=flags, hilo_steps=mask * 2),
+                dict(flags=flags | lib.TN_FLAG_HILO_AUTO, hilo_tol=1.5)):
+        with pytest.raises(lib.TNError) as ei:
+            _create(lib, prep, prec=1, max_slice_batch=64, **bad)
+        assert ei.value.status == 1
+    # automatic placement on a plan-only plan: nothing is measured, nothing split
+    h = _create(lib, prep, prec=1, flags=flags | lib.TN_FLAG_HILO_AUTO, max_slice_batch=64)
+    assert not ((lib.tn_plan_steps(h)["kinds"] & 16) > 0).any()
+    lib.tn_plan_destroy(h)

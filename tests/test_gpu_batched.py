@@ -7,6 +7,7 @@ import pytest
 
 import workloads as W
 from oracle import postprocess as pp
+from parity_checks import assert_amplitudes_close
 from oracle import statevector as sv
 
 pytestmark = pytest.mark.gpu
@@ -46,4 +47,4 @@ def test_uneven_batch_against_statevectors(E, prec, tol):
     for w, o in zip(ws, outs):
         psi = sv.simulate(w.circuit)
         ref, _ = sv.block_amplitudes(psi, w.n_qubits, w.open_qubits, w.closed_qubits, w.closed_bits)
-        assert pp.relative_l2(o.cpu().numpy(), ref) <= tol, w.name
+        assert_amplitudes_close(o.cpu().numpy(), ref, tol, w.name)

@@ -9,6 +9,7 @@ import pytest
 import workloads as W
 from oracle import einsum_tn as et
 from oracle import postprocess as pp
+from parity_checks import assert_amplitudes_close
 from oracle import statevector as sv
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +48,7 @@ def test_grid3x4_all_amplitudes(E):
     got = plan.contract().cpu().numpy()
     ref, _ = _sv_blocks(w)
     assert got.shape == (1, 4096)
-    assert pp.relative_l2(got, ref) <= C64_TOL
+    assert_amplitudes_close(got, ref, C64_TOL)
 
 
 @pytest.mark.parametrize("batch", [64, 16])
@@ -58,8 +59,7 @@ def test_grid4x6_all_slices(E, sv_grid4x6, batch):
     plan = E.Plan(prep.tn, prep.tree, max_slice_batch=batch)
     got = plan.contract().cpu().numpy()
     ref, _ = _sv_blocks(w, psi)
-    err = pp.relative_l2(got, ref)
-    assert err <= C64_TOL, err
+    assert_amplitudes_close(got, ref, C64_TOL)
 
 
 @pytest.mark.parametrize("prec,tol", [("c64", C64_TOL), ("fp16", 3e-3)])
@@ -78,8 +78,7 @@ def test_grid4x6_whole_state_vector(E, sv_grid4x6, prec, tol):
     got = amps.cpu().numpy()
     assert got.shape == (1 << 14, 1 << 10)
     ref, _ = _sv_blocks(w, psi)
-    err = pp.relative_l2(got, ref)
-    assert err <= tol, err
+    assert_amplitudes_close(got, ref, tol)
     # the blocks partition the state vector: total probability 1 (unit norm)
     assert abs(float(np.sum(np.abs(got) ** 2)) - 1.0) <= 2 * tol
     if prec == "c64":
@@ -104,7 +103,7 @@ def test_hoisted_invariant_subtrees(E, sv_grid4x6, prec):
     assert ((kinds & 4) > 0).sum() > 0
     got = plan.contract().cpu().numpy()
     ref, _ = _sv_blocks(w, psi)
-    assert pp.relative_l2(got, ref) <= (C64_TOL if prec == "c64" else 3e-3)
+    assert_amplitudes_close(got, ref, C64_TOL if prec == "c64" else 3e-3)
 
 
 @pytest.mark.parametrize("batch,n_run", [(8, 19), (4, 4), (16, 1)])
@@ -119,7 +118,7 @@ def test_partial_fraction_ragged_batches(E, batch, n_run):
     got = plan.contract(ids).cpu().numpy()
     net = et.build_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
     ref = et.contract(net, bonds, ids)
-    assert pp.relative_l2(got, ref) <= C64_TOL
+    assert_amplitudes_close(got, ref, C64_TOL)
 
 
 def test_accumulate_and_empty(E):
@@ -131,7 +130,7 @@ def test_accumulate_and_empty(E):
     full = plan.contract().cpu().numpy()
     out = plan.contract([0, 1, 2])
     plan.contract([3, 4, 5, 6, 7], out=out, accumulate=True)
-    assert pp.relative_l2(out.cpu().numpy(), full) <= C64_TOL
+    assert_amplitudes_close(out.cpu().numpy(), full, C64_TOL)
     plan.contract([], out=out)  # zero slices, overwrite -> zeros
     assert torch.count_nonzero(out).item() == 0
 

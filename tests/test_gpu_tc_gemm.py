@@ -1,7 +1,7 @@
 """Tensor-core (tcgen05) GEMM self-test through the C ABI: the stacked-4M real
 lowering of a complex GEMM against a plain FP32 CUDA-core GEMM of the same
 16-bit inputs (both accumulate in FP32; only the summation order differs).
-Every shape runs each tile form (single CTA, two-CTA cluster, chunked
+Every shape runs each tile form (one accumulator per tile, chunked
 accumulation, 256-row tiles) into an n-contiguous and an m-contiguous result."""
 import pytest
 

@@ -52,6 +52,27 @@ def test_noalloc_matches_workspace_entry_point_twice(env):
     plan.close()
 
 
+def test_noalloc_calls_allocate_no_device_memory(env):
+    # the defining property: after a first call (which loads the kernels and
+    # looks up the static array's address), further calls leave the device's
+    # free memory, as the driver reports it, unchanged
+    torch, B, E = env
+    w = W.workload("grid3x4_d8", cycles=10, l=6, G=8)
+    prep = E.prepare(w, n_sliced=4)
+    plan = E.Plan(prep.tn, prep.tree, max_slice_batch=8, own_workspace=False)
+    stream = torch.cuda.current_stream().cuda_stream
+    ids = np.arange(16, dtype=np.int64)
+    out = torch.zeros((plan.G, plan.J), dtype=torch.complex128, device="cuda")
+    B.tn_contract_slices_noalloc(plan.handle, ids, out.data_ptr(), 0, stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for acc in (0, 1, 1, 0):
+        B.tn_contract_slices_noalloc(plan.handle, ids, out.data_ptr(), acc, stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    plan.close()
+
+
 def test_noalloc_rejects_plan_beyond_static_workspace(env):
     torch, B, E = env
     w = W.workload("grid4x6_d14")
