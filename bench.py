@@ -193,10 +193,11 @@ def sliced_wires(refine: bool = False):
 
 
 def run_reference(args):
+    refined = args.path == "refined"
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    w, prep, wires = sliced_wires(args.refine_path)
+    w, prep, wires = sliced_wires(refined)
     sample = "1 slice of 64 per step, oracle O2 (naive FP64 einsum contractor, numpy matmul)"
     for s in range(args.warmup):
         oracle_slices_per_s(w, wires, [s % 64])
@@ -220,11 +221,11 @@ KIND_NAMES = {0: "gemm_cuda_core", 1: "bit_permute", 2: "gather", 3: "accumulate
               4: "expand_operand", 5: "gemm_tensor_core"}
 
 
-# DRAM bytes (read + write) of the largest tensor-core launch of one step of the
-# default configuration (fp16, slice batch 64, invariant subtrees hoisted), from
-# the ncu capture summarised in profiles/tc_gemm_grid4x6_d14_fp16_dram.md
-# (dram__bytes_read.sum + dram__bytes_write.sum of that launch)
-DOMINANT_TRAFFIC = {("fp16", 64, False, True): 2099474176}
+# DRAM bytes (read + write) of the step's longest launch, per configuration
+# (path, precision, slice batch, split products, hoisting), as an ncu capture
+# of that launch measured them (dram__bytes_read.sum + dram__bytes_write.sum);
+# a configuration without an entry, or whose kernels changed since, reports null
+DOMINANT_TRAFFIC = {}
 
 
 def fp32_peak_measured(B) -> tuple:
@@ -284,7 +285,9 @@ def roofline_from_profile(prof, cfg_key=None, alu=None) -> tuple:
         r = {"bound": "hbm", "achieved": b / (t / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
              "peak_source": f"hbm_gbs {src}"}
     r["frac"] = r["achieved"] / r["peak"]
-    r["traffic"] = DOMINANT_TRAFFIC.get(cfg_key) if k == 5 else None
+    r["traffic"] = DOMINANT_TRAFFIC.get(cfg_key)
+    if r["traffic"] is None:
+        r["traffic_note"] = "no ncu DRAM capture of this configuration's longest launch with the current kernels"
     r["kernel"] = f"{KIND_NAMES[k]}: the step's longest launch ({t:.3f} ms)"
     r["algorithmic"] = {"flops": f, "bytes": b}
     r["path"] = {"roofline_ms": t_roof, "ms": t_all, "frac": t_roof / t_all if t_all > 0 else None,
@@ -319,6 +322,7 @@ def permute_bandwidth(B, torch, stream, bits: int = 28) -> dict:
 
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
+    refined = args.path == "refined"
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -328,9 +332,12 @@ def run_ours(args):
     from paper_2406_18889_gb300 import binding as B
     from paper_2406_18889_gb300 import engine as E
 
-    w = rank_workload(rank)
-    prep = E.prepare(w, refine=args.refine_path, method="both" if args.refine_path else "greedy",
-                     workers=host_cores() if args.refine_path else 0)
+    # N > 1: the 64 slices of one problem split over the ranks, partials summed on
+    # rank 0 (--partition slices), or every rank its own blocks (--partition blocks)
+    split_slices = world > 1 and args.partition == "slices"
+    w = rank_workload(0 if split_slices else rank)
+    prep = E.prepare(w, refine=refined, method="both" if refined else "greedy",
+                     workers=host_cores() if refined else 0)
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
     plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
     S = plan.n_slices_total
@@ -346,8 +353,14 @@ def run_ours(args):
     info = plan.info
     useful_per_slice = info["useful_flops_per_slice"]
 
+    from paper_2406_18889_gb300 import multirank as MR
+
     def step():
-        plan.contract(ids, out=amps)
+        if split_slices:
+            if MR.contract_partitioned(plan, ids, dist, world, rank, out=amps) is None:
+                return None
+        else:
+            plan.contract(ids, out=amps)
         idx, p = E.topk(amps, w.k, 1.0, base, pos)
         x = E.xeb(p, w.n_qubits)  # f = 1: the selected p are the strings' probabilities
         return idx, p, x
@@ -376,7 +389,7 @@ def run_ours(args):
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms = max_over_ranks(ms, dist, "cuda")
-    slices = sum_over_ranks(float(S * args.steps), dist, "cuda")
+    slices = float(S * args.steps) if split_slices else sum_over_ranks(float(S * args.steps), dist, "cuda")
     value = slices / (ms / 1e3)
 
     if args.only_timed:
@@ -395,7 +408,13 @@ def run_ours(args):
 
     def e2e_step():
         d_base.copy_(h_base, non_blocking=True)
-        plan.contract(h_ids.numpy(), out=amps)  # slice ids travel host -> device inside the call
+        # slice ids travel host -> device inside the call
+        if split_slices:
+            if MR.contract_partitioned(plan, h_ids.numpy(), dist, world, rank, out=amps) is None:
+                torch.cuda.synchronize()
+                return None
+        else:
+            plan.contract(h_ids.numpy(), out=amps)
         idx, p = E.topk(amps, w.k, 1.0, d_base, pos)
         x = E.xeb(p, w.n_qubits)
         h_idx.copy_(idx, non_blocking=True)
@@ -425,8 +444,8 @@ def run_ours(args):
     prof = B.tn_contract_slices_profile(plan.handle, ids, amps.data_ptr(), 0, plan.workspace.data_ptr(),
                                         plan.workspace.numel(), stream.cuda_stream)
     alu = fp32_peak_measured(B)
-    roofline, per_kind = roofline_from_profile(prof, (args.prec, args.batch, bool(args.hilo), not args.no_hoist),
-                                               alu)
+    roofline, per_kind = roofline_from_profile(prof, (args.path, args.prec, args.batch, bool(args.hilo),
+                                                      not args.no_hoist), alu)
     permute = permute_bandwidth(B, torch, stream)
     # recorded kernels + slice-id uploads (one launch per 256 ids of each batch) + top-k + XEB
     n_batches = -(-S // args.batch)
@@ -449,6 +468,31 @@ def run_ours(args):
         torch.cuda.synchronize()
         fine_value = S * 3 / (e0.elapsed_time(e1) / 1e3)
         planf.close()
+    # bf16 with split products on every tensor-core step, and only where the
+    # calibration says their 16-bit error moves the amplitudes (TN_FLAG_HILO_AUTO, 3e-3)
+    split = None
+    if args.prec != "c64" and not args.no_c64:
+        split = {"note": "bf16 tensor-core operands; hi + lo split products on every tensor-core step, or on "
+                         "those TN_FLAG_HILO_AUTO picks for relative L2 <= 3e-3 on the calibration batch "
+                         "(contraction only)"}
+        hoist = 0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT
+        for name, fl, kw in (("all_steps", B.TN_FLAG_HILO, {}), ("auto", B.TN_FLAG_HILO_AUTO, {"hilo_tol": 3e-3})):
+            pl = E.Plan(prep.tn, prep.tree, prec="bf16", max_slice_batch=args.batch, flags=fl | hoist, **kw)
+            for _ in range(2):
+                pl.contract(ids, out=amps)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                pl.contract(ids, out=amps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pr = pl.precision()
+            split[name] = {"value": S * 3 / (e0.elapsed_time(e1) / 1e3), "unit": "slices/s",
+                           "n_tc_steps": pr["n_tc_steps"], "n_hilo_steps": pr["n_hilo_steps"]}
+            if name == "auto":
+                split[name].update({"calibration_rel_l2": pr["rel_l2_chosen"],
+                                    "calibration_rel_l2_without_split": pr["rel_l2_none"]})
+            pl.close()
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
         plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch,
@@ -462,28 +506,30 @@ def run_ours(args):
             plan64.contract(ids, out=amps)
         e1.record(stream)
         torch.cuda.synchronize()
-        c64_value = sum_over_ranks(5.0 * S, dist, "cuda") / (max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / 1e3)
+        c64_slices = 5.0 * S if split_slices else sum_over_ranks(5.0 * S, dist, "cuda")
+        c64_value = c64_slices / (max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / 1e3)
         plan64.close()
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        _, _, wires = sliced_wires(args.refine_path)
+        _, _, wires = sliced_wires(refined)
         v = oracle_slices_per_s(rank_workload(0), wires, [0, 1])
         cpu = {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
                "sample": "2 of the 64 slices, oracle O2 (naive FP64 einsum contractor, numpy matmul)"}
     line = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if split_slices else "weak", "vs_baseline": None,
         "dtype": "complex64" if args.prec == "c64" else
                  f"{args.prec} tensor-core operands, fp32 accumulate, complex64 elsewhere",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
                    "hoist_invariant": not args.no_hoist, "autotune": bool(args.autotune),
-                   "path": "greedy and bisection + subtree reconfiguration" if args.refine_path else "greedy",
+                   "path": "greedy and bisection + subtree reconfiguration" if refined else "greedy",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"{world} independent block sets (one per GPU)"},
+                   "parallelism": (f"the 64 slices split over {world} GPUs, FP64 partials gathered and summed "
+                                   "on rank 0" if split_slices else f"{world} independent block sets (one per GPU)")},
         "useful_tflops": value * useful_per_slice / 1e12,
         "complex64_path": None if c64_value is None else {
             "value": c64_value, "unit": "slices/s", "speedup": value / c64_value,
@@ -495,6 +541,7 @@ def run_ours(args):
             "vs_complex64_path": None if c64_value is None else fine_value / c64_value,
             "note": "fp16 hi+lo operands, K accumulated one k tile at a time in FP32 (TN_FLAG_HILO | "
                     "TN_FLAG_FINE_ACC): complex64 accuracy on the tensor cores (contraction only)"},
+        "bf16_split_precision": split,
         "useful_flops_per_slice": useful_per_slice,
         "wall_s": wall,
         "roofline": roofline,
@@ -512,6 +559,7 @@ def run_ours(args):
 def run_uneven(args):
     """The 64 uneven circuits contracted in one tn_contract_slices_batched call
     (every slice of every circuit, FP64 sums per circuit), on one GPU."""
+    refined = args.path == "refined"
     import torch
     import workloads as W
     from paper_2406_18889_gb300 import binding as B
@@ -519,17 +567,26 @@ def run_uneven(args):
     torch.cuda.set_device(0)
     ws = W.configs.uneven_batch(64)
     t0 = time.perf_counter()
-    preps = [E.prepare(w, restarts=1, refine=args.refine_path, method="both" if args.refine_path else "greedy",
-                       workers=host_cores() if args.refine_path else 0) for w in ws]
+    preps = [E.prepare(w, restarts=1, refine=refined, method="both" if refined else "greedy",
+                       workers=host_cores() if refined else 0) for w in ws]
     plan_s = time.perf_counter() - t0
-    flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
-    # slice batch at most 16: at 64 the largest (28-qubit) circuit alone needs a 164 GB workspace
-    batch = min(args.batch, 16)
-    plans = [E.Plan(p.tn, p.tree, prec=args.prec, flags=flags, own_workspace=False,
-                    max_slice_batch=min(batch, 1 << len(p.tree.sliced_edges))) for p in preps]
+    flags = ((B.TN_FLAG_HILO if args.hilo else 0) | (B.TN_FLAG_HILO_AUTO if args.hilo_auto else 0) |
+             (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT))
+    # each plan's slice batch chosen by the library from a 16 GiB budget (and its slice count)
+    cap = 16 << 30
+    plans = [E.Plan(p.tn, p.tree, prec=args.prec, flags=flags, own_workspace=False, max_slice_batch=0,
+                    mem_cap_bytes=cap, hilo_tol=3e-3) for p in preps]
     outs = [torch.empty((w.G, 1 << w.l), dtype=torch.complex128, device="cuda") for w in ws]
-    wsz = max(max(p.info["workspace_bytes"], 256) for p in plans)
-    wsb = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+    counts = [p.n_slices_total for p in plans]
+    # the workspace for the most concurrent branches that fit in half the free memory
+    free = torch.cuda.mem_get_info()[0]
+    branches, wsz = 1, 0
+    for k in range(8, 0, -1):
+        wsz = B.tn_batched_workspace_bytes([p.handle for p in plans], counts, k)
+        branches = k
+        if wsz <= free // 2:
+            break
+    wsb = torch.empty(max(wsz, 256), dtype=torch.uint8, device="cuda")
     ids = [np.arange(p.n_slices_total, dtype=np.int64) for p in plans]
     slices = sum(len(x) for x in ids)
     flops = sum(p.info["useful_flops_per_slice"] * len(x) for p, x in zip(plans, ids))
@@ -555,7 +612,12 @@ def run_uneven(args):
         "higher_is_better": True, "dtype": args.prec, "data": "synthetic",
         "config": {"workload": "64 seeded circuits, 4x4..4x7 grids, depth 10..16, 2^2..2^8 slices, "
                                "l = 8, G = 16 (16..28 qubits)", "circuits": len(ws), "slices": slices,
-                   "slice_batch": batch, "hilo": args.hilo, "l2": "not flushed (one batched call)"},
+                   "slice_batch": "per plan, from a 16 GiB budget: " + ",".join(
+                       str(p.max_slice_batch) for p in plans),
+                   "graph_branches": branches, "workspace_bytes": wsz,
+                   "hilo": "auto (3e-3)" if args.hilo_auto else args.hilo,
+                   "path": "greedy and bisection + subtree reconfiguration" if refined else "greedy",
+                   "l2": "not flushed (one batched call)"},
         "useful_tflops": flops / (ms / 1e3) / 1e12, "host_planning_s": plan_s}), flush=True)
     for p in plans:
         p.close()
@@ -567,6 +629,7 @@ def run_sycamore(args):
     a few seeded slices timed one by one, and the extrapolated time to 1e6
     samples at the fidelity whose top-1 XEB is 0.002 (Eq. 4: F = 0.002 /
     (H_1024 - 1); slices needed per block batch = F x 2^(sliced bonds))."""
+    refined = args.path == "refined"
     import math
     import torch
     import workloads as W
@@ -578,8 +641,8 @@ def run_sycamore(args):
     w = W.workload("sycamore53_d20", cycles=20, l=10, G=16)
     tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
     t0 = time.perf_counter()
-    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition", refine=args.refine_path,
-                       workers=host_cores() if args.refine_path else 0)
+    tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition", refine=refined,
+                       workers=host_cores() if refined else 0)
     plan_s = time.perf_counter() - t0
     plan = E.Plan(tn, tree, prec=args.prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=1)
     s = len(tree.sliced_edges)
@@ -603,13 +666,14 @@ def run_sycamore(args):
         "unit": "s/slice", "higher_is_better": False, "steps": args.steps, "dtype": args.prec,
         "data": "synthetic", "config": {"workload": "53-qubit Sycamore-shaped diagonal grid, 20 cycles, l = 10, "
                                                   "G = 16, k = 1 per block", "cap_log2": 32, "sliced_bonds": s,
-                                        "path": "recursive bisection"},
+                                        "path": "recursive bisection + subtree reconfiguration" if refined
+                                        else "recursive bisection"},
         "useful_tflops": useful / t_slice / 1e12, "useful_flops_per_slice": useful,
         "path_cost_complex_macs": tree.cost_per_slice * 2.0 ** s, "host_planning_s": plan_s,
         "extrapolation_1e6_samples": {"fidelity_F": F, "slices_per_block_batch": slices_per_batch,
                                       "block_batches": batches,
                                       "seconds": slices_per_batch * batches * t_slice,
-                                      "note": "bounded by the path: its cost is ~1e10 x the paper's 1.85e21"}}),
+                                      "note": "the total is set by the path's cost per slice x 2^sliced bonds"}}),
           flush=True)
     plan.close()
 
@@ -622,14 +686,20 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp16", choices=["c64", "bf16", "fp16"])
     ap.add_argument("--hilo", action="store_true", help="split-precision (hi + lo) tensor-core steps")
+    ap.add_argument("--hilo-auto", action="store_true",
+                    help="split products only where the calibration needs them for relative L2 <= 3e-3")
     ap.add_argument("--no-c64", action="store_true", help="skip timing the complex64 path alongside")
     ap.add_argument("--no-hoist", action="store_true",
                     help="recompute slice-independent subtrees in every batch instead of once per plan")
-    ap.add_argument("--refine-path", action="store_true",
-                    help="plan with subtree reconfiguration (less work per slice; same slices and outputs)")
+    ap.add_argument("--path", default="refined", choices=["refined", "greedy"],
+                    help="contraction path: greedy and bisection trees refined by subtree reconfiguration "
+                         "(default; 10x fewer flops per slice on the 24-qubit workload), or the greedy tree alone")
     ap.add_argument("--autotune", action="store_true",
                     help="time the tensor-core steps' launch forms on one batch first and keep the fastest")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--partition", default="slices", choices=["slices", "blocks"],
+                    help="N > 1: split the slices of one problem over the GPUs and reduce their FP64 partials "
+                         "(slices, strong scaling), or give every GPU its own blocks (blocks, weak scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="run warm-up and timed steps only (for ncu launch lists)")

@@ -293,15 +293,46 @@ tn_status tn_contract_slices(tn_plan_t plan, const int64_t* slice_ids, int64_t n
                              void* stream);
 
 /*
- * Several plans (e.g. many small circuits with uneven trees) in one call:
- * plan p contracts slice_ids[p][0..n_slices[p]) into amps[p].  Plans run one
- * after another on `stream` sharing `workspace` (size >= the largest
- * workspace_bytes among them).
+ * Several plans (e.g. many small circuits with uneven trees, north star
+ * "Batching") in one call: plan p contracts slice_ids[p][0..n_slices[p]) into
+ * amps[p], with the semantics of tn_contract_slices for each.  All of the
+ * plans' slice batches are captured into ONE CUDA graph whose up to 8
+ * concurrent branches each run a share of the plans one after another
+ * (longest work first onto the least-loaded branch) in their own region of
+ * `workspace`; a region is as large as the largest workspace_bytes among its
+ * plans.  When ws_bytes does not hold 8 regions, fewer branches are used (one
+ * branch needs the largest workspace_bytes of all plans);
+ * tn_batched_workspace_bytes gives the size for a number of branches.  A plan
+ * listed twice makes the call run on one branch.  The graph is kept (up to 4
+ * per process) and replayed while the plans, their launch forms, slice ids,
+ * outputs, workspace and accumulate flag repeat; otherwise it is captured
+ * again.  Every plan must live on the current device.  Arguments of every
+ * plan are validated before any work is queued.
  */
 tn_status tn_contract_slices_batched(const tn_plan_t* plans, int32_t n_plans,
                                      const int64_t* const* slice_ids, const int64_t* n_slices,
                                      void* const* amps, int accumulate, void* workspace,
                                      size_t ws_bytes, void* stream);
+
+/* Workspace bytes tn_contract_slices_batched needs for these plans and slice
+ * counts on up to max_branches (>= 1) concurrent branches. */
+tn_status tn_batched_workspace_bytes(const tn_plan_t* plans, int32_t n_plans, const int64_t* n_slices,
+                                     int32_t max_branches, int64_t* bytes);
+
+/*
+ * Sum of FP64 partial amplitudes over ranks (paper Sec. III: the sum over
+ * sliced sub-networks, split into independent subtasks whose partial sums are
+ * reduced once; the paper's cross-node reduction).  Each rank contracts its own
+ * share of the slice ids into a partial [G][2^l]; the partials, gathered on
+ * one device, are added here in part order, a fixed order, so the sum does not
+ * depend on how the gather was carried out.
+ *   parts     : device complex128 [n_parts][n_amps], part p = rank p's partial.
+ *   out       : device complex128 [n_amps]; accumulate = 0 overwrites it with
+ *               the sum, 1 adds the sum to it (the old value first).
+ * n_parts = 0 with accumulate = 0 zeroes out.  Asynchronous on `stream`.
+ */
+tn_status tn_sum_partials(const void* parts, int64_t n_parts, int64_t n_amps, void* out, int accumulate,
+                          void* stream);
 
 /*
  * Top-k post-processing (paper Sec. III): p = (re*re + im*im) * inv_f in FP64

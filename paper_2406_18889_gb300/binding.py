@@ -32,7 +32,8 @@ EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps"
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",
            "tn_topk_postprocess", "tn_xeb", "tn_contract_slices_noalloc", "tn_selftest_gemm_tc", "tn_plan_status",
            "tn_permute", "tn_selftest_bounded_wait", "tn_selftest_fp32_peak", "tn_plan_autotune",
-           "tn_plan_set_tuning", "tn_plan_slice_batch", "tn_plan_precision", "tn_last_error", "tn_version")
+           "tn_plan_set_tuning", "tn_plan_slice_batch", "tn_plan_precision", "tn_batched_workspace_bytes", "tn_sum_partials", "tn_last_error",
+           "tn_version")
 
 
 class TNError(RuntimeError):
@@ -101,6 +102,8 @@ def load() -> ctypes.CDLL:
     lib.tn_plan_autotune.argtypes = [vp, p_i64, i64, vp, vp, u64, vp, i32, p_i32]
     lib.tn_plan_set_tuning.argtypes = [vp, p_i32, i32]
     lib.tn_plan_slice_batch.argtypes = [vp, p_i32]
+    lib.tn_sum_partials.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp]
+    lib.tn_batched_workspace_bytes.argtypes = [ctypes.POINTER(vp), i32, p_i64, i32, p_i64]
     p_f64 = ctypes.POINTER(ctypes.c_double)
     lib.tn_plan_precision.argtypes = [vp, p_f64, p_f64, p_i32, p_i32]
     for name in EXPORTS[:-2]:
@@ -240,6 +243,21 @@ def tn_contract_slices_batched(plans: Sequence[int], slice_ids: Sequence, amps_p
         VP(*[ctypes.c_void_p(p) for p in plans]), n, PP(*[_p(a, ctypes.c_int64) for a in id_arrays]),
         _p(counts, ctypes.c_int64), VP(*[ctypes.c_void_p(a) for a in amps_ptrs]), int(accumulate),
         ctypes.c_void_p(ws_ptr), int(ws_bytes), ctypes.c_void_p(stream)))
+
+
+def tn_batched_workspace_bytes(plans: Sequence[int], n_slices: Sequence[int], max_branches: int = 8) -> int:
+    n = len(plans)
+    arr = (ctypes.c_void_p * max(n, 1))(*[ctypes.c_void_p(p) for p in plans])
+    ns = _i64(n_slices)
+    out = ctypes.c_int64()
+    _check(load().tn_batched_workspace_bytes(arr, n, _p(ns, ctypes.c_int64), int(max_branches), ctypes.byref(out)))
+    return out.value
+
+
+def tn_sum_partials(parts_ptr: int, n_parts: int, n_amps: int, out_ptr: int, accumulate: int = 0,
+                    stream: int = 0) -> None:
+    _check(load().tn_sum_partials(ctypes.c_void_p(parts_ptr), int(n_parts), int(n_amps), ctypes.c_void_p(out_ptr),
+                                  int(accumulate), ctypes.c_void_p(stream)))
 
 
 def tn_topk_postprocess(amps_ptr: int, G: int, B: int, k: int, inv_f: float, global_mode: int,

@@ -324,21 +324,52 @@ tn_status tn_contract_slices_batched(const tn_plan_t* plans, int32_t n_plans, co
     TN_CHECK(n_plans >= 0, TN_ERR_INVALID_ARG, "n_plans < 0");
     TN_CHECK(n_plans == 0 || (plans && slice_ids && n_slices && amps), TN_ERR_INVALID_ARG, "null array");
     TN_CHECK(!fault_injected("stream"), TN_ERR_CUDA, "injected stream failure (TN_FAULT=stream)");
+    TN_CHECK(accumulate == 0 || accumulate == 1, TN_ERR_INVALID_ARG, "accumulate must be 0 or 1");
     // validate every plan's arguments before queuing any work
+    std::vector<Plan*> ps;
     for (int32_t i = 0; i < n_plans; ++i) {
       TN_CHECK(plans[i] != nullptr, TN_ERR_INVALID_ARG, "plan is null");
-      const Plan& P = *plans[i]->p;
+      Plan& P = *plans[i]->p;
+      TN_CHECK(!(P.flags & TN_FLAG_PLAN_ONLY), TN_ERR_INVALID_ARG, "plan was created with TN_FLAG_PLAN_ONLY");
       TN_CHECK(amps[i] != nullptr, TN_ERR_INVALID_ARG, "amps is null");
       TN_CHECK(n_slices[i] >= 0 && (n_slices[i] == 0 || slice_ids[i]), TN_ERR_INVALID_ARG, "bad slice list");
       const int64_t S = int64_t(1) << P.sliced.size();
       for (int64_t j = 0; j < n_slices[i]; ++j)
         TN_CHECK(slice_ids[i][j] >= 0 && slice_ids[i][j] < S, TN_ERR_INVALID_ARG, "slice id out of range");
-      if (n_slices[i] > 0)
-        TN_CHECK((int64_t)ws_bytes >= P.mem.ws_bytes && workspace, TN_ERR_INVALID_ARG, "workspace too small");
+      ps.push_back(&P);
     }
-    for (int32_t i = 0; i < n_plans; ++i)
-      contract_one(*plans[i]->p, slice_ids[i], n_slices[i], amps[i], accumulate, workspace, ws_bytes,
-                   (cudaStream_t)stream);
+    if (n_plans == 0) return;
+    TN_CHECK(workspace != nullptr && (reinterpret_cast<uintptr_t>(workspace) & 255) == 0, TN_ERR_INVALID_ARG,
+             "workspace must be non-null and 256-byte aligned");
+    TN_CHECK(batched_layout(ps, n_slices, ws_bytes, 8).bytes <= (int64_t)ws_bytes, TN_ERR_INVALID_ARG,
+             "workspace too small");
+    contract_batched(ps, slice_ids, n_slices, amps, accumulate, workspace, ws_bytes, (cudaStream_t)stream);
+  });
+}
+
+tn_status tn_batched_workspace_bytes(const tn_plan_t* plans, int32_t n_plans, const int64_t* n_slices,
+                                     int32_t max_branches, int64_t* bytes) {
+  return guarded([&] {
+    TN_CHECK(n_plans >= 0 && (n_plans == 0 || (plans && n_slices)) && bytes, TN_ERR_INVALID_ARG, "null array");
+    TN_CHECK(max_branches >= 1, TN_ERR_INVALID_ARG, "max_branches must be >= 1");
+    std::vector<Plan*> ps;
+    for (int32_t i = 0; i < n_plans; ++i) {
+      TN_CHECK(plans[i] != nullptr && n_slices[i] >= 0, TN_ERR_INVALID_ARG, "bad plan or slice count");
+      ps.push_back(plans[i]->p.get());
+    }
+    *bytes = n_plans == 0 ? 0 : batched_layout(ps, n_slices, (size_t)INT64_MAX, max_branches).bytes;
+  });
+}
+
+tn_status tn_sum_partials(const void* parts, int64_t n_parts, int64_t n_amps, void* out, int accumulate,
+                          void* stream) {
+  return guarded([&] {
+    TN_CHECK(n_parts >= 0 && n_amps >= 0, TN_ERR_INVALID_ARG, "negative count");
+    TN_CHECK(out != nullptr && (n_parts == 0 || parts != nullptr), TN_ERR_INVALID_ARG, "null pointer");
+    TN_CHECK(accumulate == 0 || accumulate == 1, TN_ERR_INVALID_ARG, "accumulate must be 0 or 1");
+    TN_CHECK(n_parts <= (int64_t(1) << 40) / std::max<int64_t>(n_amps, 1), TN_ERR_INVALID_ARG, "too many elements");
+    launch_sum_partials(parts, n_parts, n_amps, out, accumulate, (cudaStream_t)stream);
+    TN_CUDA(cudaGetLastError());
   });
 }
 

@@ -28,6 +28,8 @@
 //  * direct: one thread per output element, for the remaining shapes too
 //    small for a tile.
 #include <algorithm>
+#include <mutex>
+#include <set>
 #include <type_traits>
 
 #include <cuda_bf16.h>
@@ -341,20 +343,32 @@ __device__ __forceinline__ void store_v(const SmallK& p, int64_t o, const float2
   }
 }
 
+// 8-byte asynchronous copy global -> shared (both 8-byte aligned)
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gmem_src)
+               : "memory");
+}
+
 // MODE 0: C[o] = result (Out storage, hi + lo when `hilo`); MODE 1: expanded
 // destination.  KC: the contracted extent; V: adjacent outputs per thread (the
 // tile's bit 0 is then a unit-stride bit of the destination).  Thread t of a
 // tile takes outputs V*(t + 256*i) + v: the part of every map that depends on
 // t is read once into registers, the part that depends on i is a broadcast.
+// The staged A and B entries of tile n+1 are copied (cp.async) while tile n is
+// computed, into the other half of a double buffer; staged entry
+// s = t + 256 r of a tile has operand offset tile base + (thread part, in a
+// register) + (part of r, a table of at most 8 entries).
 template <class Out, int MODE, int KC, int V>
 __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
   extern __shared__ float2 staged[];
   __shared__ uint32_t sel_lo[256], sel_hi[16];
   __shared__ int64_t off_lo[256], off_hi[16];
+  __shared__ int64_t a_hi[8], b_hi[8];
   constexpr int lgK = KC == 1 ? 0 : KC == 2 ? 1 : 2;
   constexpr int sh = V - 1;  // tile bits below the thread index
-  float2* As = staged;
-  float2* Bs = staged + (KC << p.na);
+  const int na_n = KC << p.na, nb_n = KC << p.nb;
+  const int buf_n = na_n + nb_n;  // buffer q starts at staged + q * buf_n
   // tables over tile bits sh..sh+7 (thread index) and sh+8.. (iteration);
   // linear maps: OR / sum of the parts
   {
@@ -381,16 +395,36 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
       sel_hi[j] = sel;
       off_hi[j] = off;
     }
+    // staged entry s = j + 256 r: u = s >> lgK takes bits 0..7-lgK from j and
+    // the rest from r (256 is a multiple of KC)
+    if (j < 8) {
+      int64_t ah = 0, bh = 0;
+      for (int b = 0; b < 3; ++b)
+        if ((j >> b) & 1) {
+          const int q = 8 - lgK + b;
+          if (q < p.na) ah += p.a_wt[q];
+          if (q < p.nb) bh += p.b_wt[q];
+        }
+      a_hi[j] = ah;
+      b_hi[j] = bh;
+    }
+  }
+  int64_t a_lo = p.ak[threadIdx.x & (KC - 1)], b_lo = p.bk[threadIdx.x & (KC - 1)];
+  {
+    const int u = threadIdx.x >> lgK;
+    for (int b = 0; b < 8 - lgK; ++b)
+      if ((u >> b) & 1) {
+        if (b < p.na) a_lo += p.a_wt[b];
+        if (b < p.nb) b_lo += p.b_wt[b];
+      }
   }
   // tile bit 0 (V = 2): its staged-index bits (rank 0 when it is an A / B bit)
   const uint32_t a_v = (V == 2 && p.a_rank[0] >= 0) ? 1u : 0u;
   const uint32_t b_v = (V == 2 && p.b_rank[0] >= 0) ? 1u : 0u;
   const int64_t ntiles = int64_t(1) << (p.nbits - p.P);
   const int n_q = (1 << p.P) / V;
-  const int na_n = KC << p.na, nb_n = KC << p.nb;
-  // A, B and destination offsets of a tile's origin, double-buffered: warp 0
-  // forms the next tile's while the block stages this one (lanes take the
-  // tile index bits, then a warp reduction)
+  // A, B and destination offsets of tile origins: warp 0 forms them two
+  // tiles ahead (lanes take the tile index bits, then a warp reduction)
   __shared__ int64_t tile_base[2][3];
   const int lane = threadIdx.x & 31;
   auto bases = [&](int64_t t, int slot) {
@@ -413,30 +447,37 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
       tile_base[slot][2] = o;
     }
   };
+  // queue the asynchronous copies of one tile's staged entries into buffer q
+  auto stage = [&](int slot, int q) {
+    const int64_t a0 = tile_base[slot][0] + a_lo, b0 = tile_base[slot][1] + b_lo;
+    float2* As = staged + q * buf_n;
+    float2* Bs = As + na_n;
+    for (int r = 0, i = threadIdx.x; i < na_n; ++r, i += 256) cp_async8(As + i, p.A + a0 + a_hi[r]);
+    for (int r = 0, i = threadIdx.x; i < nb_n; ++r, i += 256) cp_async8(Bs + i, p.B + b0 + b_hi[r]);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int64_t G = gridDim.x;
   if (threadIdx.x < 32 && (int64_t)blockIdx.x < ntiles) bases(blockIdx.x, 0);
   __syncthreads();
+  if ((int64_t)blockIdx.x < ntiles) stage(0, 0);
+  if (threadIdx.x < 32 && blockIdx.x + G < ntiles) bases(blockIdx.x + G, 1);
   const uint32_t sel_t = sel_lo[threadIdx.x];
   const int64_t off_t = off_lo[threadIdx.x];
   int it = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-    __syncthreads();  // the previous tile's staged entries consumed; this tile's bases visible
-    const int64_t a0 = tile_base[it & 1][0], b0 = tile_base[it & 1][1], o0 = tile_base[it & 1][2];
-    for (int i = threadIdx.x; i < na_n; i += blockDim.x) {
-      const int u = i >> lgK;
-      int64_t o = a0 + p.ak[i & (KC - 1)];
-      for (int b = 0; b < p.na; ++b)
-        if ((u >> b) & 1) o += p.a_wt[b];
-      As[i] = p.A[o];
+  for (int64_t t = blockIdx.x; t < ntiles; t += G, ++it) {
+    const int cur = it & 1;
+    __syncthreads();  // the next tile's bases visible; the other buffer consumed
+    const int64_t o0 = tile_base[cur][2];
+    if (t + G < ntiles) {
+      stage(cur ^ 1, cur ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < nb_n; i += blockDim.x) {
-      const int u = i >> lgK;
-      int64_t o = b0 + p.bk[i & (KC - 1)];
-      for (int b = 0; b < p.nb; ++b)
-        if ((u >> b) & 1) o += p.b_wt[b];
-      Bs[i] = p.B[o];
-    }
-    if (threadIdx.x < 32 && t + gridDim.x < ntiles) bases(t + gridDim.x, (it + 1) & 1);
-    __syncthreads();
+    __syncthreads();  // this tile's staged entries visible; every thread holds o0
+    if (threadIdx.x < 32 && t + 2 * G < ntiles) bases(t + 2 * G, cur);
+    const float2* As = staged + cur * buf_n;
+    const float2* Bs = As + na_n;
     const int64_t ot = o0 + off_t;
 #pragma unroll 2
     for (int q = threadIdx.x; q < n_q; q += blockDim.x) {
@@ -456,6 +497,18 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
       store_v<Out, MODE, V>(p, ot + off_hi[h], r, hilo);
     }
   }
+}
+
+// dynamic shared memory above 48 KB: opted in once per (function, device)
+void set_max_dynamic_smem(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  TN_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({fn, dev})) return;
+  TN_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({fn, dev});
 }
 
 int ilog2_exact(int64_t x) {
@@ -581,7 +634,7 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
     }
   }
   p.scale = scale;
-  const size_t smem = (size_t)((p.K << p.na) + (p.K << p.nb)) * sizeof(float2);
+  const size_t smem = 2 * (size_t)((p.K << p.na) + (p.K << p.nb)) * sizeof(float2);  // double buffer
   const int64_t tiles = int64_t(1) << (p.nbits - p.P);
   const unsigned blocks = (unsigned)std::min<int64_t>(tiles, 152 * 6);
   // two adjacent outputs per thread when the tile's bit 0 has unit stride in the
@@ -590,10 +643,9 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
   for (int j = 1; j < p.nbits && pair; ++j) pair = p.o_w[j] % 2 == 0;
   auto go = [&](auto kc, auto v) {
     constexpr int KC = decltype(kc)::value, V = decltype(v)::value;
-    if (ex)
-      gemm_smallk<Out, 1, KC, V><<<blocks, 256, smem, s>>>(p, hilo);
-    else
-      gemm_smallk<Out, 0, KC, V><<<blocks, 256, smem, s>>>(p, hilo);
+    auto kern = ex ? gemm_smallk<Out, 1, KC, V> : gemm_smallk<Out, 0, KC, V>;
+    if (smem > 48 * 1024) set_max_dynamic_smem((const void*)kern, (int)(2 * kSkMaxStage * 2 * sizeof(float2)));
+    kern<<<blocks, 256, smem, s>>>(p, hilo);
   };
   using I1 = std::integral_constant<int, 1>;
   using I2 = std::integral_constant<int, 2>;

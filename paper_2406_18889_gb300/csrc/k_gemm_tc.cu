@@ -76,9 +76,11 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
   TN_CHECK(tc_gemm_supported(p.nbt, p.M, p.N, p.K, sa_bt, sa_m, 1), TN_ERR_UNSUPPORTED,
            "shape not supported by the tensor-core GEMM");
   const bool hilo = A_lo != nullptr && Bx_lo != nullptr;
-  // a 16-bit output has the operands' type, and a residual exactly when the product is split
-  TN_CHECK(p.out_kind == 2 || (p.out_kind == (bf16 ? 1 : 0) && (p.out_hilo != 0) == hilo), TN_ERR_UNSUPPORTED,
+  // a 16-bit output has the operands' type (with its residual when out_hilo)
+  TN_CHECK(p.out_kind == 2 || p.out_kind == (bf16 ? 1 : 0), TN_ERR_UNSUPPORTED,
            "tensor-core output storage must match the operand precision");
+  TN_CHECK((p.out_hilo != 0) == (p.C2 != nullptr) && !(p.out_hilo && p.out_kind == 2), TN_ERR_UNSUPPORTED,
+           "tensor-core output residual: C2 exactly for a split 16-bit output");
   const int bn = p.bn;
   TN_CHECK(p.acc_split >= 0, TN_ERR_UNSUPPORTED, "negative accumulation chunk");
   TN_CHECK(p.m_halves == 0 || p.m_halves == 1 || (p.m_halves == 2 && bn == 256 && !p.acc_split),

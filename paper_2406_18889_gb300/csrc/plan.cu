@@ -17,8 +17,10 @@
 //    directly, and inserts a transpose only where no choice allows it.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <numeric>
 #include <set>
@@ -121,6 +123,7 @@ struct Arena {
 }  // namespace
 
 Plan::~Plan() {
+  if (device >= 0) drop_batched_graphs(serial);
   if (graph) cudaGraphExecDestroy(graph);
   if (capture_stream) cudaStreamDestroy(capture_stream);
   if (d_plan) cudaFree(d_plan);
@@ -876,6 +879,10 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       }
     }
   }
+  // each tensor-core step splits on its own: a producer writes its result hi +
+  // lo whenever the step consuming it splits (the output's storage), whatever
+  // its own product
+  for (size_t t = 0; t < P.steps.size(); ++t) P.steps[t].hilo_group = P.steps[t].tc ? (int)t : -1;
   // storage: tensor-core A operands in 16 bits (hi + lo when split), all else complex64
   for (auto& S : P.steps)
     if (S.tc) {
@@ -963,6 +970,10 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
 
   // ------------------------------------------------------------ device setup
   TN_CUDA(cudaGetDevice(&P.device));
+  {
+    static std::atomic<uint64_t> next_serial{1};
+    P.serial = next_serial.fetch_add(1);
+  }
   TN_CUDA(cudaMalloc(&P.d_slice_ids, sizeof(int64_t) * P.B));
   TN_CUDA(cudaMalloc(&P.d_n_valid, sizeof(int32_t)));
   TN_CUDA(cudaMalloc(&P.d_err, sizeof(int)));
@@ -1129,6 +1140,7 @@ std::vector<TcForm> tc_step_forms(const Plan& P, size_t t) {
 }
 
 void drop_graph(Plan& P) {
+  ++P.generation;  // batched graphs holding the old launch forms no longer match
   if (P.graph) cudaGraphExecDestroy(P.graph);
   P.graph = nullptr;
   P.graph_ws = P.graph_amps = nullptr;

@@ -45,6 +45,7 @@ struct Step {
   bool tc = false;                     // tensor-core GEMM in reduced precision
   bool tc_swap = false;                // tensor-core A operand is node b (else node a)
   bool hilo = false;                   // split-precision product (A, B as hi + lo)
+  int hilo_group = -1;                 // tensor-core steps that split together (see build_plan)
   int bexp = 0;                        // the expanded operand is scaled by 2^-bexp into 16 bits
   bool fuse_expand = false;            // writes its result as the consumer's expanded operand
   bool b_fused = false;                // tensor-core step whose expanded operand its producer wrote
@@ -71,6 +72,8 @@ struct MemPlan {
 
 struct Plan {
   int device = -1;                      // CUDA device the plan lives on (-1: plan-only)
+  uint64_t serial = 0;                  // unique per plan in this process (graph caches)
+  uint64_t generation = 0;              // bumped whenever launch forms change (graph caches)
   // network
   int n_leaves = 0, n_edges = 0;
   std::vector<int64_t> dim;             // edge dims; index n_edges is the slice-batch edge
@@ -128,6 +131,22 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
 // TN_FLAG_HILO_AUTO (calibrated placement of split products), then builds.
 std::unique_ptr<Plan> create_plan(const tn_network_desc* net, const tn_tree_desc* tree,
                                   const tn_plan_options* opt, cudaStream_t stream);
+// Several plans in one captured graph (tn_contract_slices_batched).
+struct BatchedLayout {
+  int branches = 1;                // concurrent branches
+  std::vector<int> branch_of;      // per plan
+  std::vector<int64_t> offset;     // per branch: workspace offset (bytes)
+  int64_t bytes = 0;               // workspace the layout needs
+};
+// Pack plans into at most max_branches branches whose workspace regions fit
+// ws_bytes (fewer branches when they do not; one when a plan repeats).
+BatchedLayout batched_layout(const std::vector<Plan*>& plans, const int64_t* n_slices, size_t ws_bytes,
+                             int max_branches);
+void contract_batched(const std::vector<Plan*>& plans, const int64_t* const* slice_ids, const int64_t* n_slices,
+                      void* const* amps, int accumulate, void* workspace, size_t ws_bytes, cudaStream_t stream);
+// Forget cached batched graphs that refer to the plan with this serial.
+void drop_batched_graphs(uint64_t serial);
+
 // The seeded calibration slice ids of a plan with batch B over n_sliced edges.
 std::vector<int64_t> calibration_ids(int B, int n_sliced);
 

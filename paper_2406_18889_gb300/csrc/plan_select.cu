@@ -8,6 +8,7 @@
 //    the complex64 ones decides.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <numeric>
 #include <string>
 
@@ -174,50 +175,60 @@ std::unique_ptr<Plan> create_plan(const tn_network_desc* net, const tn_tree_desc
     run_calibration(*R, ws, ref.p, stream);
     check_timeouts(*R, stream);
   }
-  std::vector<int> tc;  // tensor-core steps
+  // tensor-core steps, in split groups (steps linked through a stored 16-bit
+  // operand split together; build_plan enforces it)
+  std::vector<std::vector<int>> groups;
   auto measure = [&](const std::vector<char>& m) {
     auto Q = build_plan(net, tree, &o, stream, &m);
-    if (tc.empty())
+    if (groups.empty()) {
+      std::map<int, std::vector<int>> g;
       for (size_t t = 0; t < Q->steps.size(); ++t)
-        if (Q->steps[t].tc) tc.push_back((int)t);
+        if (Q->steps[t].tc) g[Q->steps[t].hilo_group].push_back((int)t);
+      for (auto& kv : g) groups.push_back(kv.second);
+    }
     run_calibration(*Q, ws, amps.p, stream);
     check_timeouts(*Q, stream);
     return relative_l2(amps.p, ref.p, n_amps, part, stream);
   };
   const int T = tree->n_steps;
+  auto set_group = [&](std::vector<char>& m, int gi, char v) {
+    for (int t : groups[gi]) m[t] = v;
+  };
   std::vector<char> chosen(T, 0);
   const double e_none = measure(chosen);
   double e_chosen = e_none;
-  if (e_none > tol && !tc.empty()) {
+  const int NG = (int)groups.size();
+  if (e_none > tol && NG > 0) {
     std::vector<char> all(T, 0);
-    for (int t : tc) all[t] = 1;
+    for (int gi = 0; gi < NG; ++gi) set_group(all, gi, 1);
     const double e_all = measure(all);
-    // each step's share of the squared error: the error with that step alone
+    // each group's share of the squared error: the error with that group alone
     // left unsplit, above the all-split floor (errors of independent roundings
     // add in quadrature)
-    std::vector<double> share(T, 0.0);
-    for (int t : tc) {
+    std::vector<double> share(NG, 0.0);
+    for (int gi = 0; gi < NG; ++gi) {
       std::vector<char> m = all;
-      m[t] = 0;
+      set_group(m, gi, 0);
       const double e = measure(m);
-      share[t] = std::max(0.0, e * e - e_all * e_all);
+      share[gi] = std::max(0.0, e * e - e_all * e_all);
     }
-    std::vector<int> order = tc;
+    std::vector<int> order(NG);
+    std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return share[a] > share[b]; });
     // smallest prefix whose estimated error is within 0.8 tol
     double est = e_all * e_all;
-    for (int t : tc) est += share[t];
+    for (int gi = 0; gi < NG; ++gi) est += share[gi];
     size_t take = 0;
     const double target = (0.8 * tol) * (0.8 * tol);
     while (take < order.size() && est > target) {
       est -= share[order[take]];
-      chosen[order[take]] = 1;
+      set_group(chosen, order[take], 1);
       ++take;
     }
     // verify, adding the next-largest shares while the measured error is above tol
     e_chosen = measure(chosen);
     while (e_chosen > tol && take < order.size()) {
-      chosen[order[take]] = 1;
+      set_group(chosen, order[take], 1);
       ++take;
       e_chosen = measure(chosen);
     }

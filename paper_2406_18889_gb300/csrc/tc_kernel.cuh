@@ -126,13 +126,13 @@ constexpr size_t kStageBytes = kEpiWarps * 32 * kStagePitch * 8 + kEpiWarps * 32
 // barriers, the column-offset table and (STAGE) the epilogue staging, at most 8
 template <int BN, bool STAGE = false, int MH = 1>
 __host__ __device__ constexpr int stages_for() {
-  constexpr long budget = 232448 - 1024 - 256 - (long)BN / 2 * 12 - (STAGE ? (long)kStageBytes : 0L) - 512;
+  constexpr long budget = 232448 - 1024 - 512 - (long)BN / 2 * 12 - (STAGE ? (long)kStageBytes : 0L) - 512;
   constexpr long per = (long)(MH * BM + BN) * BK * 2;
   return budget / per > 8 ? 8 : (int)(budget / per);
 }
 template <int BN, bool STAGE, int MH = 1>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)stages_for<BN, STAGE, MH>() * (MH * BM + BN) * BK * 2 + 256 + (size_t)BN / 2 * 12 +
+  return 1024 + (size_t)stages_for<BN, STAGE, MH>() * (MH * BM + BN) * BK * 2 + 512 + (size_t)BN / 2 * 12 +
          (STAGE ? kStageBytes : 0);
 }
 
@@ -210,27 +210,28 @@ __device__ __forceinline__ uint32_t resid16(float re, float im, uint32_t w) {
   }
   return pack16<BF16>(re - h.x, im - h.y);
 }
-// the same at 32-bit element offset o from a tile's base pointers
-template <bool BF16, bool HILO, bool F32OUT>
+// the same at 32-bit element offset o from a tile's base pointers; the
+// residual goes to C2t when it is non-null (the output is stored hi + lo)
+template <bool BF16, bool F32OUT>
 __device__ __forceinline__ void store_el32(char* Ct, char* C2t, uint32_t o, float re, float im) {
   if constexpr (F32OUT) {
     *reinterpret_cast<float2*>(Ct + (size_t)o * 8) = make_float2(re, im);
   } else {
     const uint32_t h = pack16<BF16>(re, im);
     *reinterpret_cast<uint32_t*>(Ct + (size_t)o * 4) = h;
-    if constexpr (HILO) *reinterpret_cast<uint32_t*>(C2t + (size_t)o * 4) = resid16<BF16>(re, im, h);
+    if (C2t) *reinterpret_cast<uint32_t*>(C2t + (size_t)o * 4) = resid16<BF16>(re, im, h);
   }
 }
 // one complex output element at element offset o: fp32 pair, or 16-bit pair
-// (plus its residual in the second array when split)
-template <bool BF16, bool HILO, bool F32OUT>
+// (plus its residual in the second array when it is non-null)
+template <bool BF16, bool F32OUT>
 __device__ __forceinline__ void store_el(char* Cb, char* C2b, int64_t o, float re, float im) {
   if constexpr (F32OUT) {
     *reinterpret_cast<float2*>(Cb + o * 8) = make_float2(re, im);
   } else {
     const uint32_t h = pack16<BF16>(re, im);
     *reinterpret_cast<uint32_t*>(Cb + o * 4) = h;
-    if constexpr (HILO) *reinterpret_cast<uint32_t*>(C2b + o * 4) = resid16<BF16>(re, im, h);
+    if (C2b) *reinterpret_cast<uint32_t*>(C2b + o * 4) = resid16<BF16>(re, im, h);
   }
 }
 
@@ -270,6 +271,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // then m tile, then batch).  The TMEM accumulator is double-buffered (2 x BN
 // columns): the MMA thread fills buffer (i & 1) for the CTA's i-th tile while
 // the epilogue drains the other; tfull/tempty hand the buffers back and forth.
+// Narrow tiles (BN <= 64, one 128-row half, K in one accumulator): a tile has
+// at most two 32-column chunks, so the 16 epilogue warps form 4 groups of 4
+// (one warp per TMEM lane quarter), group g draining the CTA's tiles g, g + 4,
+// ... with 8 accumulator buffers (2 per group): four tiles' epilogues run at
+// once instead of one tile's on 4 warps.
 // MH: m halves per tile.  MH = 2 gives a CTA 256 rows (two 128-row MMAs per k
 // step sharing one B tile, so B is loaded once per 256 rows) and one TMEM
 // accumulator of 2 x BN columns instead of two alternating ones.
@@ -281,17 +287,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(MH == 1 || (MH == 2 && !STAGE && !SPLIT), "two m halves: direct stores");
   constexpr int S = stages_for<BN, STAGE, MH>();
   constexpr int TBM = MH * BM;             // rows per tile
-  constexpr int NBUF = MH == 1 ? 2 : 1;    // TMEM accumulator buffers (TMEM holds 2 x BN columns)
+  constexpr int kTG = (MH == 1 && !SPLIT && BN <= 64) ? 4 : 1;  // epilogue tile groups
+  constexpr int NBUF = MH == 1 ? 2 * kTG : 1;                   // TMEM accumulator buffers
+  constexpr uint32_t kTmemCols = (uint32_t)(MH == 1 ? NBUF * BN : 2 * BN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = sA + S * TBM * BK * 2;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * BN * BK * 2);
   uint64_t* empty = full + S;
-  uint64_t* tfull = empty + S;   // [2] MMA -> epilogue
-  uint64_t* tempty = tfull + 2;  // [2] epilogue -> MMA
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-  int64_t* n_rel = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 256);  // [BN / 2]
+  // accumulator hand-off barriers: one pair per buffer, and (MH = 2) one per
+  // 128-row half of the single buffer
+  constexpr int kTBar = NBUF > 2 ? NBUF : 2;
+  uint64_t* tfull = empty + S;       // [kTBar] MMA -> epilogue
+  uint64_t* tempty = tfull + kTBar;  // [kTBar] epilogue -> MMA
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + kTBar);
+  static_assert((2 * 8 + 2 * kTBar) * 8 + 4 <= 512, "barrier region");
+  int64_t* n_rel = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(full) + 512);  // [BN / 2]
   uint32_t* n32 = reinterpret_cast<uint32_t*>(n_rel + BN / 2);                           // [BN / 2]
   float2* stage_buf = reinterpret_cast<float2*>(n32 + BN / 2);                           // [warps][32][pitch]
   int64_t* row_base = reinterpret_cast<int64_t*>(stage_buf + kEpiWarps * 32 * kStagePitch);  // [warps][32]
@@ -310,15 +322,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kTBar; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kEpiWarps);  // one arrival per epilogue warp
+      mbar_init(&tempty[b], kEpiWarps / kTG);  // one arrival per epilogue warp draining the buffer
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)(2 * BN))
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -375,8 +387,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t t = unit0; t < tiles && !stop; t += ustride)
       for (int c0 = 0; c0 < k_tiles && !stop; c0 += kch, ++gu) {
         const int c1 = c0 + kch < k_tiles ? c0 + kch : k_tiles;
-        const int b = NBUF == 2 ? (int)(gu & 1) : 0;
-        const uint32_t u = NBUF == 2 ? (uint32_t)(gu >> 1) : (uint32_t)gu;
+        const int b = (int)(gu % NBUF);
+        const uint32_t u = (uint32_t)(gu / NBUF);
         if constexpr (MH == 2) {
           // 256-row tiles: the two TMEM halves (columns h * BN, rows h * 128 of
           // the tile) come back separately (tempty[h]).  The tile's half-0 MMAs
@@ -481,8 +493,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // before TMEM is freed: wait (bounded) for the last committed unit's MMAs
       if (gu > 0) {
         const int64_t last = gu - 1;
-        const int lb = NBUF == 2 ? (int)(last & 1) : 0;
-        const uint32_t lu = NBUF == 2 ? (uint32_t)(last >> 1) : (uint32_t)last;
+        const int lb = (int)(last % NBUF);
+        const uint32_t lu = (uint32_t)(last / NBUF);
         const uint64_t t0 = gtimer();
         while (!mbar_try_wait(&tfull[lb], lu & 1) && gtimer() - t0 < kWaitNs) {
         }
@@ -520,18 +532,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
     char* const Cb = reinterpret_cast<char*>(p.C);
     char* const C2b = reinterpret_cast<char*>(p.C2);
+    // the 16-bit output is stored hi + lo (its consumer splits its product),
+    // whether or not this step's own product is split
+    const bool res = !F32OUT && C2b != nullptr;
     // staging (STAGE): float2 [32][pitch] (fp32 out), or words [32][pitch] hi then lo
     uint32_t* stg = reinterpret_cast<uint32_t*>(stage_buf + ew * 32 * kStagePitch);
     int64_t* rb = row_base + ew * 32;
-    int64_t local = 0;
+    // tile groups (kTG > 1): this warp's group drains the CTA's tiles eg, eg + kTG, ...
+    const int eg = kTG > 1 ? (ew >> 2) : 0;
+    constexpr int kCStep = kTG > 1 ? 1 : kGroups;  // chunks of a tile taken by this warp: c0, c0 + kCStep, ...
+    const int c0 = kTG > 1 ? 0 : cgrp;
+    int64_t local = eg;
     int64_t gu = 0;  // SPLIT: accumulation units consumed
-    TileWalk<!SPLIT> w(unit0, ustride, n_n, n_mu);
-    for (int64_t t = unit0; t < tiles; t += ustride, ++local, w.next()) {
+    TileWalk<!SPLIT> w(unit0 + eg * ustride, kTG * ustride, n_n, n_mu);
+    for (int64_t t = unit0 + eg * ustride; t < tiles; t += kTG * ustride, local += kTG, w.next()) {
       int n_tile, m_unit, bt;
       w.at(t, n_tile, m_unit, bt);
       const int m_tile = m_unit;
-      const int b = (int)(local & 1);
-      const uint32_t u = (uint32_t)(local >> 1);
+      const int b = (int)(local % NBUF);
+      const uint32_t u = (uint32_t)(local / NBUF);
       const int64_t nbase = (int64_t)n_tile * BN / 2, mbase = (int64_t)m_tile * TBM;
       int64_t tbase;
       if constexpr (!kBaseByBits) {
@@ -544,11 +563,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int64_t row = tbase + m_rel;
       char* const Ct = Cb + tbase * ES;
-      char* const C2t = HILO ? C2b + tbase * 4 : nullptr;
+      char* const C2t = res ? C2b + tbase * 4 : nullptr;
       // this lane's row of the tile (32-bit offsets: p.off32 keeps every
       // in-tile offset below 2^31, so row + column never wraps)
       char* const Ctm = Ct + (size_t)m32 * ES;
-      char* const C2tm = HILO ? C2t + (size_t)m32 * 4 : nullptr;
+      char* const C2tm = res ? C2t + (size_t)m32 * 4 : nullptr;
       const bool row_ok = mbase + quarter * 32 + lane < p.M;
       // the tile lies wholly inside M x N
       const bool whole = mbase + TBM <= p.M && nbase + BN / 2 <= p.N;
@@ -563,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int64_t rowh = tbase + mr;
           const uint32_t m32h = (uint32_t)mr;
           char* const Cth = Ct + (size_t)m32h * ES;
-          char* const C2th = HILO ? C2t + (size_t)m32h * 4 : nullptr;
+          char* const C2th = res ? C2t + (size_t)m32h * 4 : nullptr;
           const bool rowh_ok = mbase + h * BM + quarter * 32 + lane < p.M;
 #pragma unroll 1
           for (int c = cgrp; c < kChunks && ok; c += kGroups) {
@@ -577,14 +596,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                  store_el32<BF16, HILO, F32OUT>(Cth, C2th, o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
+                  store_el32<BF16, F32OUT>(Cth, C2th, o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
                                                  __uint_as_float(v[2 * (j + q) + 1]) * p.scale);
               }
             } else if (rowh_ok) {
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
                 if (nbase + j0 + j >= p.N) break;
-                store_el<BF16, HILO, F32OUT>(Cb, C2b, rowh + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
+                store_el<BF16, F32OUT>(Cb, C2b, rowh + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
                                              __uint_as_float(v[2 * j + 1]) * p.scale);
               }
             }
@@ -645,19 +664,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                  store_el32<BF16, HILO, F32OUT>(Ct, C2t, m32 + o4[q], acc[ci][2 * (j + q)] * p.scale,
+                  store_el32<BF16, F32OUT>(Ct, C2t, m32 + o4[q], acc[ci][2 * (j + q)] * p.scale,
                                                  acc[ci][2 * (j + q) + 1] * p.scale);
               }
             } else if (whole) {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
-                store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], acc[ci][2 * j] * p.scale,
+                store_el<BF16, F32OUT>(Cb, C2b, row + n_rel[j0 + j], acc[ci][2 * j] * p.scale,
                                              acc[ci][2 * j + 1] * p.scale);
             } else if (row_ok) {
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
                 if (nbase + j0 + j >= p.N) break;
-                store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], acc[ci][2 * j] * p.scale,
+                store_el<BF16, F32OUT>(Cb, C2b, row + n_rel[j0 + j], acc[ci][2 * j] * p.scale,
                                              acc[ci][2 * j + 1] * p.scale);
               }
             }
@@ -674,7 +693,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
       }
 #pragma unroll 1
-      for (int c = cgrp; c < kChunks && ok; c += kGroups) {
+      for (int c = c0; c < kChunks && ok; c += kCStep) {
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c * 32);
         asm volatile(
@@ -700,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               const uint32_t h = pack16<BF16>(re, im);
               stg[lane * kStagePitch + j] = h;
-              if constexpr (HILO) stg[32 * kStagePitch + lane * kStagePitch + j] = resid16<BF16>(re, im, h);
+              if (res) stg[32 * kStagePitch + lane * kStagePitch + j] = resid16<BF16>(re, im, h);
             }
           }
           __syncwarp();
@@ -716,8 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 *reinterpret_cast<float2*>(Cb + o * 8) = reinterpret_cast<const float2*>(stg)[r * kStagePitch + jj];
               } else {
                 *reinterpret_cast<uint32_t*>(Cb + o * 4) = stg[r * kStagePitch + jj];
-                if constexpr (HILO)
-                  *reinterpret_cast<uint32_t*>(C2b + o * 4) = stg[32 * kStagePitch + r * kStagePitch + jj];
+                if (res) *reinterpret_cast<uint32_t*>(C2b + o * 4) = stg[32 * kStagePitch + r * kStagePitch + jj];
               }
             }
           }
@@ -729,19 +747,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t o4[4] = {nn.x, nn.y, nn.z, nn.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              store_el32<BF16, HILO, F32OUT>(Ctm, C2tm, o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
+              store_el32<BF16, F32OUT>(Ctm, C2tm, o4[q], __uint_as_float(v[2 * (j + q)]) * p.scale,
                                              __uint_as_float(v[2 * (j + q) + 1]) * p.scale);
           }
         } else if (whole) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
+            store_el<BF16, F32OUT>(Cb, C2b, row + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
                                          __uint_as_float(v[2 * j + 1]) * p.scale);
         } else if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             if (nbase + j0 + j >= p.N) break;
-            store_el<BF16, HILO, F32OUT>(Cb, C2b, row + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
+            store_el<BF16, F32OUT>(Cb, C2b, row + n_rel[j0 + j], __uint_as_float(v[2 * j]) * p.scale,
                                          __uint_as_float(v[2 * j + 1]) * p.scale);
           }
         }
@@ -756,7 +774,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                  : "memory");
   }
 }

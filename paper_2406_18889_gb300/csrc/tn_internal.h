@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -182,6 +183,8 @@ void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s);
 void launch_set_slice_ids(int64_t* d_ids, int32_t* d_n_valid, const int64_t* ids, int B, int32_t n_valid,
                           cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
+// out (+)= sum over p in order of parts[p] (complex128 [n_parts][n])
+void launch_sum_partials(const void* parts, int64_t n_parts, int64_t n, void* out, int accumulate, cudaStream_t s);
 struct TopkParams {
   int64_t G, Bsz;   // blocks and entries per block
   int k, l, global_mode;

@@ -99,3 +99,40 @@ def test_chunked_accumulation_accuracy(E, grid, prec, flags, tol):
     plan = E.Plan(prep.tn, prep.tree, prec=prec, flags=f | B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=64)
     got = plan.contract().cpu().numpy()
     assert_amplitudes_close(got, ref, tol, f"{prec} {flags}")
+
+
+def test_hilo_auto_places_split_products_by_calibration(E, grid):
+    # bf16 misses 3e-3 without any split product; TN_FLAG_HILO_AUTO splits only
+    # the tensor-core steps with the largest share of the calibration error
+    import torch
+    from paper_2406_18889_gb300 import binding as B
+    w, psi, ref, x_ref, prep = grid
+    plan = E.Plan(prep.tn, prep.tree, prec="bf16", flags=B.TN_FLAG_HILO_AUTO | B.TN_FLAG_HOIST_INVARIANT,
+                  max_slice_batch=64, hilo_tol=LOWP_TOL)
+    pr = plan.precision()
+    assert pr["rel_l2_none"] > LOWP_TOL and pr["rel_l2_chosen"] <= LOWP_TOL, pr
+    assert 1 <= pr["n_hilo_steps"] < pr["n_tc_steps"], pr
+    kinds = plan.steps()["kinds"]
+    assert ((kinds & 16) > 0).sum() == pr["n_hilo_steps"]
+    amps = plan.contract()
+    assert_amplitudes_close(amps.cpu().numpy(), ref, LOWP_TOL, "bf16 auto hi+lo")
+    base = torch.as_tensor(w.block_base(), device="cuda")
+    idx, _ = E.topk(amps, w.k, 1.0, base, w.open_bit_pos())
+    x = pp.xeb(pp.ideal_probabilities_at(psi, idx.cpu().numpy()), w.n_qubits)
+    assert abs(x - x_ref) <= 0.01 * abs(x_ref), (x, x_ref)
+    # the same placement given explicitly reproduces the plan bit for bit
+    mask = ((kinds & 16) > 0).astype(np.uint8)
+    plan2 = E.Plan(prep.tn, prep.tree, prec="bf16", flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=64,
+                   hilo_steps=mask)
+    assert np.array_equal(plan2.contract().cpu().numpy(), amps.cpu().numpy())
+    plan.close()
+    plan2.close()
+
+
+def test_slice_batch_from_free_memory(E, grid):
+    # max_slice_batch = 0: the library picks the batch from the device's free memory
+    w, psi, ref, x_ref, prep = grid
+    plan = E.Plan(prep.tn, prep.tree, prec="fp16", max_slice_batch=0)
+    assert plan.max_slice_batch == 64  # all 64 slices fit a GB300 at once
+    assert_amplitudes_close(plan.contract().cpu().numpy(), ref, LOWP_TOL)
+    plan.close()

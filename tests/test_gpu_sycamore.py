@@ -11,6 +11,7 @@ import pytest
 import workloads as W
 from oracle import einsum_tn as et
 from oracle import postprocess as pp
+from parity_checks import assert_amplitudes_close
 
 pytestmark = pytest.mark.gpu
 
@@ -34,26 +35,44 @@ def case():
     wires = [tn.wire_of_edge[e] for e in tree.sliced_edges]
     net = et.build_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
     ref = et.contract_each_slice(net, wires, ids)
-    return E, E.Prepared(tn, tree), ids, ref
+    eps32 = complex64_error(net, wires, ids[0], ref[0])
+    return E, E.Prepared(tn, tree), ids, ref, eps32
 
 
-def c64_tolerance(plan) -> float:
-    """FP32 bound for a sub-network of S pairwise steps: each step rounds its result to
-    FP32 (relative u = 2^-24) and errors add along the tree at worst linearly, so
-    relative L2 <= 2 u S.  This network has ~1050 steps (bound ~1.25e-4); the 1e-5 bar of
-    the 24-qubit workloads is kept there."""
-    return max(1e-5, 2 * 2.0 ** -24 * len(plan.steps()["k"]))
+def complex64_error(net, wires, sid, ref):
+    """Relative L2 error of an independent complex64 contraction of sub-network
+    `sid`: the oracle's own network, pairwise order and slicing, with every
+    tensor cast to complex64 so that each product and sum rounds to FP32
+    (NumPy's complex64 matmul).  It measures what complex64 arithmetic itself
+    allows on this network (~1050 pairwise steps)."""
+    sl = [et._as_label(x) for x in wires]
+    arrs, labs = et._fix(net.arrays, net.labels, net.dims, sl, sid)
+    c32 = et.contract_arrays([a.astype(np.complex64) for a in arrs], labs, net.dims, net.output)
+    got = et._as_blocks(net, c32.astype(np.complex128))
+    return pp.relative_l2(got, ref)
 
 
-@pytest.mark.parametrize("prec", ["c64", "fp16"])
+def test_complex64_arithmetic_misses_1e5_at_this_shape(case):
+    # the reading behind the complex64 bar below: complex64 arithmetic itself
+    # errs by more than 1e-5 on this network (measured ~1.7e-5)
+    E, prep, ids, ref, eps32 = case
+    assert 1e-5 < eps32 < 1e-4, eps32
+
+
+@pytest.mark.parametrize("prec", ["c64", "fp16+hilo+fine", "fp16"])
 def test_sycamore_shaped_slices(case, prec):
-    E, prep, ids, ref = case
-    plan = E.Plan(prep.tn, prep.tree, prec=prec, max_slice_batch=4)
-    tol = c64_tolerance(plan) if prec == "c64" else 3e-3
+    # complex64 and the complex64-accuracy tensor-core mode: within 2.5x the
+    # error of the independent complex64 contraction (the 1e-5 bar of the
+    # 24-qubit workloads is beyond complex64 arithmetic here); fp16: 3e-3
+    from paper_2406_18889_gb300 import binding as B
+    E, prep, ids, ref, eps32 = case
+    flags = B.TN_FLAG_HILO | B.TN_FLAG_FINE_ACC if "hilo" in prec else 0
+    plan = E.Plan(prep.tn, prep.tree, prec=prec[:4] if prec != "c64" else "c64", flags=flags, max_slice_batch=4)
+    tol = 3e-3 if prec == "fp16" else max(1e-5, 2.5 * eps32)
     for i, sid in enumerate(ids):
         got = plan.contract([sid]).cpu().numpy()
         assert np.abs(ref[i]).max() < 1e-10  # deep below the fp16 range
-        assert pp.relative_l2(got, ref[i]) <= tol, (prec, sid)
+        assert_amplitudes_close(got, ref[i], tol, f"{prec} slice {sid}")
     plan.close()
 
 
@@ -83,4 +102,4 @@ def test_sycamore_20_cycles_fp16_agrees_with_complex64():
         out[prec] = plan.contract(ids).cpu().numpy()
         plan.close()
     assert np.abs(out["c64"]).max() > 0
-    assert pp.relative_l2(out["fp16"], out["c64"]) <= 3e-3
+    assert_amplitudes_close(out["fp16"], out["c64"], 3e-3, "fp16 vs complex64, 20 cycles")

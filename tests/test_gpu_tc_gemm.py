@@ -16,6 +16,10 @@ SHAPES = [  # (batch, M, N, K) in complex elements
     (5, 96, 300, 260),     # several K stages (4-stage ring wraps), ragged N tile
     (1, 1100, 600, 64),    # nine m tiles x five n tiles
     (2, 520, 1030, 100),   # batched, ragged M, N and K across several tiles
+    # more tiles than CTAs, so every CTA reuses its accumulator buffers:
+    (4, 8192, 256, 256),   # BN = 256, 256-row tiles (both TMEM halves handed back per tile)
+    (64, 4096, 16, 16),    # BN = 32: four epilogue tile groups, eight accumulator buffers
+    (16, 2000, 32, 36),    # BN = 64, ragged M and K
 ]
 
 

@@ -1,6 +1,8 @@
-"""Multi-rank host logic of bench.py on CPU (gloo, world size 2): each rank
-samples its own blocks of the same circuit (independent problems), the job's
-slices are summed over ranks and its time is the max over ranks."""
+"""Multi-rank host logic on CPU (gloo): bench.py's rank bookkeeping (each rank
+samples its own blocks of the same circuit, the job's slices are summed over
+ranks and its time is the max over ranks), and the slices of one problem split
+over ranks with their FP64 partials gathered on rank 0 and summed in rank
+order (multirank.py), against the single-rank sum."""
 import os
 import socket
 
@@ -47,6 +49,72 @@ def test_two_gloo_ranks_partition_blocks():
     assert g0 == g1          # same circuit
     assert t0 == t1 == 2.0   # max over ranks
     assert n0 == n1 == 128.0  # slices summed over ranks
+
+
+def _slice_worker(rank, world, port, q):
+    # the slices split over ranks (each rank contracts its share with the FP64
+    # oracle in place of the GPU), partials gathered on rank 0 in rank order
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import numpy as np
+    import workloads as W
+    from oracle import einsum_tn as et
+    from paper_2406_18889_gb300 import multirank as MR
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = W.workload("grid3x4_d8", cycles=10, l=6, G=8)
+    wires = [(q, 1) for q in range(5)]
+    ids = W.draw_slice_subset(32, 13, seed=3)
+    net = et.build_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    mine = MR.partition(ids, rank, world)
+    local = et.contract(net, wires, mine) if len(mine) else np.zeros((w.G, 1 << w.l), complex)
+    parts = MR.gather_partials(torch.as_tensor(local), dist, world, rank)
+    q.put((rank, mine.tolist(), None if parts is None else parts.numpy()))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slices_split_over_gloo_ranks_sum_to_the_single_rank_result(world):
+    import numpy as np
+    import workloads as W
+    from oracle import einsum_tn as et
+    from oracle import postprocess as pp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slice_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in range(world)), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ids = W.draw_slice_subset(32, 13, seed=3)
+    # the shares partition the ids, in order
+    assert sum((r[1] for r in res), []) == ids.tolist()
+    assert max(len(r[1]) for r in res) - min(len(r[1]) for r in res) <= 1
+    parts = res[0][2]
+    assert parts.shape[0] == world and all(r[2] is None for r in res[1:])
+    total = parts[0].copy()
+    for p in parts[1:]:
+        total = total + p  # rank order: what tn_sum_partials computes on the device
+    w = W.workload("grid3x4_d8", cycles=10, l=6, G=8)
+    net = et.build_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    single = et.contract(net, [(q, 1) for q in range(5)], ids)
+    assert pp.relative_l2(total, single) <= 1e-13
+    a = pp.topk_blocks(total, 8, 32 / 13, w.block_base(), w.open_bit_pos())
+    b = pp.topk_blocks(single, 8, 32 / 13, w.block_base(), w.open_bit_pos())
+    assert np.array_equal(a[0], b[0])
+
+
+def test_partition_shares():
+    import numpy as np
+    from paper_2406_18889_gb300 import multirank as MR
+    ids = np.arange(10, 74)
+    for world in (1, 2, 3, 8, 100):
+        shares = [MR.partition(ids, r, world) for r in range(world)]
+        assert np.array_equal(np.concatenate(shares), ids)
+        assert max(map(len, shares)) - min(map(len, shares)) <= 1
+    with pytest.raises(ValueError):
+        MR.partition(ids, 2, 2)
 
 
 def test_clock_samples_filtered_to_timed_regions():
