@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(256) gemm_tiled(GemmParams p, float scale, boo
   TO* __restrict__ C2 = (TO*)p.C2;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TN;
+  // blockIdx.x walks the (m tile, n tile) grid, n tile fastest
+  const int64_t n_tiles = (p.N + TN - 1) / TN;
+  const int64_t m0 = (int64_t)(blockIdx.x / n_tiles) * TM, n0 = (int64_t)(blockIdx.x % n_tiles) * TN;
   const bool a_kc = flags & 1;
   const bool b_nc = flags & 2;
   for (int i = tid; i < TM; i += 256) {
@@ -365,7 +367,13 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
   __shared__ uint32_t sel_lo[256], sel_hi[16];
   __shared__ int64_t off_lo[256], off_hi[16];
   __shared__ int64_t a_hi[8], b_hi[8];
+  __shared__ int64_t w_a[kMaxBits], w_b[kMaxBits], w_o[kMaxBits];  // position-bit weights (lanes read them per bit)
   constexpr int lgK = KC == 1 ? 0 : KC == 2 ? 1 : 2;
+  for (int j = threadIdx.x; j < p.nbits; j += blockDim.x) {
+    w_a[j] = p.a_w[j];
+    w_b[j] = p.b_w[j];
+    w_o[j] = p.o_w[j];
+  }
   constexpr int sh = V - 1;  // tile bits below the thread index
   const int na_n = KC << p.na, nb_n = KC << p.nb;
   const int buf_n = na_n + nb_n;  // buffer q starts at staged + q * buf_n
@@ -431,9 +439,9 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
     int64_t a = 0, b = 0, o = 0;
     for (int j = p.P + lane; j < p.nbits; j += 32)
       if ((t >> (j - p.P)) & 1) {
-        a += p.a_w[j];
-        b += p.b_w[j];
-        o += p.o_w[j];
+        a += w_a[j];
+        b += w_b[j];
+        o += w_o[j];
       }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
@@ -447,16 +455,25 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
       tile_base[slot][2] = o;
     }
   };
-  // queue the asynchronous copies of one tile's staged entries into buffer q
+  // queue the asynchronous copies of one tile's staged entries into buffer q.
+  // Entry s = (u << lgK) | k is read from global memory in s order and stored
+  // k-major (k * 2^na + u), so that the lanes of a warp, which take
+  // consecutive u, read shared memory without bank conflicts
+  const int na_u = 1 << p.na, nb_u = 1 << p.nb;
+  const int a_dst = (threadIdx.x & (KC - 1)) * na_u + (threadIdx.x >> lgK);
+  const int b_dst = (threadIdx.x & (KC - 1)) * nb_u + (threadIdx.x >> lgK);
   auto stage = [&](int slot, int q) {
     const int64_t a0 = tile_base[slot][0] + a_lo, b0 = tile_base[slot][1] + b_lo;
     float2* As = staged + q * buf_n;
     float2* Bs = As + na_n;
-    for (int r = 0, i = threadIdx.x; i < na_n; ++r, i += 256) cp_async8(As + i, p.A + a0 + a_hi[r]);
-    for (int r = 0, i = threadIdx.x; i < nb_n; ++r, i += 256) cp_async8(Bs + i, p.B + b0 + b_hi[r]);
+    for (int r = 0, i = threadIdx.x; i < na_n; ++r, i += 256)
+      cp_async8(As + a_dst + (r << (8 - lgK)), p.A + a0 + a_hi[r]);
+    for (int r = 0, i = threadIdx.x; i < nb_n; ++r, i += 256)
+      cp_async8(Bs + b_dst + (r << (8 - lgK)), p.B + b0 + b_hi[r]);
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   const int64_t G = gridDim.x;
+  __syncthreads();  // the weight tables
   if (threadIdx.x < 32 && (int64_t)blockIdx.x < ntiles) bases(blockIdx.x, 0);
   __syncthreads();
   if ((int64_t)blockIdx.x < ntiles) stage(0, 0);
@@ -487,11 +504,11 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
       float2 r[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const float2* a = As + ((ua | (v ? a_v : 0u)) << lgK);
-        const float2* b = Bs + ((ub | (v ? b_v : 0u)) << lgK);
+        const float2* a = As + (ua | (v ? a_v : 0u));
+        const float2* b = Bs + (ub | (v ? b_v : 0u));
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < KC; ++k) cmac(acc, a[k], b[k]);
+        for (int k = 0; k < KC; ++k) cmac(acc, a[k * na_u], b[k * nb_u]);
         r[v] = make_float2(acc.x * p.scale, acc.y * p.scale);
       }
       store_v<Out, MODE, V>(p, ot + off_hi[h], r, hilo);
@@ -542,11 +559,10 @@ bool fastest_unit(const Runs& r) { return r.n > 0 && r.st[0] == 1; }
 template <int TM, int TN, int TK, int TY, int TX, class In, class Out>
 void launch_tiled(const GemmParams& p, float scale, bool hilo, cudaStream_t s) {
   int64_t gx = (p.N + TN - 1) / TN, gy = (p.M + TM - 1) / TM;
-  TN_CHECK(gx < (1LL << 31) && gy < 65536, TN_ERR_UNSUPPORTED, "GEMM grid too large");
+  TN_CHECK(gx * gy < (1LL << 31), TN_ERR_UNSUPPORTED, "GEMM grid too large");
   unsigned gz = (unsigned)std::min<int64_t>(p.nbt, 65535);
   const int flags = (fastest_unit(p.a_k) || !fastest_unit(p.a_m) ? 1 : 0) | (fastest_unit(p.b_n) ? 2 : 0);
-  gemm_tiled<TM, TN, TK, TY, TX, In, Out><<<dim3((unsigned)gx, (unsigned)gy, gz), 256, 0, s>>>(p, scale, hilo,
-                                                                                             flags);
+  gemm_tiled<TM, TN, TK, TY, TX, In, Out><<<dim3((unsigned)(gx * gy), 1, gz), 256, 0, s>>>(p, scale, hilo, flags);
 }
 
 // Small-K launch; `ex` non-null: the result goes to that expanded operand.
@@ -644,7 +660,9 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
   auto go = [&](auto kc, auto v) {
     constexpr int KC = decltype(kc)::value, V = decltype(v)::value;
     auto kern = ex ? gemm_smallk<Out, 1, KC, V> : gemm_smallk<Out, 0, KC, V>;
-    if (smem > 48 * 1024) set_max_dynamic_smem((const void*)kern, (int)(2 * kSkMaxStage * 2 * sizeof(float2)));
+    // the double buffer (up to 64 KB) plus the static tables can pass the 48 KB
+    // a launch may use without the opt-in
+    set_max_dynamic_smem((const void*)kern, (int)(2 * kSkMaxStage * 2 * sizeof(float2)));
     kern<<<blocks, 256, smem, s>>>(p, hilo);
   };
   using I1 = std::integral_constant<int, 1>;

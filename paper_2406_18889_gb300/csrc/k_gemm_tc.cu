@@ -91,6 +91,19 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     const int64_t sn = p.c_n.n > 0 ? p.c_n.st[0] : big, sm = p.c_m.n > 0 ? p.c_m.st[0] : big;
     // only for write-heavy tiles (up to four k tiles); deeper tiles hide the per-row stores
     p.stage_n = (sn < sm && 2 * p.K <= 4 * BK && p.m_halves != 2) ? 1 : 0;
+    // 16-byte stores along n instead: n's first run has unit stride and holds
+    // whole groups of VN outputs, every other stride keeps groups 16-byte
+    // aligned, and the rows sit VN apart (a warp's 32 rows then write one
+    // contiguous 512-byte span per store)
+    const int64_t VN = p.out_kind == 2 ? 2 : 4;
+    bool vec = p.c_n.n > 0 && p.c_n.st[0] == 1 && (int64_t(1) << p.c_n.lg[0]) % VN == 0 && sm == VN &&
+               p.acc_split == 0;
+    for (const Runs* R : {&p.c_n, &p.c_m, &p.c_bt})
+      for (int r = (R == &p.c_n ? 1 : 0); r < R->n && vec; ++r) vec = R->st[r] % VN == 0;
+    vec = vec && (reinterpret_cast<uintptr_t>(p.C) & 15) == 0 &&
+          (!p.out_hilo || (reinterpret_cast<uintptr_t>(p.C2) & 15) == 0);
+    p.vec = vec ? 1 : 0;
+    if (vec) p.stage_n = 0;
   }
   const int64_t tbm = (p.m_halves == 2 ? 2 : 1) * (int64_t)BM;  // rows per tile
   TN_CHECK(p.nbt * ((p.M + tbm - 1) / tbm) * ((2 * p.N + bn - 1) / bn) < (int64_t(1) << 31) &&
@@ -307,6 +320,21 @@ __global__ void diff_t_kernel(const float2* a, const float2* b, int64_t nbt, int
   }
   atomicMax(max_diff, __float_as_uint(md));
 }
+// the same for a result stored [bt][n / 2][m][n % 2] (pairs of n outputs
+// contiguous, rows two apart: the 16-byte store layout of fp32 outputs)
+__global__ void diff_il_kernel(const float2* a, const float2* b, int64_t nbt, int64_t M, int64_t N,
+                               unsigned* max_diff) {
+  float md = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbt * M * N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bt = i / (M * N), r = i - bt * M * N, m = r / N, n = r - m * N;
+    const float2 x = a[bt * M * N + (n / 2) * 2 * M + m * 2 + (n % 2)];
+    const float dx = x.x - b[i].x, dy = x.y - b[i].y;
+    md = fmaxf(md, sqrtf(dx * dx + dy * dy));
+    if (!(x.x == x.x) || !(x.y == x.y)) md = 3.0e38f;
+  }
+  atomicMax(max_diff, __float_as_uint(md));
+}
 }  // namespace
 
 double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
@@ -380,6 +408,31 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
       p.m_halves = v == 1 ? 2 : 1;
       launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
       diff_t_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt, M, N, mx);
+    }
+    // and (M, N powers of two) pairs of n outputs contiguous with rows two
+    // apart, which the epilogue writes with 16-byte stores
+    auto pow2 = [](int64_t x) { return x > 0 && (x & (x - 1)) == 0; };
+    if (pow2(M) && pow2(N) && N >= 2) {
+      int lgM = 0, lgN = 0;
+      while ((int64_t(1) << lgM) < M) ++lgM;
+      while ((int64_t(1) << lgN) < N) ++lgN;
+      p.c_m = single_run(M, 2);
+      p.c_n.n = lgN > 1 ? 2 : 1;
+      p.c_n.lg[0] = 1;
+      p.c_n.st[0] = 1;
+      if (lgN > 1) {
+        p.c_n.lg[1] = (int8_t)(lgN - 1);
+        p.c_n.st[1] = 2 * M;
+      }
+      p.c_bt = single_run(nbt, M * N);
+      for (int v = 0; v < 2; ++v) {
+        if (v == 1 && p.bn != 256) break;
+        TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
+        p.acc_split = 0;
+        p.m_halves = v == 1 ? 2 : 1;
+        launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
+        diff_il_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt, M, N, mx);
+      }
     }
     unsigned h[2] = {0, 0};
     TN_CUDA(cudaMemcpyAsync(h, mx, 8, cudaMemcpyDeviceToHost, s));

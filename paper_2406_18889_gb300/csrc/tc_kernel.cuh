@@ -235,6 +235,28 @@ __device__ __forceinline__ void store_el(char* Cb, char* C2b, int64_t o, float r
   }
 }
 
+// 16 bytes of consecutive complex outputs at 32-bit element offset o (16-byte
+// aligned): 4 values as 16-bit pairs (and their residuals to C2t when it is
+// non-null), or 2 values as fp32 pairs; v holds (re, im) of each, unscaled
+template <bool BF16, bool F32OUT>
+__device__ __forceinline__ void store_vec16(char* Ct, char* C2t, uint32_t o, const uint32_t* v, float scale) {
+  if constexpr (F32OUT) {
+    *reinterpret_cast<float4*>(Ct + (size_t)o * 8) =
+        make_float4(__uint_as_float(v[0]) * scale, __uint_as_float(v[1]) * scale, __uint_as_float(v[2]) * scale,
+                    __uint_as_float(v[3]) * scale);
+  } else {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float re = __uint_as_float(v[2 * q]) * scale, im = __uint_as_float(v[2 * q + 1]) * scale;
+      h[q] = pack16<BF16>(re, im);
+      if (C2t) l[q] = resid16<BF16>(re, im, h[q]);
+    }
+    *reinterpret_cast<uint4*>(Ct + (size_t)o * 4) = make_uint4(h[0], h[1], h[2], h[3]);
+    if (C2t) *reinterpret_cast<uint4*>(C2t + (size_t)o * 4) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 // 32 consecutive accumulator columns of this warp's TMEM lane quarter
 __device__ __forceinline__ void tmem_ld32_h(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
@@ -589,7 +611,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t v[32];
             tmem_ld32_h(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * BN + c * 32), v);
             const int j0 = c * 16;
-            if (whole && p.off32) {
+            if (whole && p.off32 && p.vec) {
+              constexpr int VN = F32OUT ? 2 : 4;
+#pragma unroll
+              for (int j = 0; j < 16; j += VN) store_vec16<BF16, F32OUT>(Cth, C2th, n32[j0 + j], v + 2 * j, p.scale);
+            } else if (whole && p.off32) {
 #pragma unroll
               for (int j = 0; j < 16; j += 4) {
                 const uint4 nn = *reinterpret_cast<const uint4*>(n32 + j0 + j);
@@ -740,6 +766,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           __syncwarp();
+        } else if (whole && p.off32 && p.vec) {
+          // runs of VN outputs consecutive along n: one 16-byte store each
+          constexpr int VN = F32OUT ? 2 : 4;
+#pragma unroll
+          for (int j = 0; j < 16; j += VN) store_vec16<BF16, F32OUT>(Ctm, C2tm, n32[j0 + j], v + 2 * j, p.scale);
         } else if (whole && p.off32) {
 #pragma unroll
           for (int j = 0; j < 16; j += 4) {

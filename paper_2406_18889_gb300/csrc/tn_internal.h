@@ -125,6 +125,7 @@ struct TcGemmParams {
   int stage_n;                // write tiles out along n (n is the output's contiguous index)
   int acc_split;              // > 0: accumulate K in chunks of this many k tiles, summed in FP32 registers
   int off32;                  // every offset inside a tile (from its base) fits in 32 bits (set by the launcher)
+  int vec;                    // 16-byte stores of consecutive n outputs (set by the launcher)
   int m_halves;               // 2: 256-row tiles, two 128-row MMAs sharing each B tile (tile width 256 only)
 };
 

@@ -21,10 +21,9 @@ within 15% of ln 2^15 and the MCMC XEB within 0.35 F_num + 0.05 of F_num
 (2^16 correlated samples).
 
 The paper-scale case (5x6 grid, 30 qubits, k = 2^15 of 2^30; a 16 GiB state
-vector and ~4 minutes on the host) runs when TN_PAPER_SCALE=1.
+vector, ~3 minutes on the host cores) runs in the default GPU suite too.
 """
 import math
-import os
 
 import numpy as np
 import pytest
@@ -127,7 +126,6 @@ def test_topk_amplification_24_qubits(sv_grid4x6):
     _check(rows, 24, 1 << 9)
 
 
-@pytest.mark.skipif(os.environ.get("TN_PAPER_SCALE") != "1", reason="paper-scale study: set TN_PAPER_SCALE=1")
 def test_topk_amplification_30_qubits_paper_scale():
     E = _engine()
     w = W.workload("grid4x6_d14", rows=5, cols=6, l=30, G=1, seed=SEED0 + 6)
