@@ -625,7 +625,8 @@ def run_uneven(args):
 
 def run_sycamore(args):
     """The 53-qubit Sycamore-shaped circuit, 20 cycles (l = 10 open qubits, G = 16
-    blocks, k = 1 per block): a bisection-search plan under a 2^32-element cap,
+    blocks, k = 1 per block): a bisection-search plan (refined by subtree
+    reconfiguration unless --path greedy) under a 2^32-element cap,
     a few seeded slices timed one by one, and the extrapolated time to 1e6
     samples at the fidelity whose top-1 XEB is 0.002 (Eq. 4: F = 0.002 /
     (H_1024 - 1); slices needed per block batch = F x 2^(sliced bonds))."""
@@ -644,7 +645,8 @@ def run_sycamore(args):
     tree = P.plan_tree(tn, cap_log2=32, restarts=1, method="partition", refine=refined,
                        workers=host_cores() if refined else 0)
     plan_s = time.perf_counter() - t0
-    plan = E.Plan(tn, tree, prec=args.prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=1)
+    flags = B.TN_FLAG_HOIST_INVARIANT | (B.TN_FLAG_HILO_AUTO if args.hilo_auto and args.prec != "c64" else 0)
+    plan = E.Plan(tn, tree, prec=args.prec, flags=flags, max_slice_batch=1, hilo_tol=2e-3)
     s = len(tree.sliced_edges)
     ids = W.draw_slice_subset(1 << min(s, 62), 1 + args.steps, seed=20)
     amps = plan.contract(ids[:1])  # warm-up: graph capture
@@ -658,6 +660,18 @@ def run_sycamore(args):
     torch.cuda.synchronize()
     t_slice = e0.elapsed_time(e1) / args.steps / 1e3
     useful = plan.info["useful_flops_per_slice"]
+    # error of the timed precision on the last timed slice, against the complex64 path
+    precision = None
+    if args.prec != "c64":
+        one = plan.contract(ids[-1:])
+        plan64 = E.Plan(tn, tree, prec="c64", flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=1)
+        ref = plan64.contract(ids[-1:])
+        plan64.close()
+        torch.cuda.synchronize()
+        rel = float(torch.linalg.vector_norm(one - ref) / torch.linalg.vector_norm(ref))
+        pr = plan.precision()
+        precision = {"rel_l2_vs_complex64_one_slice": rel, "split_steps": pr["n_hilo_steps"],
+                     "tensor_core_steps": pr["n_tc_steps"], "calibration_rel_l2": pr["rel_l2_chosen"]}
     F = 0.002 / (sum(1.0 / j for j in range(1, 1025)) - 1.0)
     slices_per_batch = F * 2.0 ** s
     batches = 1e6 / w.G
@@ -668,7 +682,7 @@ def run_sycamore(args):
                                                   "G = 16, k = 1 per block", "cap_log2": 32, "sliced_bonds": s,
                                         "path": "recursive bisection + subtree reconfiguration" if refined
                                         else "recursive bisection"},
-        "useful_tflops": useful / t_slice / 1e12, "useful_flops_per_slice": useful,
+        "useful_tflops": useful / t_slice / 1e12, "useful_flops_per_slice": useful, "precision": precision,
         "path_cost_complex_macs": tree.cost_per_slice * 2.0 ** s, "host_planning_s": plan_s,
         "extrapolation_1e6_samples": {"fidelity_F": F, "slices_per_block_batch": slices_per_batch,
                                       "block_batches": batches,

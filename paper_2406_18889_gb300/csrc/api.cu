@@ -193,7 +193,7 @@ tn_status tn_plan_steps(tn_plan_t plan, int32_t max_steps, int64_t* batch, int64
       if (k) k[t] = S.gp.K;
       if (kinds) kinds[t] = (S.variant ? 1 : 0) | (S.post_perm ? 2 : 0) | (S.hoisted ? 4 : 0) | (S.tc ? 8 : 0) |
                                (S.hilo ? 16 : 0) | (S.fuse_expand ? 32 : 0) | (S.b_fused ? 64 : 0) |
-                               (S.micro ? 128 : 0);
+                               (S.micro ? 128 : 0) | (S.pair_rows ? 256 : 0);
     }
   });
 }

@@ -28,6 +28,7 @@
 //  * direct: one thread per output element, for the remaining shapes too
 //    small for a tile.
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <set>
 #include <type_traits>
@@ -516,6 +517,121 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
   }
 }
 
+// ------------------------------------------------------------------ rows
+// Small K with few outputs per row (K <= 4, N <= 8, the result written in
+// place): thread t takes rows (bt, m) of the step, loads the row's K entries
+// of A once (16-byte loads when they are contiguous), forms all N outputs in
+// registers from B (held in registers when the step has one batch) and stores
+// them (pairs when consecutive n are adjacent).  Row r = bt * M + m is
+// addressed bit-linearly: its low 8 bits (the thread) by a register part,
+// the rest (the chunk of 256 rows) by a warp reduction over per-bit weights.
+struct RowsK {
+  const float2* A;
+  const float2* B;
+  void* C;
+  void* C2;
+  int nbits;                               // log2 of the rows
+  int64_t a_w[kMaxBits], c_w[kMaxBits], b_w[kMaxBits];  // row bit -> A / C / B offset
+  int64_t ak[4], bk[4];                    // contracted-index offsets
+  int64_t cn[8], bn[8];                    // output / B offsets of n
+  int a_vec;                               // a row's K entries contiguous and 16-byte aligned
+  int b_fixed;                             // one batch: B the same for every row
+  int c_pairs;                             // n = 2i, 2i + 1 adjacent and pair-aligned
+  float scale;
+};
+
+template <class Out, int KC, int NC>
+__global__ void __launch_bounds__(256) gemm_rows(RowsK p, bool hilo) {
+  __shared__ int64_t w[3][kMaxBits];
+  for (int j = threadIdx.x; j < p.nbits; j += blockDim.x) {
+    w[0][j] = p.a_w[j];
+    w[1][j] = p.c_w[j];
+    w[2][j] = p.b_w[j];
+  }
+  __syncthreads();
+  using TO = typename Out::T;
+  TO* C = reinterpret_cast<TO*>(p.C);
+  TO* C2 = reinterpret_cast<TO*>(p.C2);
+  const int lane = threadIdx.x & 31;
+  // the thread's part of the row offsets (row bits 0..7)
+  int64_t a_t = 0, c_t = 0, b_t = 0;
+  for (int j = 0; j < 8 && j < p.nbits; ++j)
+    if ((threadIdx.x >> j) & 1) {
+      a_t += w[0][j];
+      c_t += w[1][j];
+      b_t += w[2][j];
+    }
+  float2 bf[KC][NC];
+  if (p.b_fixed) {
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+#pragma unroll
+      for (int n = 0; n < NC; ++n) bf[k][n] = __ldg(p.B + p.bk[k] + p.bn[n]);
+  }
+  const int64_t rows = int64_t(1) << p.nbits;
+  const int64_t chunks = (rows + 255) >> 8;
+  for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+    // chunk offsets: lane j sums the weights of row bits 8 + j, 40 + j
+    int64_t a0 = 0, c0 = 0, b0 = 0;
+    for (int j = 8 + lane; j < p.nbits; j += 32)
+      if ((c >> (j - 8)) & 1) {
+        a0 += w[0][j];
+        c0 += w[1][j];
+        b0 += w[2][j];
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+      b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+    }
+    if ((c << 8) + threadIdx.x >= rows) continue;
+    const int64_t ao = a0 + a_t, co = c0 + c_t;
+    float2 a[KC];
+    if (KC >= 2 && p.a_vec) {
+#pragma unroll
+      for (int k = 0; k < KC; k += 2) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(p.A + ao + k));
+        a[k] = make_float2(v.x, v.y);
+        a[k + 1] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < KC; ++k) a[k] = __ldcs(p.A + ao + p.ak[k]);
+    }
+    float2 r[NC];
+#pragma unroll
+    for (int n = 0; n < NC; ++n) r[n] = make_float2(0.f, 0.f);
+    if (p.b_fixed) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+#pragma unroll
+        for (int n = 0; n < NC; ++n) cmac(r[n], a[k], bf[k][n]);
+    } else {
+      const int64_t bo = b0 + b_t;
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+#pragma unroll
+        for (int n = 0; n < NC; ++n) cmac(r[n], a[k], __ldg(p.B + bo + p.bk[k] + p.bn[n]));
+    }
+#pragma unroll
+    for (int n = 0; n < NC; ++n) r[n] = make_float2(r[n].x * p.scale, r[n].y * p.scale);
+    if (NC >= 2 && p.c_pairs) {
+      SmallK q{};  // store_v reads only the destination pointers
+      q.C = p.C;
+      q.C2 = p.C2;
+#pragma unroll
+      for (int n = 0; n < NC; n += 2) {
+        const float2 v2[2] = {r[n], r[n + 1]};
+        store_v<Out, 0, 2>(q, co + p.cn[n], v2, hilo);
+      }
+    } else {
+#pragma unroll
+      for (int n = 0; n < NC; ++n) store_out<Out>(C, C2, co + p.cn[n], r[n], hilo);
+    }
+  }
+}
+
 // dynamic shared memory above 48 KB: opted in once per (function, device)
 void set_max_dynamic_smem(const void* fn, int bytes) {
   static std::mutex mu;
@@ -526,6 +642,21 @@ void set_max_dynamic_smem(const void* fn, int bytes) {
   if (done.count({fn, dev})) return;
   TN_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done.insert({fn, dev});
+}
+
+// CTAs of 256 threads resident per SM for a function and its dynamic shared
+// memory (cached: the launch sequence of a plan asks again and again)
+int resident_blocks(const void* fn, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> known;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = known.find({fn, smem});
+  if (it != known.end()) return it->second;
+  int n = 1;
+  TN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, smem));
+  n = std::max(n, 1);
+  known[{fn, smem}] = n;
+  return n;
 }
 
 int ilog2_exact(int64_t x) {
@@ -565,9 +696,102 @@ void launch_tiled(const GemmParams& p, float scale, bool hilo, cudaStream_t s) {
   gemm_tiled<TM, TN, TK, TY, TX, In, Out><<<dim3((unsigned)(gx * gy), 1, gz), 256, 0, s>>>(p, scale, hilo, flags);
 }
 
+// The row kernel for a small-K step written in place, when its rows suit it
+// (A rows of K contiguous entries, rows written densely): false otherwise.
+template <class Out>
+bool launch_rows(const GemmParams& g, float scale, cudaStream_t s, bool hilo) {
+  if (g.K > 4 || !(g.N == 2 || g.N == 4 || g.N == 8)) return false;
+  const int64_t rows = g.nbt * g.M;
+  if (rows < 256) return false;
+  RowsK p{};
+  p.A = (const float2*)g.A;
+  p.B = (const float2*)g.B;
+  p.C = g.C;
+  p.C2 = g.C2;
+  p.nbits = ilog2_exact(rows);
+  const int lgM = ilog2_exact(g.M);
+  if (p.nbits > kMaxBits) return false;
+  for (int j = 0; j < p.nbits; ++j) {
+    if (j < lgM) {
+      const int64_t bit = int64_t(1) << j;
+      p.a_w[j] = run_offset(g.a_m, bit);
+      p.c_w[j] = run_offset(g.c_m, bit);
+      p.b_w[j] = 0;
+    } else {
+      const int64_t bit = int64_t(1) << (j - lgM);
+      p.a_w[j] = run_offset(g.a_bt, bit);
+      p.c_w[j] = run_offset(g.c_bt, bit);
+      p.b_w[j] = run_offset(g.b_bt, bit);
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    p.ak[k] = k < g.K ? run_offset(g.a_k, k) : 0;
+    p.bk[k] = k < g.K ? run_offset(g.b_k, k) : 0;
+  }
+  for (int n = 0; n < 8; ++n) {
+    p.cn[n] = n < g.N ? run_offset(g.c_n, n) : 0;
+    p.bn[n] = n < g.N ? run_offset(g.b_n, n) : 0;
+  }
+  // a warp's 32 rows: A read as one contiguous span, C written densely
+  if (p.a_w[0] != g.K || p.c_w[0] > g.N) return false;
+  bool a_vec = g.K >= 2 && (reinterpret_cast<uintptr_t>(g.A) & 15) == 0;
+  for (int k = 0; k < g.K && a_vec; ++k) a_vec = p.ak[k] == k;
+  for (int j = 0; j < p.nbits && a_vec; ++j) a_vec = p.a_w[j] % 2 == 0;
+  p.a_vec = a_vec ? 1 : 0;
+  bool b_fixed = true;
+  for (int j = 0; j < p.nbits; ++j) b_fixed = b_fixed && p.b_w[j] == 0;
+  p.b_fixed = b_fixed ? 1 : 0;
+  const size_t pair_bytes = 2 * sizeof(typename Out::T);
+  bool pairs = (reinterpret_cast<uintptr_t>(g.C) % pair_bytes) == 0 &&
+               (!hilo || (reinterpret_cast<uintptr_t>(g.C2) % pair_bytes) == 0);
+  for (int n = 0; n < g.N && pairs; n += 2) pairs = p.cn[n + 1] == p.cn[n] + 1 && p.cn[n] % 2 == 0;
+  for (int j = 0; j < p.nbits && pairs; ++j) pairs = p.c_w[j] % 2 == 0;
+  p.c_pairs = pairs ? 1 : 0;
+  p.scale = scale;
+  // every offset is a sum over a subset of these non-negative weights
+  {
+    int64_t sa = 0, sc = 0, sb = 0, ka = 0, kb = 0, nc = 0, nb = 0;
+    for (int j = 0; j < p.nbits; ++j) {
+      TN_CHECK(p.a_w[j] >= 0 && p.c_w[j] >= 0 && p.b_w[j] >= 0, TN_ERR_UNSUPPORTED, "negative stride");
+      sa += p.a_w[j];
+      sc += p.c_w[j];
+      sb += p.b_w[j];
+    }
+    for (int k = 0; k < g.K; ++k) {
+      ka = std::max(ka, p.ak[k]);
+      kb = std::max(kb, p.bk[k]);
+    }
+    for (int n = 0; n < g.N; ++n) {
+      nc = std::max(nc, p.cn[n]);
+      nb = std::max(nb, p.bn[n]);
+    }
+    TN_CHECK(sa + ka < rows * g.K && sc + nc < rows * g.N && sb + kb + nb < g.nbt * g.K * g.N, TN_ERR_INVALID_ARG,
+             "internal: row-kernel index maps exceed their tensors");
+  }
+  const unsigned blocks = (unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 8);
+  auto go = [&](auto kc, auto nc) {
+    constexpr int KC = decltype(kc)::value, NC = decltype(nc)::value;
+    gemm_rows<Out, KC, NC><<<blocks, 256, 0, s>>>(p, hilo);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using I4 = std::integral_constant<int, 4>;
+  using I8 = std::integral_constant<int, 8>;
+  auto by_n = [&](auto kc) {
+    if (g.N == 2) go(kc, I2{});
+    else if (g.N == 4) go(kc, I4{});
+    else go(kc, I8{});
+  };
+  if (g.K == 1) by_n(I1{});
+  else if (g.K == 2) by_n(I2{});
+  else by_n(I4{});
+  return true;
+}
+
 // Small-K launch; `ex` non-null: the result goes to that expanded operand.
 template <class Out>
 void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, const ExpandedDst* ex) {
+  if (!ex && launch_rows<Out>(g, scale, s, hilo)) return;
   SmallK p{};
   p.A = (const float2*)g.A;
   p.B = (const float2*)g.B;
@@ -652,7 +876,6 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
   p.scale = scale;
   const size_t smem = 2 * (size_t)((p.K << p.na) + (p.K << p.nb)) * sizeof(float2);  // double buffer
   const int64_t tiles = int64_t(1) << (p.nbits - p.P);
-  const unsigned blocks = (unsigned)std::min<int64_t>(tiles, 152 * 6);
   // two adjacent outputs per thread when the tile's bit 0 has unit stride in the
   // destination and every other bit an even one (aligned vector stores)
   bool pair = p.P >= 1 && p.o_w[0] == 1 && (!ex || p.hp % 2 == 0);
@@ -663,7 +886,11 @@ void launch_smallk(const GemmParams& g, float scale, cudaStream_t s, bool hilo, 
     // the double buffer (up to 64 KB) plus the static tables can pass the 48 KB
     // a launch may use without the opt-in
     set_max_dynamic_smem((const void*)kern, (int)(2 * kSkMaxStage * 2 * sizeof(float2)));
-    kern<<<blocks, 256, smem, s>>>(p, hilo);
+    // one wave: as many CTAs as are resident at once (a second, partial wave
+    // would leave SMs idle at the end), each walking tiles grid-stride
+    const int per_sm = resident_blocks((const void*)kern, smem);
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)152 * std::max(per_sm, 1));
+    kern<<<grid, 256, smem, s>>>(p, hilo);
   };
   using I1 = std::integral_constant<int, 1>;
   using I2 = std::integral_constant<int, 2>;

@@ -93,10 +93,10 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     p.stage_n = (sn < sm && 2 * p.K <= 4 * BK && p.m_halves != 2) ? 1 : 0;
     // 16-byte stores along n instead: n's first run has unit stride and holds
     // whole groups of VN outputs, every other stride keeps groups 16-byte
-    // aligned, and the rows sit VN apart (a warp's 32 rows then write one
-    // contiguous 512-byte span per store)
-    const int64_t VN = p.out_kind == 2 ? 2 : 4;
-    bool vec = p.c_n.n > 0 && p.c_n.st[0] == 1 && (int64_t(1) << p.c_n.lg[0]) % VN == 0 && sm == VN &&
+    // aligned, and rows sit at most 32 bytes apart (a warp's 32 rows then
+    // write one span of 512 or 1024 bytes per store, or two of them fill it)
+    const int64_t VN = p.out_kind == 2 ? 2 : 4, ES = p.out_kind == 2 ? 8 : 4;
+    bool vec = p.c_n.n > 0 && p.c_n.st[0] == 1 && (int64_t(1) << p.c_n.lg[0]) % VN == 0 && sm * ES <= 32 &&
                p.acc_split == 0;
     for (const Runs* R : {&p.c_n, &p.c_m, &p.c_bt})
       for (int r = (R == &p.c_n ? 1 : 0); r < R->n && vec; ++r) vec = R->st[r] % VN == 0;
@@ -174,19 +174,24 @@ __device__ __forceinline__ I run_off_i(const Runs& R, I i) {
 }
 
 // I: index type (32-bit when B and Bx have fewer than 2^31 elements)
+// pair = 1: the block-diagonal operand of a row-paired step, [[B, 0], [0, B]]
+// (N, K are twice B's extents; entry (k', n') is B[k' mod K/2][n' mod N/2]
+// when k' and n' fall in the same half, else 0)
 template <class T2, class T, class TIN, class I>
 __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, Runs b_n, int64_t nbt, int64_t N,
                                 int64_t K, int64_t half_pitch, T2* __restrict__ Bx, T2* __restrict__ Bx_lo,
-                                float bscale) {
+                                float bscale, int pair) {
   const I total = (I)(nbt * N * half_pitch);
   const I hp = (I)half_pitch, NN = (I)N, KK = (I)K;
+  const I Nh = NN >> pair, Kh = KK >> pair;  // B's own extents
   for (I x = blockIdx.x * (I)blockDim.x + threadIdx.x; x < total; x += (I)gridDim.x * blockDim.x) {
     const I k = x % hp;
     const I t = x / hp;
     const I n = t % NN, bt = t / NN;
     float re = 0.f, im = 0.f;
-    if (k < KK) {
-      const TIN v = B[run_off_i<I>(b_bt, bt) + run_off_i<I>(b_k, k) + run_off_i<I>(b_n, n)];
+    if (k < KK && (!pair || (n >= Nh) == (k >= Kh))) {
+      const I ks = pair ? k % Kh : k, ns = pair ? n % Nh : n;
+      const TIN v = B[run_off_i<I>(b_bt, bt) + run_off_i<I>(b_k, ks) + run_off_i<I>(b_n, ns)];
       re = (float)v.x * bscale;  // power of two: exact unless out of range
       im = (float)v.y * bscale;
     }
@@ -215,38 +220,44 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, 
 template <class I>
 void expand_typed(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
                   int64_t K, int64_t half_pitch, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo,
-                  float bscale, unsigned blocks) {
+                  float bscale, unsigned blocks, int pair) {
   if (bf16) {
     if (in_c64)
       expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2, I><<<blocks, 256, 0, s>>>(
           (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo,
-          bscale);
+          bscale, pair);
     else
       expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162, I><<<blocks, 256, 0, s>>>(
           (const __nv_bfloat162*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
-          (__nv_bfloat162*)Bx_lo, bscale);
+          (__nv_bfloat162*)Bx_lo, bscale, pair);
   } else {
     if (in_c64)
       expand_b_kernel<__half2, __half, float2, I><<<blocks, 256, 0, s>>>(
-          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale, pair);
     else
       expand_b_kernel<__half2, __half, __half2, I><<<blocks, 256, 0, s>>>(
-          (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale);
+          (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale,
+          pair);
   }
 }
 }  // namespace
 
 void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
-                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo, float bscale) {
-  const int64_t half_pitch = (2 * K + BK - 1) / BK * BK / 2;
-  const int64_t total = nbt * N * half_pitch;
+                     int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo, float bscale,
+                     bool pair) {
+  // pair: the operand of the row-paired GEMM, extents 2N x 2K
+  const int64_t Ne = pair ? 2 * N : N, Ke = pair ? 2 * K : K;
+  const int64_t half_pitch = (2 * Ke + BK - 1) / BK * BK / 2;
+  const int64_t total = nbt * Ne * half_pitch;
   if (total <= 0) return;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
   // 32-bit indices when every index and offset of B and the expanded copy fits
-  if (2 * total < (int64_t(1) << 31) && nbt * N * K < (int64_t(1) << 30))
-    expand_typed<int32_t>(B, b_bt, b_k, b_n, nbt, N, K, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks);
+  if (2 * total < (int64_t(1) << 31) && nbt * Ne * Ke < (int64_t(1) << 30))
+    expand_typed<int32_t>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks,
+                          pair ? 1 : 0);
   else
-    expand_typed<int64_t>(B, b_bt, b_k, b_n, nbt, N, K, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks);
+    expand_typed<int64_t>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks,
+                          pair ? 1 : 0);
 }
 
 int64_t expanded_half_pitch(int64_t K) { return (2 * K + BK - 1) / BK * BK / 2; }

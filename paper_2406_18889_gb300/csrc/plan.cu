@@ -333,8 +333,39 @@ TcRoles tc_roles(const Step& S, bool* ok_out = nullptr) {
     r.c_m = g.c_n;
     r.c_n = g.c_m;
   }
+  if (S.pair_rows) {
+    // Row pairs: A's rows are K contiguous entries, so rows 2i and 2i + 1 read
+    // as one row of 2K entries -- a whole 128-byte k tile instead of a half-
+    // filled one -- and the GEMM becomes C'[i][(p, n)] = sum_{(p', k)}
+    // A'[i][(p', k)] B'[(p', k)][(p, n)] with B' = [[B, 0], [0, B]]: half the
+    // rows, twice N and K (the zero blocks cost tensor flops, not bytes).  The
+    // output keeps its layout: row 2i + p of C is row i of C' at column
+    // block p, so m loses its lowest bit to a new top digit of n.
+    r.M /= 2;
+    r.N *= 2;
+    r.K *= 2;
+    r.a_m *= 2;
+    const int64_t pst = r.c_m.st[0];
+    if (r.c_m.lg[0] == 1) {
+      for (int i = 1; i < r.c_m.n; ++i) {
+        r.c_m.lg[i - 1] = r.c_m.lg[i];
+        r.c_m.st[i - 1] = r.c_m.st[i];
+      }
+      --r.c_m.n;
+    } else {
+      r.c_m.lg[0] = (int8_t)(r.c_m.lg[0] - 1);
+      r.c_m.st[0] = 2 * pst;
+    }
+    r.c_n.lg[r.c_n.n] = 1;
+    r.c_n.st[r.c_n.n] = pst;
+    ++r.c_n.n;
+  }
   if (ok_out) *ok_out = ok;
   return r;
+}
+// expanded-operand bytes of a tensor-core step (its GEMM as run, hi + lo doubled)
+int64_t tc_bx_bytes(const Step& S, const TcRoles& r) {
+  return expanded_b_bytes(S.gp.nbt, r.N, r.K) * (S.hilo ? 2 : 1);
 }
 
 // split products also accumulate K in chunks (the tensor cores' own
@@ -405,7 +436,7 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
       if (S.post_perm) tmax = std::max(tmax, node_bytes(P, S.c, c64));
       if (!c64 && S.tc) {
         TcRoles r = tc_roles(S);
-        bmax = std::max(bmax, expanded_b_bytes(S.gp.nbt, r.N, r.K) * (S.hilo ? 2 : 1));
+        bmax = std::max(bmax, tc_bx_bytes(S, r));
       }
     }
   for (size_t t = 0; t < P.steps.size(); ++t)
@@ -449,7 +480,7 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
       if (S.b_fused)
         M.bx_off[t] = M.off[r.b_node];
       else
-        bx = M.bx_off[t] = ws.alloc(expanded_b_bytes(S.gp.nbt, r.N, r.K) * (S.hilo ? 2 : 1));
+        bx = M.bx_off[t] = ws.alloc(tc_bx_bytes(S, r));
     }
     if (tmp >= 0) ws.release(tmp);
     if (bx >= 0) ws.release(bx);
@@ -553,8 +584,10 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
     TN_CHECK(NA.kind == P.skind && NA.hilo == S.hilo, TN_ERR_INVALID_ARG, "internal: tensor-core operand storage");
     if (!S.b_fused) {
       R.begin(4, 0, (double)node_bytes(P, r.b_node, false) + (double)bx_bytes * (S.hilo ? 2 : 1));
-      launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N, r.K, P.skind == KIND_BF16, bx, s,
-                      b_c64, bx_lo, ldexpf(1.0f, -S.bexp));
+      // row-paired steps: B's own extents, written block-diagonally
+      const int pr = S.pair_rows ? 1 : 0;
+      launch_expand_b(X.base(r.b_node), r.b_bt, r.b_k, r.b_n, S.gp.nbt, r.N >> pr, r.K >> pr,
+                      P.skind == KIND_BF16, bx, s, b_c64, bx_lo, ldexpf(1.0f, -S.bexp), S.pair_rows);
       R.end();
     }
     TcGemmParams tp{};
@@ -902,6 +935,19 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
       if (Q.hoisted || Q.tc || Q.post_perm || Q.gp.K > 4 || expanded_half_pitch(r.K) != r.K) continue;
       Q.fuse_expand = true;
       S.b_fused = true;
+    }
+  // row pairs (tc_roles): tensor-core steps whose A rows are K contiguous
+  // entries filling at most half a k tile, N small, B expanded by its own
+  // launch, no split product
+  if (P.skind != KIND_C64)
+    for (auto& S : P.steps) {
+      if (!S.tc || S.hilo || S.b_fused) continue;
+      const TcRoles r = tc_roles(S);
+      if (r.a_m != r.K || r.K % 2 != 0 || 4 * r.K > kTcKTile || r.N > 32 || r.M < 256 || r.c_m.n < 1 ||
+          r.c_n.n >= kMaxRuns)
+        continue;
+      if (!tc_gemm_supported(S.gp.nbt, r.M / 2, 2 * r.N, 2 * r.K, r.a_bt, 2 * r.a_m, 1)) continue;
+      S.pair_rows = true;
     }
   // micro steps: per-batch CUDA-core steps with at most 2^14 outputs and K <= 4
   // whose operands are leaves, plan-resident results or other micro steps;

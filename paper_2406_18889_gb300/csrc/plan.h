@@ -50,6 +50,7 @@ struct Step {
   bool fuse_expand = false;            // writes its result as the consumer's expanded operand
   bool b_fused = false;                // tensor-core step whose expanded operand its producer wrote
   bool micro = false;                  // small per-batch step run inside the fused small-step launch
+  bool pair_rows = false;              // tensor-core step run with row pairs (see tc_roles in plan.cu)
   int tc_bn = 0, tc_mh = 0;            // tuned tensor-core launch form (tc_bn 0: the default heuristics)
   double cost = 0;                     // complex MACs with the batch edge at its planned size
   double cost_one = 0;                 // complex MACs of one sub-network

@@ -110,6 +110,9 @@ struct StridedCopy {
   int64_t in_stride[kMaxBits];
 };
 
+// real k per stage of the tensor-core GEMM (one 128-byte row of 16-bit values)
+constexpr int kTcKTile = 64;
+
 // Tensor-core GEMM on interleaved 16-bit complex data (stacked 4M lowering):
 // C[bt][m][n] = scale * sum_k A[bt][m][k] B[bt][k][n]; extents in complex elements.
 struct TcGemmParams {
@@ -208,9 +211,10 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
 // expand a complex operand B[bt][k][n] (index maps b_bt, b_k, b_n) stored as fp32
 // (in_c64) or 16-bit complex into its real 2x2 form; with Bx_lo non-null also
 // the rounding residual of every entry
+// pair: write the block-diagonal [[B, 0], [0, B]] of a row-paired step (2N x 2K)
 void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
                      int64_t K, bool bf16, void* Bx, cudaStream_t s, bool in_c64 = false, void* Bx_lo = nullptr,
-                     float bscale = 1.0f);
+                     float bscale = 1.0f, bool pair = false);
 Runs single_run(int64_t extent, int64_t stride);
 // true when a wait on a barrier nothing completes gave up after limit_ns and raised its flag
 bool selftest_bounded_wait(uint64_t limit_ns, cudaStream_t s);
