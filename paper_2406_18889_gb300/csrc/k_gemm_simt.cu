@@ -522,9 +522,11 @@ __global__ void __launch_bounds__(256) gemm_smallk(SmallK p, bool hilo) {
 // place): thread t takes rows (bt, m) of the step, loads the row's K entries
 // of A once (16-byte loads when they are contiguous), forms all N outputs in
 // registers from B (held in registers when the step has one batch) and stores
-// them (pairs when consecutive n are adjacent).  Row r = bt * M + m is
-// addressed bit-linearly: its low 8 bits (the thread) by a register part,
-// the rest (the chunk of 256 rows) by a warp reduction over per-bit weights.
+// them (pairs when consecutive n are adjacent).  A thread takes 2 or 4 rows
+// of a chunk and issues their loads together.  Row r = bt * M + m is
+// addressed bit-linearly: its low bits (the thread and its row within the
+// chunk) by a register part, the rest (the chunk) by a warp reduction over
+// per-bit weights.
 struct RowsK {
   const float2* A;
   const float2* B;
@@ -541,7 +543,7 @@ struct RowsK {
 };
 
 template <class Out, int KC, int NC>
-__global__ void __launch_bounds__(256) gemm_rows(RowsK p, bool hilo) {
+__global__ void __launch_bounds__(256, 2) gemm_rows(RowsK p, bool hilo) {
   __shared__ int64_t w[3][kMaxBits];
   for (int j = threadIdx.x; j < p.nbits; j += blockDim.x) {
     w[0][j] = p.a_w[j];
@@ -568,13 +570,33 @@ __global__ void __launch_bounds__(256) gemm_rows(RowsK p, bool hilo) {
 #pragma unroll
       for (int n = 0; n < NC; ++n) bf[k][n] = __ldg(p.B + p.bk[k] + p.bn[n]);
   }
+  // a chunk is 256 R rows: thread t takes rows t + 256 q (q < R), the row
+  // bits 8, 9 being q; their R A loads are issued before any arithmetic, so
+  // each thread keeps several rows' loads in flight (R = 2 where the B
+  // registers of a larger tile leave no room for four rows)
+  constexpr int R = KC * NC <= 16 ? 4 : 2;
+  constexpr int lgR = R == 4 ? 2 : 1;
+  int64_t a_q[R], c_q[R], b_q[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    a_q[q] = a_t;
+    c_q[q] = c_t;
+    b_q[q] = b_t;
+    for (int j = 0; j < lgR; ++j)
+      if (((q >> j) & 1) && 8 + j < p.nbits) {
+        a_q[q] += w[0][8 + j];
+        c_q[q] += w[1][8 + j];
+        b_q[q] += w[2][8 + j];
+      }
+  }
   const int64_t rows = int64_t(1) << p.nbits;
-  const int64_t chunks = (rows + 255) >> 8;
+  const int lgC = 8 + lgR;
+  const int64_t chunks = (rows + (256 * R - 1)) >> lgC;
   for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
-    // chunk offsets: lane j sums the weights of row bits 8 + j, 40 + j
+    // chunk offsets: lane j sums the weights of row bits lgC + j, lgC + 32 + j
     int64_t a0 = 0, c0 = 0, b0 = 0;
-    for (int j = 8 + lane; j < p.nbits; j += 32)
-      if ((c >> (j - 8)) & 1) {
+    for (int j = lgC + lane; j < p.nbits; j += 32)
+      if ((c >> (j - lgC)) & 1) {
         a0 += w[0][j];
         c0 += w[1][j];
         b0 += w[2][j];
@@ -585,49 +607,57 @@ __global__ void __launch_bounds__(256) gemm_rows(RowsK p, bool hilo) {
       c0 += __shfl_xor_sync(0xffffffffu, c0, o);
       b0 += __shfl_xor_sync(0xffffffffu, b0, o);
     }
-    if ((c << 8) + threadIdx.x >= rows) continue;
-    const int64_t ao = a0 + a_t, co = c0 + c_t;
-    float2 a[KC];
-    if (KC >= 2 && p.a_vec) {
+    float2 a[R][KC];
 #pragma unroll
-      for (int k = 0; k < KC; k += 2) {
-        const float4 v = __ldcs(reinterpret_cast<const float4*>(p.A + ao + k));
-        a[k] = make_float2(v.x, v.y);
-        a[k + 1] = make_float2(v.z, v.w);
+    for (int q = 0; q < R; ++q) {
+      if ((c << lgC) + (q << 8) + threadIdx.x >= rows) continue;
+      const int64_t ao = a0 + a_q[q];
+      if (KC >= 2 && p.a_vec) {
+#pragma unroll
+        for (int k = 0; k < KC; k += 2) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(p.A + ao + k));
+          a[q][k] = make_float2(v.x, v.y);
+          a[q][k + 1] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < KC; ++k) a[q][k] = __ldcs(p.A + ao + p.ak[k]);
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < KC; ++k) a[k] = __ldcs(p.A + ao + p.ak[k]);
-    }
-    float2 r[NC];
-#pragma unroll
-    for (int n = 0; n < NC; ++n) r[n] = make_float2(0.f, 0.f);
-    if (p.b_fixed) {
-#pragma unroll
-      for (int k = 0; k < KC; ++k)
-#pragma unroll
-        for (int n = 0; n < NC; ++n) cmac(r[n], a[k], bf[k][n]);
-    } else {
-      const int64_t bo = b0 + b_t;
-#pragma unroll
-      for (int k = 0; k < KC; ++k)
-#pragma unroll
-        for (int n = 0; n < NC; ++n) cmac(r[n], a[k], __ldg(p.B + bo + p.bk[k] + p.bn[n]));
     }
 #pragma unroll
-    for (int n = 0; n < NC; ++n) r[n] = make_float2(r[n].x * p.scale, r[n].y * p.scale);
-    if (NC >= 2 && p.c_pairs) {
-      SmallK q{};  // store_v reads only the destination pointers
-      q.C = p.C;
-      q.C2 = p.C2;
+    for (int q = 0; q < R; ++q) {
+      if ((c << lgC) + (q << 8) + threadIdx.x >= rows) continue;
+      const int64_t co = c0 + c_q[q];
+      float2 r[NC];
 #pragma unroll
-      for (int n = 0; n < NC; n += 2) {
-        const float2 v2[2] = {r[n], r[n + 1]};
-        store_v<Out, 0, 2>(q, co + p.cn[n], v2, hilo);
+      for (int n = 0; n < NC; ++n) r[n] = make_float2(0.f, 0.f);
+      if (p.b_fixed) {
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+#pragma unroll
+          for (int n = 0; n < NC; ++n) cmac(r[n], a[q][k], bf[k][n]);
+      } else {
+        const int64_t bo = b0 + b_q[q];
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+#pragma unroll
+          for (int n = 0; n < NC; ++n) cmac(r[n], a[q][k], __ldg(p.B + bo + p.bk[k] + p.bn[n]));
       }
-    } else {
 #pragma unroll
-      for (int n = 0; n < NC; ++n) store_out<Out>(C, C2, co + p.cn[n], r[n], hilo);
+      for (int n = 0; n < NC; ++n) r[n] = make_float2(r[n].x * p.scale, r[n].y * p.scale);
+      if (NC >= 2 && p.c_pairs) {
+        SmallK sq{};  // store_v reads only the destination pointers
+        sq.C = p.C;
+        sq.C2 = p.C2;
+#pragma unroll
+        for (int n = 0; n < NC; n += 2) {
+          const float2 v2[2] = {r[n], r[n + 1]};
+          store_v<Out, 0, 2>(sq, co + p.cn[n], v2, hilo);
+        }
+      } else {
+#pragma unroll
+        for (int n = 0; n < NC; ++n) store_out<Out>(C, C2, co + p.cn[n], r[n], hilo);
+      }
     }
   }
 }
@@ -768,7 +798,8 @@ bool launch_rows(const GemmParams& g, float scale, cudaStream_t s, bool hilo) {
     TN_CHECK(sa + ka < rows * g.K && sc + nc < rows * g.N && sb + kb + nb < g.nbt * g.K * g.N, TN_ERR_INVALID_ARG,
              "internal: row-kernel index maps exceed their tensors");
   }
-  const unsigned blocks = (unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 8);
+  // at most two resident blocks per SM; chunks of up to 1024 rows
+  const unsigned blocks = (unsigned)std::min<int64_t>((rows + 511) / 512, 152 * 4);
   auto go = [&](auto kc, auto nc) {
     constexpr int KC = decltype(kc)::value, NC = decltype(nc)::value;
     gemm_rows<Out, KC, NC><<<blocks, 256, 0, s>>>(p, hilo);

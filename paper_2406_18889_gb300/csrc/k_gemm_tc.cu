@@ -177,20 +177,23 @@ __device__ __forceinline__ I run_off_i(const Runs& R, I i) {
 // pair = 1: the block-diagonal operand of a row-paired step, [[B, 0], [0, B]]
 // (N, K are twice B's extents; entry (k', n') is B[k' mod K/2][n' mod N/2]
 // when k' and n' fall in the same half, else 0)
-template <class T2, class T, class TIN, class I>
+// P2: half_pitch, N and K are powers of two (lg[] their logs, lg[2] that of
+// K >> pair), so the index splits are shifts and masks
+template <class T2, class T, class TIN, class I, bool P2>
 __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, Runs b_n, int64_t nbt, int64_t N,
                                 int64_t K, int64_t half_pitch, T2* __restrict__ Bx, T2* __restrict__ Bx_lo,
-                                float bscale, int pair) {
+                                float bscale, int pair, int4 lg) {
   const I total = (I)(nbt * N * half_pitch);
   const I hp = (I)half_pitch, NN = (I)N, KK = (I)K;
   const I Nh = NN >> pair, Kh = KK >> pair;  // B's own extents
   for (I x = blockIdx.x * (I)blockDim.x + threadIdx.x; x < total; x += (I)gridDim.x * blockDim.x) {
-    const I k = x % hp;
-    const I t = x / hp;
-    const I n = t % NN, bt = t / NN;
+    const I k = P2 ? (x & (hp - 1)) : x % hp;
+    const I t = P2 ? (x >> lg.x) : x / hp;
+    const I n = P2 ? (t & (NN - 1)) : t % NN, bt = P2 ? (t >> lg.y) : t / NN;
     float re = 0.f, im = 0.f;
     if (k < KK && (!pair || (n >= Nh) == (k >= Kh))) {
-      const I ks = pair ? k % Kh : k, ns = pair ? n % Nh : n;
+      const I ks = !pair ? k : P2 ? (k & (Kh - 1)) : k % Kh;
+      const I ns = !pair ? n : P2 ? (n & (Nh - 1)) : n % Nh;
       const TIN v = B[run_off_i<I>(b_bt, bt) + run_off_i<I>(b_k, ks) + run_off_i<I>(b_n, ns)];
       re = (float)v.x * bscale;  // power of two: exact unless out of range
       im = (float)v.y * bscale;
@@ -217,28 +220,37 @@ __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, 
   }
 }
 
-template <class I>
+template <class I, bool P2>
 void expand_typed(const void* B, const Runs& b_bt, const Runs& b_k, const Runs& b_n, int64_t nbt, int64_t N,
                   int64_t K, int64_t half_pitch, bool bf16, void* Bx, cudaStream_t s, bool in_c64, void* Bx_lo,
-                  float bscale, unsigned blocks, int pair) {
+                  float bscale, unsigned blocks, int pair, int4 lg) {
   if (bf16) {
     if (in_c64)
-      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2, I><<<blocks, 256, 0, s>>>(
+      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, float2, I, P2><<<blocks, 256, 0, s>>>(
           (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx, (__nv_bfloat162*)Bx_lo,
-          bscale, pair);
+          bscale, pair, lg);
     else
-      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162, I><<<blocks, 256, 0, s>>>(
+      expand_b_kernel<__nv_bfloat162, __nv_bfloat16, __nv_bfloat162, I, P2><<<blocks, 256, 0, s>>>(
           (const __nv_bfloat162*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__nv_bfloat162*)Bx,
-          (__nv_bfloat162*)Bx_lo, bscale, pair);
+          (__nv_bfloat162*)Bx_lo, bscale, pair, lg);
   } else {
     if (in_c64)
-      expand_b_kernel<__half2, __half, float2, I><<<blocks, 256, 0, s>>>(
-          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale, pair);
+      expand_b_kernel<__half2, __half, float2, I, P2><<<blocks, 256, 0, s>>>(
+          (const float2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale, pair,
+          lg);
     else
-      expand_b_kernel<__half2, __half, __half2, I><<<blocks, 256, 0, s>>>(
+      expand_b_kernel<__half2, __half, __half2, I, P2><<<blocks, 256, 0, s>>>(
           (const __half2*)B, b_bt, b_k, b_n, nbt, N, K, half_pitch, (__half2*)Bx, (__half2*)Bx_lo, bscale,
-          pair);
+          pair, lg);
   }
+}
+
+// log2 of x, or -1 when x is not a power of two
+int log2_or_neg(int64_t x) {
+  if (x <= 0 || (x & (x - 1))) return -1;
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  return r;
 }
 }  // namespace
 
@@ -251,13 +263,23 @@ void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Run
   const int64_t total = nbt * Ne * half_pitch;
   if (total <= 0) return;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  const int4 lg = make_int4(log2_or_neg(half_pitch), log2_or_neg(Ne), log2_or_neg(pair ? K : Ke), 0);
+  const bool p2 = lg.x >= 0 && lg.y >= 0 && lg.z >= 0;
   // 32-bit indices when every index and offset of B and the expanded copy fits
-  if (2 * total < (int64_t(1) << 31) && nbt * Ne * Ke < (int64_t(1) << 30))
-    expand_typed<int32_t>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks,
-                          pair ? 1 : 0);
+  const bool i32 = 2 * total < (int64_t(1) << 31) && nbt * Ne * Ke < (int64_t(1) << 30);
+  const int pr = pair ? 1 : 0;
+  if (i32 && p2)
+    expand_typed<int32_t, true>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale,
+                                blocks, pr, lg);
+  else if (i32)
+    expand_typed<int32_t, false>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale,
+                                 blocks, pr, lg);
+  else if (p2)
+    expand_typed<int64_t, true>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale,
+                                blocks, pr, lg);
   else
-    expand_typed<int64_t>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale, blocks,
-                          pair ? 1 : 0);
+    expand_typed<int64_t, false>(B, b_bt, b_k, b_n, nbt, Ne, Ke, half_pitch, bf16, Bx, s, in_c64, Bx_lo, bscale,
+                                 blocks, pr, lg);
 }
 
 int64_t expanded_half_pitch(int64_t K) { return (2 * K + BK - 1) / BK * BK / 2; }
