@@ -177,45 +177,55 @@ __device__ __forceinline__ I run_off_i(const Runs& R, I i) {
 // pair = 1: the block-diagonal operand of a row-paired step, [[B, 0], [0, B]]
 // (N, K are twice B's extents; entry (k', n') is B[k' mod K/2][n' mod N/2]
 // when k' and n' fall in the same half, else 0)
-// P2: half_pitch, N and K are powers of two (lg[] their logs, lg[2] that of
-// K >> pair), so the index splits are shifts and masks
+// Four consecutive k per thread (half_pitch is a multiple of 32), so each of
+// the two rows gets one 16-byte store.  P2: half_pitch, N and K are powers of
+// two (lg.x, lg.y their logs), so the index splits are shifts and masks.
+template <class T2>
+struct alignas(16) Quad {
+  T2 v[4];
+};
+
 template <class T2, class T, class TIN, class I, bool P2>
 __global__ void expand_b_kernel(const TIN* __restrict__ B, Runs b_bt, Runs b_k, Runs b_n, int64_t nbt, int64_t N,
                                 int64_t K, int64_t half_pitch, T2* __restrict__ Bx, T2* __restrict__ Bx_lo,
                                 float bscale, int pair, int4 lg) {
-  const I total = (I)(nbt * N * half_pitch);
-  const I hp = (I)half_pitch, NN = (I)N, KK = (I)K;
+  const I hq = (I)(half_pitch >> 2), NN = (I)N, KK = (I)K;
+  const I total = (I)nbt * NN * hq;
   const I Nh = NN >> pair, Kh = KK >> pair;  // B's own extents
   for (I x = blockIdx.x * (I)blockDim.x + threadIdx.x; x < total; x += (I)gridDim.x * blockDim.x) {
-    const I k = P2 ? (x & (hp - 1)) : x % hp;
-    const I t = P2 ? (x >> lg.x) : x / hp;
+    const I k0 = (P2 ? (x & (hq - 1)) : x % hq) << 2;
+    const I t = P2 ? (x >> (lg.x - 2)) : x / hq;
     const I n = P2 ? (t & (NN - 1)) : t % NN, bt = P2 ? (t >> lg.y) : t / NN;
-    float re = 0.f, im = 0.f;
-    if (k < KK && (!pair || (n >= Nh) == (k >= Kh))) {
-      const I ks = !pair ? k : P2 ? (k & (Kh - 1)) : k % Kh;
-      const I ns = !pair ? n : P2 ? (n & (Nh - 1)) : n % Nh;
-      const TIN v = B[run_off_i<I>(b_bt, bt) + run_off_i<I>(b_k, ks) + run_off_i<I>(b_n, ns)];
-      re = (float)v.x * bscale;  // power of two: exact unless out of range
-      im = (float)v.y * bscale;
-    }
-    const T hre = T(re), him = T(im);
-    T2 r0, r1;
-    r0.x = hre;
-    r0.y = neg16<T>(him);
-    r1.x = him;
-    r1.y = hre;
-    const int64_t row0 = ((int64_t)bt * 2 * N + 2 * (int64_t)n) * half_pitch;
-    Bx[row0 + k] = r0;
-    Bx[row0 + half_pitch + k] = r1;
-    if (Bx_lo) {
+    const I ns = !pair ? n : P2 ? (n & (Nh - 1)) : n % Nh;
+    const I base = run_off_i<I>(b_bt, bt) + run_off_i<I>(b_n, ns);
+    Quad<T2> h0, h1, l0, l1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const I k = k0 + j;
+      float re = 0.f, im = 0.f;
+      if (k < KK && (!pair || (n >= Nh) == (k >= Kh))) {
+        const I ks = !pair ? k : P2 ? (k & (Kh - 1)) : k % Kh;
+        const TIN v = B[base + run_off_i<I>(b_k, ks)];
+        re = (float)v.x * bscale;  // power of two: exact unless out of range
+        im = (float)v.y * bscale;
+      }
+      const T hre = T(re), him = T(im);
+      h0.v[j].x = hre;
+      h0.v[j].y = neg16<T>(him);
+      h1.v[j].x = him;
+      h1.v[j].y = hre;
       const T lre = T(re - (float)hre), lim = T(im - (float)him);
-      T2 l0, l1;
-      l0.x = lre;
-      l0.y = neg16<T>(lim);
-      l1.x = lim;
-      l1.y = lre;
-      Bx_lo[row0 + k] = l0;
-      Bx_lo[row0 + half_pitch + k] = l1;
+      l0.v[j].x = lre;
+      l0.v[j].y = neg16<T>(lim);
+      l1.v[j].x = lim;
+      l1.v[j].y = lre;
+    }
+    const int64_t row0 = ((int64_t)bt * 2 * N + 2 * (int64_t)n) * half_pitch + k0;
+    *reinterpret_cast<Quad<T2>*>(Bx + row0) = h0;
+    *reinterpret_cast<Quad<T2>*>(Bx + row0 + half_pitch) = h1;
+    if (Bx_lo) {
+      *reinterpret_cast<Quad<T2>*>(Bx_lo + row0) = l0;
+      *reinterpret_cast<Quad<T2>*>(Bx_lo + row0 + half_pitch) = l1;
     }
   }
 }
@@ -262,7 +272,9 @@ void launch_expand_b(const void* B, const Runs& b_bt, const Runs& b_k, const Run
   const int64_t half_pitch = (2 * Ke + BK - 1) / BK * BK / 2;
   const int64_t total = nbt * Ne * half_pitch;
   if (total <= 0) return;
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  TN_CHECK(half_pitch % 4 == 0 && (uintptr_t)Bx % 16 == 0 && (uintptr_t)Bx_lo % 16 == 0, TN_ERR_UNSUPPORTED,
+           "expanded operand not 16-byte aligned");
+  const unsigned blocks = (unsigned)std::min<int64_t>((total / 4 + 255) / 256, 152 * 32);
   const int4 lg = make_int4(log2_or_neg(half_pitch), log2_or_neg(Ne), log2_or_neg(pair ? K : Ke), 0);
   const bool p2 = lg.x >= 0 && lg.y >= 0 && lg.z >= 0;
   // 32-bit indices when every index and offset of B and the expanded copy fits
