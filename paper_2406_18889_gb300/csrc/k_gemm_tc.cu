@@ -92,18 +92,37 @@ void launch_gemm_tc(const void* A, const void* A_lo, int64_t sa_bt, int64_t sa_m
     // only for write-heavy tiles (up to four k tiles); deeper tiles hide the per-row stores
     p.stage_n = (sn < sm && 2 * p.K <= 4 * BK && p.m_halves != 2) ? 1 : 0;
     // 16-byte stores along n instead: n's first run has unit stride and holds
-    // whole groups of VN outputs, every other stride keeps groups 16-byte
-    // aligned, and rows sit at most 32 bytes apart (a warp's 32 rows then
-    // write one span of 512 or 1024 bytes per store, or two of them fill it)
+    // whole groups of VN outputs, and every other stride keeps groups 16-byte
+    // aligned.  Rows one group apart: each lane stores its own row (a warp's
+    // 32 rows write one span of 512 bytes per store).  Rows further apart:
+    // the pieces go through shared memory and L lanes store L consecutive
+    // pieces of one row (L = the pieces in n's first run, at most a chunk
+    // row's 16 / VN), so that every store fills whole 32-byte sectors.
     const int64_t VN = p.out_kind == 2 ? 2 : 4, ES = p.out_kind == 2 ? 8 : 4;
-    bool vec = p.c_n.n > 0 && p.c_n.st[0] == 1 && (int64_t(1) << p.c_n.lg[0]) % VN == 0 && sm * ES <= 32 &&
-               p.acc_split == 0;
+    bool vec = p.c_n.n > 0 && p.c_n.st[0] == 1 && (int64_t(1) << p.c_n.lg[0]) % VN == 0 && p.acc_split == 0;
     for (const Runs* R : {&p.c_n, &p.c_m, &p.c_bt})
       for (int r = (R == &p.c_n ? 1 : 0); r < R->n && vec; ++r) vec = R->st[r] % VN == 0;
     vec = vec && (reinterpret_cast<uintptr_t>(p.C) & 15) == 0 &&
           (!p.out_hilo || (reinterpret_cast<uintptr_t>(p.C2) & 15) == 0);
-    p.vec = vec ? 1 : 0;
-    if (vec) p.stage_n = 0;
+    // (staging shortens the operand ring: write-heavy tiles only, as above)
+    p.vec = 0;
+    p.vec_staged = 0;
+    p.vec_lpr_lg = 0;
+    const int64_t pieces = vec ? std::min<int64_t>((int64_t(1) << p.c_n.lg[0]) / VN, 16 / VN) : 0;
+    if (vec && sm * ES <= 16) {
+      p.vec = 1;
+      p.stage_n = 0;
+    } else if (vec && pieces >= 2 && p.m_halves != 2 && 2 * p.K <= 4 * BK) {
+      int lg = 0;
+      while ((int64_t(2) << lg) <= pieces) ++lg;
+      p.vec = 1;
+      p.vec_staged = 1;
+      p.vec_lpr_lg = lg;
+      p.stage_n = 1;
+    } else if (vec && sm * ES <= 32) {
+      p.vec = 1;  // two stores fill each 32-byte span
+      p.stage_n = 0;
+    }
   }
   const int64_t tbm = (p.m_halves == 2 ? 2 : 1) * (int64_t)BM;  // rows per tile
   TN_CHECK(p.nbt * ((p.M + tbm - 1) / tbm) * ((2 * p.N + bn - 1) / bn) < (int64_t(1) << 31) &&
@@ -380,6 +399,23 @@ __global__ void diff_il_kernel(const float2* a, const float2* b, int64_t nbt, in
   }
   atomicMax(max_diff, __float_as_uint(md));
 }
+// a 16-bit result with its rounding residual, stored [bt][n / g][m][n % g]
+// (g = N: [bt][m][n]), compared as hi + lo
+template <class T2>
+__global__ void diff_hl_kernel(const T2* hi, const T2* lo, const float2* b, int64_t nbt, int64_t M, int64_t N,
+                               int64_t g, unsigned* max_diff) {
+  float md = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbt * M * N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bt = i / (M * N), r = i - bt * M * N, m = r / N, n = r - m * N;
+    const int64_t o = bt * M * N + (n / g) * g * M + m * g + (n % g);
+    const float xr = (float)hi[o].x + (float)lo[o].x, xi = (float)hi[o].y + (float)lo[o].y;
+    const float dx = xr - b[i].x, dy = xi - b[i].y;
+    md = fmaxf(md, sqrtf(dx * dx + dy * dy));
+    if (!(xr == xr) || !(xi == xi)) md = 3.0e38f;
+  }
+  atomicMax(max_diff, __float_as_uint(md));
+}
 }  // namespace
 
 double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16, uint64_t seed, cudaStream_t s,
@@ -477,6 +513,39 @@ double selftest_gemm_tc(int64_t nbt, int64_t M, int64_t N, int64_t K, bool bf16,
         p.m_halves = v == 1 ? 2 : 1;
         launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
         diff_il_kernel<<<1024, 256, 0, s>>>((const float2*)C, (const float2*)R, nbt, M, N, mx);
+      }
+    }
+    // and 16-bit results with their residuals (M, N powers of two, N >= 8):
+    // rows of 8 consecutive n outputs 32 bytes apart, and [bt][m][n] (the
+    // 16-byte pieces staged through shared memory, two and four lanes per row)
+    if (pow2(M) && pow2(N) && N >= 8) {
+      int lgN = 0;
+      while ((int64_t(1) << lgN) < N) ++lgN;
+      char* lo = reinterpret_cast<char*>(C) + nbt * M * N * 4;
+      for (int gi = 0; gi < (N > 8 ? 2 : 1); ++gi) {
+        const int64_t g = gi ? N : 8;
+        p.out_kind = bf16 ? 1 : 0;
+        p.out_hilo = 1;
+        p.C2 = lo;
+        p.acc_split = 0;
+        p.m_halves = 0;
+        p.c_bt = single_run(nbt, M * N);
+        p.c_m = single_run(M, g);
+        p.c_n = single_run(g, 1);
+        if (g < N) {
+          p.c_n.n = 2;
+          p.c_n.lg[0] = 3;
+          p.c_n.lg[1] = (int8_t)(lgN - 3);
+          p.c_n.st[1] = 8 * M;
+        }
+        TN_CUDA(cudaMemsetAsync(C, 0xff, nbt * M * N * 8, s));
+        launch_gemm_tc(A, nullptr, M * K, K, Bx, nullptr, p, bf16, s);
+        if (bf16)
+          diff_hl_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>((const __nv_bfloat162*)C, (const __nv_bfloat162*)lo,
+                                                              (const float2*)R, nbt, M, N, g, mx);
+        else
+          diff_hl_kernel<__half2><<<1024, 256, 0, s>>>((const __half2*)C, (const __half2*)lo, (const float2*)R, nbt,
+                                                       M, N, g, mx);
       }
     }
     unsigned h[2] = {0, 0};

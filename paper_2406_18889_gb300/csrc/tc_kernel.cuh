@@ -239,26 +239,49 @@ __device__ __forceinline__ void store_el(char* Cb, char* C2b, int64_t o, float r
   }
 }
 
-// 16 bytes of consecutive complex outputs at 32-bit element offset o (16-byte
-// aligned): 4 values as 16-bit pairs (and their residuals to C2t when it is
-// non-null), or 2 values as fp32 pairs; v holds (re, im) of each, unscaled
+// 16 bytes of consecutive complex outputs from v (re, im of each, unscaled):
+// 4 values as 16-bit pairs in hv (their residuals in lv when res), or 2
+// values as fp32 pairs
 template <bool BF16, bool F32OUT>
-__device__ __forceinline__ void store_vec16(char* Ct, char* C2t, uint32_t o, const uint32_t* v, float scale) {
+__device__ __forceinline__ void pack_vec16(const uint32_t* v, float scale, bool res, uint4& hv, uint4& lv) {
   if constexpr (F32OUT) {
-    *reinterpret_cast<float4*>(Ct + (size_t)o * 8) =
-        make_float4(__uint_as_float(v[0]) * scale, __uint_as_float(v[1]) * scale, __uint_as_float(v[2]) * scale,
-                    __uint_as_float(v[3]) * scale);
+    hv = make_uint4(__float_as_uint(__uint_as_float(v[0]) * scale), __float_as_uint(__uint_as_float(v[1]) * scale),
+                    __float_as_uint(__uint_as_float(v[2]) * scale), __float_as_uint(__uint_as_float(v[3]) * scale));
+    lv = hv;
   } else {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float re = __uint_as_float(v[2 * q]) * scale, im = __uint_as_float(v[2 * q + 1]) * scale;
       h[q] = pack16<BF16>(re, im);
-      if (C2t) l[q] = resid16<BF16>(re, im, h[q]);
+      l[q] = res ? resid16<BF16>(re, im, h[q]) : 0u;
     }
-    *reinterpret_cast<uint4*>(Ct + (size_t)o * 4) = make_uint4(h[0], h[1], h[2], h[3]);
-    if (C2t) *reinterpret_cast<uint4*>(C2t + (size_t)o * 4) = make_uint4(l[0], l[1], l[2], l[3]);
+    hv = make_uint4(h[0], h[1], h[2], h[3]);
+    lv = make_uint4(l[0], l[1], l[2], l[3]);
   }
+}
+
+// the same stored at 32-bit element offset o (16-byte aligned) of Ct, and the
+// residuals at o of C2t when it is non-null
+template <bool BF16, bool F32OUT>
+__device__ __forceinline__ void store_vec16(char* Ct, char* C2t, uint32_t o, const uint32_t* v, float scale) {
+  uint4 hv, lv;
+  pack_vec16<BF16, F32OUT>(v, scale, !F32OUT && C2t != nullptr, hv, lv);
+  *reinterpret_cast<uint4*>(Ct + (size_t)o * (F32OUT ? 8 : 4)) = hv;
+  if (!F32OUT && C2t) *reinterpret_cast<uint4*>(C2t + (size_t)o * 4) = lv;
+}
+
+// Shared-memory slot (in 16-byte units) of piece q of row r of a warp's
+// staged chunk (32 rows x PR pieces, PR = 4 or 8): line (r / 8) * PR + q, bank
+// group (r ^ reverse(q)) mod 8.  Rows write their pieces one q at a time
+// (8 consecutive rows per phase) and lanes read back L consecutive pieces of
+// 8 / L consecutive rows per phase (L = 1 .. PR, powers of two): reversing
+// q's bits puts its low bits on the group's high bits, so either phase sees
+// 8 distinct bank groups.
+template <int PR>
+__device__ __forceinline__ int stage_slot(int r, int q) {
+  const int rq = PR == 4 ? (((q & 1) << 2) | (q & 2)) : (((q & 1) << 2) | (q & 2) | ((q >> 2) & 1));
+  return ((((r >> 3) * PR + q) << 3) | ((r ^ rq) & 7));
 }
 
 // 32 consecutive accumulator columns of this warp's TMEM lane quarter
@@ -555,6 +578,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t w_n = kBaseByBits && lane < 31 ? run_offset(p.c_n, int64_t(1) << lane) : 0;
     const uint32_t m32 = (uint32_t)m_rel;
     constexpr int ES = F32OUT ? 8 : 4;  // bytes per output element
+    // staged 16-byte pieces (STAGE with p.vec_staged): a chunk row holds kPR
+    // pieces of kVN outputs; in store i, lane L takes piece q_i(L) of row
+    // r_i(L), 2^lgL lanes per row (mr[i]: that row's in-tile offset)
+    constexpr int kVN = F32OUT ? 2 : 4, kPR = 16 / kVN, kLgPR = kPR == 4 ? 2 : 3;
+    static_assert(32 * kPR * 16 * (F32OUT ? 1 : 2) <= 32 * kStagePitch * 8, "staged pieces fit a warp's stage");
+    const bool vst = STAGE && p.vec && p.vec_staged && p.off32;
+    const int lgL = vst ? p.vec_lpr_lg : 0;
+    uint32_t mr[kPR];
+#pragma unroll
+    for (int i = 0; i < kPR; ++i)
+      mr[i] = STAGE ? __shfl_sync(0xffffffffu, m32, ((i >> (kLgPR - lgL)) << (5 - lgL)) + (lane >> lgL)) : 0u;
     asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
     char* const Cb = reinterpret_cast<char*>(p.C);
     char* const C2b = reinterpret_cast<char*>(p.C2);
@@ -739,7 +773,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int j0 = c * 16;  // first complex column of the chunk
-        if (STAGE) {
+        if (STAGE && vst && whole) {
+          // 16-byte pieces staged through shared memory: each lane writes its
+          // row's pieces, then 2^lgL lanes store consecutive pieces of one
+          // row together, so that a store covers whole sectors
+          uint4* sv = reinterpret_cast<uint4*>(stg);
+#pragma unroll
+          for (int q = 0; q < kPR; ++q) {
+            uint4 hv, lv;
+            pack_vec16<BF16, F32OUT>(v + 2 * kVN * q, p.scale, res, hv, lv);
+            const int sl = stage_slot<kPR>(lane, q);
+            sv[sl] = hv;
+            if (res) sv[32 * kPR + sl] = lv;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < kPR; ++i) {
+            const int q = ((i & ((kPR >> lgL) - 1)) << lgL) + (lane & ((1 << lgL) - 1));
+            const int r = ((i >> (kLgPR - lgL)) << (5 - lgL)) + (lane >> lgL);
+            const int sl = stage_slot<kPR>(r, q);
+            const uint32_t o = mr[i] + n32[j0 + q * kVN];
+            *reinterpret_cast<uint4*>(Ct + (size_t)o * ES) = sv[sl];
+            if (res) *reinterpret_cast<uint4*>(C2t + (size_t)o * 4) = sv[32 * kPR + sl];
+          }
+          __syncwarp();
+        } else if (STAGE) {
           // transpose through shared memory, already converted: lanes then run along n
 #pragma unroll
           for (int j = 0; j < 16; ++j) {

@@ -129,7 +129,9 @@ struct TcGemmParams {
   int acc_split;              // > 0: accumulate K in chunks of this many k tiles, summed in FP32 registers
   int off32;                  // every offset inside a tile (from its base) fits in 32 bits (set by the launcher)
   int vec;                    // 16-byte stores of consecutive n outputs (set by the launcher)
-  int m_halves;               // 2: 256-row tiles, two 128-row MMAs sharing each B tile (tile width 256 only)
+  int vec_staged;             // with vec and stage_n: the 16-byte pieces go through shared memory and
+  int vec_lpr_lg;             // 2^vec_lpr_lg lanes store consecutive pieces of one row together (launcher)
+  int m_halves;              // 2: 256-row tiles, two 128-row MMAs sharing each B tile (tile width 256 only)
 };
 
 // ------------------------------------------------------------ launchers
