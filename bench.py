@@ -6,15 +6,20 @@ Workload (one "step" = one pass of the whole hot path over one batch):
   6 sliced bonds (64 sub-networks), 10 open qubits (1024 amplitudes per block),
   64 blocks of closed bitstrings; a step contracts all 64 slices with an FP64
   cross-slice sum, keeps the top 64 strings per block and scores them by XEB.
+  Subtrees that depend on no sliced bond are contracted once per step and
+  shared by its 64 slices (--hoist: once per plan instead).
 
-Metric: slices/s (whole job, all ranks) and useful complex TFLOP/s
-(8 x complex MACs of the sub-networks, the paper's Table I convention).
+Metric: slices/s (whole job, all ranks) and the executed complex TFLOP/s
+(8 real flops per complex multiply-add the step's kernels perform).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec c64] [--impl reference]
 
-N > 1 runs one process per GPU (torchrun); each rank samples its own 64
-blocks of the same circuit (independent problems, no collective on the data
-path) and the job's value is the sum over ranks; time is the max over ranks.
+N > 1 runs one process per GPU (torchrun).  --partition slices (default):
+the 64 slices of the one problem are split over the ranks and their FP64
+partial sums added on rank 0 (strong scaling).  --partition blocks: each rank
+samples its own 64 blocks of the same circuit (independent problems, no
+collective on the data path), the job's value the sum over ranks (weak
+scaling).  Time is the max over ranks.
 """
 from __future__ import annotations
 
@@ -185,19 +190,38 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def sliced_wires(refine: bool = False):
+def prepare_path(w, path: str, batch: int = 64):
+    """The contraction tree of workload w for --path: "time" (greedy and
+    bisection trees refined for the flop count, then re-optimised for the
+    estimated time of one batch of ``batch`` slices: multiply-adds plus the
+    elements each step moves), "refined" (the flop-refined trees alone) or
+    "greedy"."""
     from paper_2406_18889_gb300 import engine as E
+    if path == "greedy":
+        return E.prepare(w)
+    kw = {}
+    if path == "time":
+        kw = dict(objective="time", batch_log2=max(int(batch).bit_length() - 1, 0))
+    return E.prepare(w, refine=True, method="both", workers=host_cores(), **kw)
+
+
+PATH_DESC = {"time": "greedy and bisection + subtree reconfiguration, re-optimised for time per batch "
+                     "(multiply-adds + 145 x elements moved)",
+             "refined": "greedy and bisection + subtree reconfiguration (fewest multiply-adds)",
+             "greedy": "greedy"}
+
+
+def sliced_wires(path: str = "greedy", batch: int = 64):
     w = rank_workload(0)
-    prep = E.prepare(w, refine=refine, method="both" if refine else "greedy", workers=host_cores() if refine else 0)
+    prep = prepare_path(w, path, batch)
     return w, prep, [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
 
 
 def run_reference(args):
-    refined = args.path == "refined"
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    w, prep, wires = sliced_wires(refined)
+    w, prep, wires = sliced_wires(args.path, args.batch)
     sample = "1 slice of 64 per step, oracle O2 (naive FP64 einsum contractor, numpy matmul)"
     for s in range(args.warmup):
         oracle_slices_per_s(w, wires, [s % 64])
@@ -322,7 +346,6 @@ def permute_bandwidth(B, torch, stream, bits: int = 28) -> dict:
 
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
-    refined = args.path == "refined"
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -336,9 +359,9 @@ def run_ours(args):
     # rank 0 (--partition slices), or every rank its own blocks (--partition blocks)
     split_slices = world > 1 and args.partition == "slices"
     w = rank_workload(0 if split_slices else rank)
-    prep = E.prepare(w, refine=refined, method="both" if refined else "greedy",
-                     workers=host_cores() if refined else 0)
-    flags = (B.TN_FLAG_HILO if args.hilo else 0) | (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
+    prep = prepare_path(w, args.path, args.batch)
+    hoist = B.TN_FLAG_HOIST_INVARIANT if args.hoist else 0
+    flags = (B.TN_FLAG_HILO if args.hilo else 0) | hoist
     plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
     S = plan.n_slices_total
     ids = np.arange(S, dtype=np.int64)
@@ -445,7 +468,8 @@ def run_ours(args):
                                         plan.workspace.numel(), stream.cuda_stream)
     alu = fp32_peak_measured(B)
     roofline, per_kind = roofline_from_profile(prof, (args.path, args.prec, args.batch, bool(args.hilo),
-                                                      not args.no_hoist), alu)
+                                                      bool(args.hoist)), alu)
+    executed_per_slice = float(prof["flops"].sum()) / S
     permute = permute_bandwidth(B, torch, stream)
     # recorded kernels + slice-id uploads (one launch per 256 ids of each batch) + top-k + XEB
     n_batches = -(-S // args.batch)
@@ -456,8 +480,7 @@ def run_ours(args):
     fine_value = None
     if args.prec != "c64" and not args.no_c64:
         planf = E.Plan(prep.tn, prep.tree, prec="fp16", max_slice_batch=args.batch,
-                       flags=B.TN_FLAG_HILO | B.TN_FLAG_FINE_ACC |
-                       (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT))
+                       flags=B.TN_FLAG_HILO | B.TN_FLAG_FINE_ACC | hoist)
         for _ in range(2):
             planf.contract(ids, out=amps)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -475,7 +498,6 @@ def run_ours(args):
         split = {"note": "bf16 tensor-core operands; hi + lo split products on every tensor-core step, or on "
                          "those TN_FLAG_HILO_AUTO picks for relative L2 <= 3e-3 on the calibration batch "
                          "(contraction only)"}
-        hoist = 0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT
         for name, fl, kw in (("all_steps", B.TN_FLAG_HILO, {}), ("auto", B.TN_FLAG_HILO_AUTO, {"hilo_tol": 3e-3})):
             pl = E.Plan(prep.tn, prep.tree, prec="bf16", max_slice_batch=args.batch, flags=fl | hoist, **kw)
             for _ in range(2):
@@ -495,8 +517,7 @@ def run_ours(args):
             pl.close()
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
-        plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch,
-                        flags=0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT)
+        plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch, flags=hoist)
         for _ in range(3):
             plan64.contract(ids, out=amps)
         torch.cuda.synchronize()
@@ -513,7 +534,7 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        _, _, wires = sliced_wires(refined)
+        _, _, wires = sliced_wires(args.path, args.batch)
         v = oracle_slices_per_s(rank_workload(0), wires, [0, 1])
         cpu = {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
                "sample": "2 of the 64 slices, oracle O2 (naive FP64 einsum contractor, numpy matmul)"}
@@ -525,16 +546,18 @@ def run_ours(args):
                  f"{args.prec} tensor-core operands, fp32 accumulate, complex64 elsewhere",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
-                   "hoist_invariant": not args.no_hoist, "autotune": bool(args.autotune),
-                   "path": "greedy and bisection + subtree reconfiguration" if refined else "greedy",
+                   "hoist_invariant": bool(args.hoist), "autotune": bool(args.autotune),
+                   "path": PATH_DESC[args.path],
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": (f"the 64 slices split over {world} GPUs, FP64 partials gathered and summed "
                                    "on rank 0" if split_slices else f"{world} independent block sets (one per GPU)")},
-        "useful_tflops": value * useful_per_slice / 1e12,
+        "useful_tflops": value * executed_per_slice / 1e12,
+        "useful_flops_note": "flops the step's kernels execute (8 per complex multiply-add), per slice: "
+                             "slice-independent subtrees run once per batch and are shared by its slices",
         "complex64_path": None if c64_value is None else {
             "value": c64_value, "unit": "slices/s", "speedup": value / c64_value,
-            "useful_tflops": c64_value * useful_per_slice / 1e12, "fp32_peak_tflops": alu[0],
-            "alu_frac": c64_value * useful_per_slice / 1e12 / alu[0], "fp32_peak_source": alu[1],
+            "useful_tflops": c64_value * executed_per_slice / 1e12, "fp32_peak_tflops": alu[0],
+            "alu_frac": c64_value * executed_per_slice / 1e12 / alu[0], "fp32_peak_source": alu[1],
             "note": "same workload and batch through the complex64 CUDA-core path (contraction only)"},
         "complex64_accuracy_tensor_core_path": None if fine_value is None else {
             "value": fine_value, "unit": "slices/s",
@@ -542,7 +565,10 @@ def run_ours(args):
             "note": "fp16 hi+lo operands, K accumulated one k tile at a time in FP32 (TN_FLAG_HILO | "
                     "TN_FLAG_FINE_ACC): complex64 accuracy on the tensor cores (contraction only)"},
         "bf16_split_precision": split,
-        "useful_flops_per_slice": useful_per_slice,
+        "useful_flops_per_slice": executed_per_slice,
+        "subnetwork_flops": useful_per_slice,
+        "subnetwork_flops_note": "8 x complex multiply-adds of one sub-network along the tree, every step "
+                                 "counted (the paper's Table I convention)",
         "wall_s": wall,
         "roofline": roofline,
         "permute": permute,
@@ -558,8 +584,10 @@ def run_ours(args):
 
 def run_uneven(args):
     """The 64 uneven circuits contracted in one tn_contract_slices_batched call
-    (every slice of every circuit, FP64 sums per circuit), on one GPU."""
-    refined = args.path == "refined"
+    (every slice of every circuit, FP64 sums per circuit), on one GPU.
+    --path time plans the flop-refined trees here: the slice batch of each
+    plan is the library's choice, not known when the tree is searched."""
+    refined = args.path != "greedy"
     import torch
     import workloads as W
     from paper_2406_18889_gb300 import binding as B
@@ -571,7 +599,7 @@ def run_uneven(args):
                        workers=host_cores() if refined else 0) for w in ws]
     plan_s = time.perf_counter() - t0
     flags = ((B.TN_FLAG_HILO if args.hilo else 0) | (B.TN_FLAG_HILO_AUTO if args.hilo_auto else 0) |
-             (0 if args.no_hoist else B.TN_FLAG_HOIST_INVARIANT))
+             (B.TN_FLAG_HOIST_INVARIANT if args.hoist else 0))
     # each plan's slice batch chosen by the library from a 16 GiB budget (and its slice count)
     cap = 16 << 30
     plans = [E.Plan(p.tn, p.tree, prec=args.prec, flags=flags, own_workspace=False, max_slice_batch=0,
@@ -630,7 +658,7 @@ def run_sycamore(args):
     a few seeded slices timed one by one, and the extrapolated time to 1e6
     samples at the fidelity whose top-1 XEB is 0.002 (Eq. 4: F = 0.002 /
     (H_1024 - 1); slices needed per block batch = F x 2^(sliced bonds))."""
-    refined = args.path == "refined"
+    refined = args.path != "greedy"
     import math
     import torch
     import workloads as W
@@ -703,11 +731,13 @@ def main(argv=None):
     ap.add_argument("--hilo-auto", action="store_true",
                     help="split products only where the calibration needs them for relative L2 <= 3e-3")
     ap.add_argument("--no-c64", action="store_true", help="skip timing the complex64 path alongside")
-    ap.add_argument("--no-hoist", action="store_true",
-                    help="recompute slice-independent subtrees in every batch instead of once per plan")
-    ap.add_argument("--path", default="refined", choices=["refined", "greedy"],
-                    help="contraction path: greedy and bisection trees refined by subtree reconfiguration "
-                         "(default; 10x fewer flops per slice on the 24-qubit workload), or the greedy tree alone")
+    ap.add_argument("--hoist", action="store_true",
+                    help="contract slice-independent subtrees once, at plan creation, instead of once in every "
+                         "batch (the default: every step does all of its batch's work)")
+    ap.add_argument("--path", default="time", choices=["time", "refined", "greedy"],
+                    help="contraction tree: time (default; flop-refined greedy and bisection trees re-optimised "
+                         "for the estimated time of one slice batch: multiply-adds plus the elements moved), "
+                         "refined (fewest multiply-adds) or greedy")
     ap.add_argument("--autotune", action="store_true",
                     help="time the tensor-core steps' launch forms on one batch first and keep the fastest")
     ap.add_argument("--batch", type=int, default=64)

@@ -210,9 +210,10 @@ class Prepared:
 
 def prepare(workload, n_sliced: Optional[int] = None, restarts: int = 4, seed: int = 0,
             sliced_wires: Optional[Sequence] = None, method: str = "greedy", refine: bool = False,
-            workers: int = 0) -> Prepared:
+            workers: int = 0, objective: str = "flops", batch_log2: Optional[int] = None) -> Prepared:
     """Network + contraction tree of a workload (host planning, once per circuit).
-    ``method`` / ``refine`` / ``workers`` select the path search (``pathfind.plan_tree``)."""
+    ``method`` / ``refine`` / ``workers`` / ``objective`` / ``batch_log2`` select the
+    path search (``pathfind.plan_tree``)."""
     tn = circuit_network(workload.circuit, workload.open_qubits, workload.closed_qubits,
                          workload.closed_bits)
     sliced = None
@@ -220,5 +221,5 @@ def prepare(workload, n_sliced: Optional[int] = None, restarts: int = 4, seed: i
         sliced = [tn.edge_of_wire[tuple(w)] for w in sliced_wires]
     s = workload.n_sliced if n_sliced is None else n_sliced
     tree = plan_tree(tn, n_sliced=s, restarts=restarts, seed=seed, sliced=sliced, method=method, refine=refine,
-                     workers=workers)
+                     workers=workers, objective=objective, batch_log2=batch_log2)
     return Prepared(tn, tree)

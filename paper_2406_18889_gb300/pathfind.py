@@ -222,6 +222,12 @@ def choose_slices(leaves, pairs, lg, keep, n_edges: int, n_sliced: int = 0,
     return chosen
 
 
+# Multiply-adds per element moved at which a 16-bit tensor-core step is as long
+# bound by HBM as by the tensor pipe: 8 real flops per complex MAC at ~1.94
+# PFLOP/s against 4 bytes per complex element at ~6.7 TB/s.
+ALPHA_TC = 145.0
+
+
 SWEEP = [(1.0, 0.0), (2.0, 0.0), (1.0, 0.25), (1.5, 0.25), (2.0, 0.25), (2.0, 0.5), (1.5, 0.5),
          (3.0, 0.5), (2.0, 0.75)]
 
@@ -393,7 +399,15 @@ PARTITION_IMBALANCES = (0.2, 0.3, 0.4, 0.5)
 def _candidate_trees(job):
     """Slicing (and with ``refine`` the refined trees) of one candidate path:
     a list of (pairs, sliced).  Top level, so that a process pool can run it."""
-    leaves, pairs, lg, keep, n_edges, n_sliced, cap_log2, sliced, refine, groups = job
+    leaves, pairs, lg, keep, n_edges, n_sliced, cap_log2, sliced, refine, groups, timing = job
+    out = _candidate_trees_flops(leaves, pairs, lg, keep, n_edges, n_sliced, cap_log2, sliced, refine, groups)
+    if timing is None:
+        return out
+    batch_log2, alpha = timing
+    return out + [(retime(leaves, p, lg, keep, sl, batch_log2, alpha), sl) for p, sl in out]
+
+
+def _candidate_trees_flops(leaves, pairs, lg, keep, n_edges, n_sliced, cap_log2, sliced, refine, groups):
     if sliced is None:
         sl = choose_slices(leaves, pairs, lg, keep, n_edges, n_sliced, cap_log2) \
             if (n_sliced or cap_log2 is not None) else []
@@ -425,7 +439,8 @@ def _candidate_trees(job):
 def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = None,
               restarts: int = 4, seed: int = 0, sliced: Optional[Sequence[int]] = None,
               method: str = "greedy", refine: bool = False, groups: Sequence[int] = (2, 4),
-              workers: int = 0) -> Tree:
+              workers: int = 0, objective: str = "flops", batch_log2: Optional[int] = None,
+              alpha: float = ALPHA_TC) -> Tree:
     """Search paths -- the greedy alpha/temperature sweep (``restarts`` seeds per
     noisy setting), recursive bisection at several balance windows, or both
     (``method``) -- slice each (unless ``sliced`` is given), keep the cheapest
@@ -435,9 +450,17 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     network without its sliced bonds is reconfigured, its intermediates kept
     within the cap or, without one, within the unrefined tree's largest.
     ``workers`` > 1 slices and refines the candidates in that many processes
-    (started with spawn); the result does not depend on it."""
+    (started with spawn); the result does not depend on it.
+
+    ``objective``: "flops" keeps the tree with the fewest multiply-adds over
+    all slices; "time" also re-optimises every candidate for ``time_cost``
+    (multiply-adds plus ``alpha`` per element moved, slices run
+    2^``batch_log2`` at a time, default all of them) and keeps the tree with
+    the lowest estimated time over all batches."""
     if method not in ("greedy", "partition", "both"):
         raise ValueError("method must be greedy, partition or both")
+    if objective not in ("flops", "time"):
+        raise ValueError("objective must be flops or time")
     lg = log2dims(tn)
     keep = frozenset(tn.output_edges())
     leaves = [frozenset(e) for e in tn.leaf_edges]
@@ -449,8 +472,12 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     if method in ("partition", "both"):
         for imb in PARTITION_IMBALANCES:
             candidates.append(partition_path(leaves, lg, keep, imbalance=imb))
+    timing = None
+    if objective == "time":
+        nb = len(sliced) if sliced is not None else n_sliced
+        timing = (int(batch_log2) if batch_log2 is not None else int(nb), float(alpha))
     jobs = [(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced, cap_log2,
-             None if sliced is None else list(sliced), refine, tuple(groups)) for pairs in candidates]
+             None if sliced is None else list(sliced), refine, tuple(groups), timing) for pairs in candidates]
     if workers > 1 and len(jobs) > 1:
         import multiprocessing
         from concurrent.futures import ProcessPoolExecutor
@@ -465,7 +492,11 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
             mx, cost, vcost = tree_stats(leaves, pairs, lg, keep, sl)
             if cap_log2 is not None and mx > cap_log2:
                 continue
-            key = (cost * 2.0 ** len(sl), mx)
+            if timing is None:
+                key = (cost * 2.0 ** len(sl), mx)
+            else:
+                bl = min(timing[0], len(sl))
+                key = (time_cost(leaves, pairs, lg, keep, sl, bl, timing[1]) * 2.0 ** (len(sl) - bl), mx)
             if best is None or key < best[0]:
                 best = (key, pairs, sl, mx, cost, vcost)
     if best is None:
@@ -540,7 +571,7 @@ def memory_cap_sweep(tn: TensorNetwork, caps_log2: Sequence[float], method: str 
 
 # ------------------------------------------------------------ subtree reconfiguration
 def reconfigure(leaves: Sequence[FrozenSet[int]], pairs, lg: Sequence[float], keep: FrozenSet[int],
-                cap_log2: Optional[float] = None, size: int = 8, sweeps: int = 3):
+                cap_log2: Optional[float] = None, size: int = 8, sweeps: int = 3, alpha: float = 0.0):
     """Local re-optimisation of a contraction tree (the path stays a tree over the
     same leaves with the same output).
 
@@ -585,7 +616,10 @@ def reconfigure(leaves: Sequence[FrozenSet[int]], pairs, lg: Sequence[float], ke
 
     def step_cost(v: int) -> float:
         a, b = child[v]
-        return 2.0 ** weight(mask[a] | mask[b])
+        c = 2.0 ** weight(mask[a] | mask[b])
+        if alpha:
+            c += alpha * (2.0 ** weight(mask[a]) + 2.0 ** weight(mask[b]) + 2.0 ** weight(mask[v]))
+        return c
 
     def try_node(v: int) -> bool:
         nonlocal nxt
@@ -613,6 +647,8 @@ def reconfigure(leaves: Sequence[FrozenSet[int]], pairs, lg: Sequence[float], ke
         for S in range(1, full + 1):
             out[S] = union[S] & (union[full ^ S] | mask[v])
         wout = [weight(out[S]) for S in range(full + 1)]
+        # a merge's memory term: both operands read, the result written
+        mem = [alpha * 2.0 ** x for x in wout] if alpha else None
         best = [0.0] * (full + 1)
         split = [0] * (full + 1)
         for S in range(1, full + 1):
@@ -628,6 +664,8 @@ def reconfigure(leaves: Sequence[FrozenSet[int]], pairs, lg: Sequence[float], ke
                 if sub & low:
                     rest = S ^ sub
                     c = best[sub] + best[rest]
+                    if mem is not None:
+                        c += mem[sub] + mem[rest] + mem[S]
                     if c < bc:
                         c += 2.0 ** weight(out[sub] | out[rest])
                         if c < bc:
@@ -741,3 +779,46 @@ def slice_and_reconfigure(leaves, pairs, lg, keep, n_edges: int, cap_log2: float
         # under the cap (capping it here was measured to give worse trees)
         pairs = reconfigure(stripped, pairs, lg, keep, size=size)
     return refine_sliced(leaves, pairs, lg, keep, sl, cap_log2=cap_log2, size=size)
+
+
+# ------------------------------------------------------------ time objective
+
+
+def batched_leaves(leaves, sliced, lg, keep, batch_log2: int):
+    """The network as one batch of 2^batch_log2 slices runs it: sliced bonds
+    removed, and a batch edge (id len(lg), an output edge) on every leaf that
+    held a sliced bond, so that every slice-dependent tensor carries it and
+    the rest do not.  Returns (leaves, lg, keep)."""
+    sl = set(sliced)
+    eb = len(lg)
+    out = [frozenset(x - sl) | (frozenset((eb,)) if x & sl else frozenset()) for x in leaves]
+    return out, list(lg) + [float(batch_log2)], frozenset(keep) | {eb}
+
+
+def time_cost(leaves, pairs, lg, keep, sliced, batch_log2: int, alpha: float) -> float:
+    """Estimated time of one batch of 2^batch_log2 slices, in multiply-adds:
+    over every step, its multiply-adds plus alpha x the elements it reads and
+    writes (both operands and the result), each at its batched size -- a step
+    that depends on no sliced bond runs once per batch, unbatched."""
+    bl, blg, bkeep = batched_leaves(leaves, sliced, lg, keep, batch_log2)
+    nodes = replay(bl, pairs, bkeep)
+    size = lambda s: 2.0 ** sum(blg[e] for e in s)  # noqa: E731
+    total = 0.0
+    for t, (i, j) in enumerate(pairs):
+        c = nodes[len(leaves) + t]
+        total += size(nodes[i] | nodes[j]) + alpha * (size(nodes[i]) + size(nodes[j]) + size(c))
+    return total
+
+
+def retime(leaves, pairs, lg, keep, sliced, batch_log2: int, alpha: float = ALPHA_TC, size: int = 10):
+    """Subtree reconfiguration of a sliced tree for ``time_cost``: the batched
+    network (``batched_leaves``) re-contracted with every step costing its
+    multiply-adds plus alpha x the elements of its operands and result, no
+    batched intermediate larger than the tree's largest.  On the GB300 the
+    flop-minimal trees of shallow circuits are bound by HBM (their steps move
+    many elements per multiply-add), so fewer bytes for more flops is faster.
+    Returns the new SSA pairs."""
+    bl, blg, bkeep = batched_leaves(leaves, sliced, lg, keep, batch_log2)
+    nodes = replay(bl, pairs, bkeep)
+    cap = max(sum(blg[e] for e in s) for s in nodes)
+    return reconfigure(bl, pairs, blg, bkeep, cap_log2=cap, size=size, alpha=alpha)

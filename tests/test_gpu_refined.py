@@ -1,10 +1,17 @@
-"""The refined contraction tree of the 24-qubit, 14-cycle workload (greedy and
-bisection trees re-optimised by subtree reconfiguration, six sliced bonds
-chosen two at a time): the bench's default plan.  Its steps are skinnier than
-the greedy tree's (batched 4096 x 4096 x 16 x 16, 2^23 x 4 x 4), which is where
-the narrow-tile epilogue groups, 16-byte epilogue stores, row-paired
-tensor-core steps and the small-K row kernel run.  All 64 slices against the
-FP64 state vector, complex64 and fp16, and the fp16 selection's XEB."""
+"""The refined contraction trees of the 24-qubit, 14-cycle workload against the
+FP64 state vector: all 64 slices, complex64 and fp16, and the fp16
+selection's XEB.
+
+* "refined": greedy and bisection trees re-optimised by subtree
+  reconfiguration for the fewest multiply-adds, six sliced bonds chosen two at
+  a time.  Its steps are skinny (batched 4096 x 4096 x 16 x 16, 2^23 x 4 x 4):
+  narrow-tile epilogue groups, 16-byte epilogue stores, row-paired
+  tensor-core steps and the small-K row kernel run here.
+* "time" (the bench's default tree): the same trees re-optimised for the
+  estimated time of one 64-slice batch (multiply-adds plus 145 x the elements
+  each step moves), where slice-independent subtrees run once per batch.  It
+  is run as the bench runs it (every step of every batch, nothing hoisted)
+  and with slice-independent subtrees hoisted to plan creation."""
 import os
 
 import numpy as np
@@ -17,8 +24,8 @@ from parity_checks import assert_amplitudes_close
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def refined(sv_grid4x6):
+@pytest.fixture(scope="module", params=["time", "refined"])
+def tree(request, sv_grid4x6):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -26,27 +33,36 @@ def refined(sv_grid4x6):
     __graft_entry__.build()
     from paper_2406_18889_gb300 import engine as E
     w, psi = sv_grid4x6
-    prep = E.prepare(w, refine=True, method="both", workers=len(os.sched_getaffinity(0)))
+    kw = dict(objective="time", batch_log2=6) if request.param == "time" else {}
+    prep = E.prepare(w, refine=True, method="both", workers=len(os.sched_getaffinity(0)), **kw)
     greedy = E.prepare(w)
-    assert prep.tree.cost_per_slice < 0.2 * greedy.tree.cost_per_slice  # ~10x fewer MACs per sub-network
+    if request.param == "refined":
+        assert prep.tree.cost_per_slice < 0.2 * greedy.tree.cost_per_slice  # ~10x fewer MACs per sub-network
     assert len(prep.tree.sliced_edges) == 6
     ref, _ = sv.block_amplitudes(psi, w.n_qubits, w.open_qubits, w.closed_qubits, w.closed_bits)
-    return E, w, psi, ref, prep
+    return request.param, E, w, psi, ref, prep
 
 
-@pytest.mark.parametrize("prec,tol", [("c64", 1e-5), ("fp16", 3e-3)])
-def test_refined_tree_against_statevector(refined, prec, tol):
+@pytest.mark.parametrize("prec,tol,hoist", [("c64", 1e-5, False), ("fp16", 3e-3, False), ("fp16", 3e-3, True)])
+def test_tree_against_statevector(tree, prec, tol, hoist):
     import torch
     from paper_2406_18889_gb300 import binding as B
-    E, w, psi, ref, prep = refined
-    plan = E.Plan(prep.tn, prep.tree, prec=prec, flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=64)
+    name, E, w, psi, ref, prep = tree
+    if name == "refined" and not hoist and prec == "fp16":
+        pytest.skip("the refined tree's fp16 case runs hoisted (its slice-independent part is tiny)")
+    plan = E.Plan(prep.tn, prep.tree, prec=prec, flags=B.TN_FLAG_HOIST_INVARIANT if hoist else 0,
+                  max_slice_batch=64)
     kinds = plan.steps()["kinds"]
     if prec == "fp16":
         assert ((kinds & 8) > 0).sum() >= 4
         assert ((kinds & 256) > 0).sum() >= 1, "no row-paired tensor-core step"
+    if hoist:
+        assert ((kinds & 4) > 0).sum() >= 1, "nothing hoisted"
+    else:
+        assert ((kinds & 4) > 0).sum() == 0
     amps = plan.contract()
     B.tn_plan_status(plan.handle, torch.cuda.current_stream().cuda_stream)
-    assert_amplitudes_close(amps.cpu().numpy(), ref, tol, f"refined tree, {prec}")
+    assert_amplitudes_close(amps.cpu().numpy(), ref, tol, f"{name} tree, {prec}, hoist={hoist}")
     base = torch.as_tensor(w.block_base(), device="cuda")
     idx, _ = E.topk(amps, w.k, 1.0, base, w.open_bit_pos())
     ri, _ = pp.topk_blocks(ref, w.k, 1.0, w.block_base(), w.open_bit_pos())
@@ -56,12 +72,11 @@ def test_refined_tree_against_statevector(refined, prec, tol):
     plan.close()
 
 
-def test_refined_tree_batches_agree(refined):
-    # slice batch 16 (four batches) against batch 64: the same per-slice
-    # amplitudes summed in FP64 in another grouping
-    from paper_2406_18889_gb300 import binding as B
-    E, w, psi, ref, prep = refined
-    a = E.Plan(prep.tn, prep.tree, prec="fp16", flags=B.TN_FLAG_HOIST_INVARIANT, max_slice_batch=16)
+def test_tree_batches_agree(tree):
+    # slice batch 16 (four batches) against the state vector: the same
+    # per-slice amplitudes summed in FP64 in another grouping
+    name, E, w, psi, ref, prep = tree
+    a = E.Plan(prep.tn, prep.tree, prec="fp16", flags=0, max_slice_batch=16)
     got = a.contract().cpu().numpy()
-    assert_amplitudes_close(got, ref, 3e-3, "refined tree, fp16, batch 16")
+    assert_amplitudes_close(got, ref, 3e-3, f"{name} tree, fp16, batch 16")
     a.close()
