@@ -360,7 +360,7 @@ def run_ours(args):
     split_slices = world > 1 and args.partition == "slices"
     w = rank_workload(0 if split_slices else rank)
     prep = prepare_path(w, args.path, args.batch)
-    hoist = B.TN_FLAG_HOIST_INVARIANT if args.hoist else 0
+    hoist = (B.TN_FLAG_HOIST_INVARIANT if args.hoist else 0) | (B.TN_FLAG_SERIAL_GRAPH if args.serial_graph else 0)
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | hoist
     plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
     S = plan.n_slices_total
@@ -547,6 +547,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
                    "hoist_invariant": bool(args.hoist), "autotune": bool(args.autotune),
+                   "graph": "one chain" if args.serial_graph else "concurrent branches",
                    "path": PATH_DESC[args.path],
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": (f"the 64 slices split over {world} GPUs, FP64 partials gathered and summed "
@@ -734,6 +735,8 @@ def main(argv=None):
     ap.add_argument("--hoist", action="store_true",
                     help="contract slice-independent subtrees once, at plan creation, instead of once in every "
                          "batch (the default: every step does all of its batch's work)")
+    ap.add_argument("--serial-graph", action="store_true",
+                    help="one chain of launches per batch graph instead of concurrent branches")
     ap.add_argument("--path", default="time", choices=["time", "refined", "greedy"],
                     help="contraction tree: time (default; flop-refined greedy and bisection trees re-optimised "
                          "for the estimated time of one slice batch: multiply-adds plus the elements moved), "

@@ -77,6 +77,12 @@ typedef enum {
                                         calibration batch's amplitudes most, until their relative L2
                                         against a complex64 pass is within hilo_tol (selection at
                                         tn_plan_create, see tn_plan_precision) */
+#define TN_FLAG_SERIAL_GRAPH 0x80u   /* the batch graph runs every launch in one chain.  Default:
+                                        the launches are spread over concurrent graph branches, each
+                                        waiting only for the launches whose workspace ranges it
+                                        shares (its operands, or memory they freed), so that the
+                                        slice-independent subtrees -- which have a workspace region
+                                        of their own -- overlap the rest of the batch */
 
 typedef struct tn_plan_s* tn_plan_t;
 

@@ -27,6 +27,7 @@ TN_FLAG_PLAN_ONLY = 0x4
 TN_FLAG_HILO = 0x8
 TN_FLAG_FINE_ACC = 0x20
 TN_FLAG_HILO_AUTO = 0x40
+TN_FLAG_SERIAL_GRAPH = 0x80
 
 EXPORTS = ("tn_plan_create", "tn_plan_destroy", "tn_plan_query", "tn_plan_steps",
            "tn_contract_slices", "tn_contract_slices_batched", "tn_contract_slices_profile",

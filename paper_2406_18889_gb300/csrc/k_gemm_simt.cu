@@ -215,6 +215,8 @@ __device__ __forceinline__ I run_off(const Runs& R, I i) {
   return o;
 }
 
+constexpr int64_t kDirectVecMin = int64_t(152) * 256 * 4;  // outputs from which a thread takes four
+
 template <class In, class Out, class I>
 __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bool hilo) {
   using TI = typename In::T;
@@ -235,7 +237,9 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
     }
   // four consecutive outputs per thread when C's fastest run (pos 0) spans >= 4
   // elements: they differ only in that run's digit, i.e. in one group's index
-  const bool vec = p.c_dec.n > 0 && p.c_dec.pos[0] == 0 && p.c_dec.lg[0] >= 2 && (total & 3) == 0;
+  // (only when the grid is full anyway: small steps take one output per thread)
+  const bool vec = p.c_dec.n > 0 && p.c_dec.pos[0] == 0 && p.c_dec.lg[0] >= 2 && (total & 3) == 0 &&
+                   total >= (I)kDirectVecMin;
   const int g0 = p.c_dec.grp[0];
   const I step0 = I(1) << p.c_dec.shift[0];
   const I per = vec ? 4 : 1;
@@ -257,7 +261,19 @@ __global__ void __launch_bounds__(256) gemm_direct(GemmParams p, float scale, bo
         for (int k = 0; k < 4; ++k)
           if (k < K) cmac(acc, In::ld(a[ak[k]]), In::ld(b[bk[k]]));
       } else {
-        for (int k = 0; k < K; ++k)
+        // four k at a time, their eight loads issued before the multiply-adds
+        int k = 0;
+        for (; k + 4 <= K; k += 4) {
+          TI av[4], bv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            av[q] = a[run_off<I>(p.a_k, (I)(k + q))];
+            bv[q] = b[run_off<I>(p.b_k, (I)(k + q))];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cmac(acc, In::ld(av[q]), In::ld(bv[q]));
+        }
+        for (; k < K; ++k)
           cmac(acc, In::ld(a[run_off<I>(p.a_k, (I)k)]), In::ld(b[run_off<I>(p.b_k, (I)k)]));
       }
       store_out<Out>(C, (TO*)p.C2, (int64_t)(x + v), make_float2(acc.x * scale, acc.y * scale), hilo);
@@ -944,7 +960,7 @@ void launch_typed(const GemmParams& p, float scale, cudaStream_t s, bool hilo = 
     if (p.K <= 4) return launch_smallk<Out>(p, scale, s, hilo, nullptr);
   }
   if (p.K <= 4 || (p.M < 16 && p.N < 16) || outputs * p.K < (1 << 16)) {
-    int64_t blocks = std::min<int64_t>((outputs / 4 + 255) / 256 + 1, 152 * 64);
+    int64_t blocks = std::min<int64_t>((outputs >= kDirectVecMin ? outputs / 4 : outputs) / 256 + 1, 152 * 64);
     if (p.elems_max < (int64_t(1) << 31))
       gemm_direct<In, Out, int32_t><<<(unsigned)blocks, 256, 0, s>>>(p, scale, hilo);
     else

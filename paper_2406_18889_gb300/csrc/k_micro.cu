@@ -77,21 +77,48 @@ __global__ void __launch_bounds__(kMicroThreads) micro_kernel(const MicroStep* _
     const int K = d.K, total = 1 << nb, kind = d.out_kind;
     const bool hilo = d.out_hilo != 0;
     const float scale = d.scale;
-    for (int x = threadIdx.x; x < total; x += blockDim.x) {
-      const int2 l = tab[x & 127], h = tab[128 + (x >> 7)];
-      const int ao = l.x + h.x, bo = l.y + h.y;
-      float2 acc = make_float2(0.f, 0.f);
+    int ak[4], bk[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < K) cmac_m(acc, A[ao + d.ak[k]], B[bo + d.bk[k]]);
-      acc.x *= scale;
-      acc.y *= scale;
-      if (kind == 2)
-        reinterpret_cast<float2*>(C)[x] = acc;
-      else if (kind == 0)
-        store16<__half2>(C, C2, x, acc, hilo);
-      else
-        store16<__nv_bfloat162>(C, C2, x, acc, hilo);
+    for (int k = 0; k < 4; ++k) {
+      ak[k] = d.ak[k];
+      bk[k] = d.bk[k];
+    }
+    // kU outputs per thread per pass, all of their operand loads issued before
+    // any arithmetic: a step is a few dependent memory round trips, not one
+    // per output
+    constexpr int kU = 4;
+    for (int x0 = threadIdx.x; x0 < total; x0 += kU * kMicroThreads) {
+      float2 av[kU][4], bv[kU][4];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int x = x0 + u * kMicroThreads;
+        const int xs = x < total ? x : 0;
+        const int2 l = tab[xs & 127], h = tab[128 + (xs >> 7)];
+        const int ao = l.x + h.x, bo = l.y + h.y;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool on = k < K && x < total;
+          av[u][k] = on ? A[ao + ak[k]] : make_float2(0.f, 0.f);
+          bv[u][k] = on ? B[bo + bk[k]] : make_float2(0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int x = x0 + u * kMicroThreads;
+        if (x >= total) break;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < K) cmac_m(acc, av[u][k], bv[u][k]);
+        acc.x *= scale;
+        acc.y *= scale;
+        if (kind == 2)
+          reinterpret_cast<float2*>(C)[x] = acc;
+        else if (kind == 0)
+          store16<__half2>(C, C2, x, acc, hilo);
+        else
+          store16<__nv_bfloat162>(C, C2, x, acc, hilo);
+      }
     }
     __syncthreads();  // this step's results are visible to the group's next step
   }

@@ -126,6 +126,8 @@ Plan::~Plan() {
   if (device >= 0) drop_batched_graphs(serial);
   if (graph) cudaGraphExecDestroy(graph);
   if (capture_stream) cudaStreamDestroy(capture_stream);
+  for (cudaStream_t st : branch_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : unit_events) cudaEventDestroy(e);
   if (d_plan) cudaFree(d_plan);
   if (d_slice_ids) cudaFree(d_slice_ids);
   if (d_n_valid) cudaFree(d_n_valid);
@@ -446,47 +448,86 @@ MemPlan plan_memory(const Plan& P, bool c64, const std::vector<std::vector<int>>
     }
   M.create_scratch = (tmax || bmax) ? round_up(tmax, 256) + bmax : 0;
   M.plan_bytes = poff;
-  Arena ws;
+  // Two arenas: the batch's slice-independent steps (and fused small-step
+  // groups) allocate in `wi`, everything else in `ws`; the workspace is
+  // [wi | ws].  Regions of one arena are reused only within it, so the
+  // slice-independent subtrees share no memory with the rest of the batch
+  // but the results the slice-dependent steps read from them, and can run
+  // concurrently with it (the batch graph's branches).
+  Arena ws, wi;
+  M.wsz.assign(nn, 0);
+  M.tmp_sz.assign(P.steps.size(), 0);
+  M.bx_sz.assign(P.steps.size(), 0);
+  std::vector<char> in_wi(nn, 0), tmp_wi(P.steps.size(), 0), bx_wi(P.steps.size(), 0);
+  auto alloc_node = [&](int x, int64_t bytes, bool inv) {
+    M.off[x] = (inv ? wi : ws).alloc(bytes);
+    M.wsz[x] = round_up(std::max<int64_t>(bytes, 1), 256);
+    in_wi[x] = inv ? 1 : 0;
+  };
+  auto release_node = [&](int x) {
+    if (!M.in_plan[x]) (in_wi[x] ? wi : ws).release(M.off[x]);
+  };
   for (int i = 0; i < P.n_leaves; ++i)
     if (P.nodes[i].variant) {
       M.gather_node.push_back(i);
-      M.off[i] = ws.alloc(node_bytes(P, i, c64));
+      alloc_node(i, node_bytes(P, i, c64), false);
     }
   if (M.micro) {
     // the fused small steps run together right after the gather: each result
     // gets its own region; their operands and inner results are free afterwards
-    for (const Step& S : P.steps)
-      if (S.micro) M.off[S.c] = ws.alloc(node_bytes(P, S.c, c64));
+    for (size_t g = 0; g < P.micro_groups.size(); ++g)
+      for (int t : P.micro_groups[g]) {
+        const Step& S = P.steps[t];
+        alloc_node(S.c, node_bytes(P, S.c, c64), (int)g < P.n_micro_inv);
+      }
     for (const Step& S : P.steps)
       if (S.micro)
         for (int x : {S.a, S.b})
-          if (!M.in_plan[x] && (P.nodes[x].leaf || P.steps[x - P.n_leaves].micro)) ws.release(M.off[x]);
+          if (!M.in_plan[x] && (P.nodes[x].leaf || P.steps[x - P.n_leaves].micro)) release_node(x);
   }
   for (size_t t = 0; t < P.steps.size(); ++t) {
     const Step& S = P.steps[t];
     if (S.hoisted || (M.micro && S.micro)) continue;
+    const bool inv = !S.variant;
+    Arena& A = inv ? wi : ws;
     if (!c64 && S.fuse_expand) {
       // the result is stored only as its consumer's expanded operand
       const Step& U = P.steps[P.nodes[S.c].consumer];
       TcRoles r = tc_roles(U);
-      M.off[S.c] = ws.alloc(expanded_b_bytes(U.gp.nbt, r.N, r.K) * (U.hilo ? 2 : 1));
+      alloc_node(S.c, expanded_b_bytes(U.gp.nbt, r.N, r.K) * (U.hilo ? 2 : 1), inv);
     } else {
-      M.off[S.c] = ws.alloc(node_bytes(P, S.c, c64));
+      alloc_node(S.c, node_bytes(P, S.c, c64), inv);
     }
     int64_t tmp = -1, bx = -1;
-    if (S.post_perm) tmp = M.tmp_off[t] = ws.alloc(node_bytes(P, S.c, c64));
+    if (S.post_perm) {
+      tmp = M.tmp_off[t] = A.alloc(node_bytes(P, S.c, c64));
+      M.tmp_sz[t] = round_up(std::max<int64_t>(node_bytes(P, S.c, c64), 1), 256);
+      tmp_wi[t] = inv;
+    }
     if (!c64 && S.tc) {
       TcRoles r = tc_roles(S);
-      if (S.b_fused)
-        M.bx_off[t] = M.off[r.b_node];
-      else
-        bx = M.bx_off[t] = ws.alloc(tc_bx_bytes(S, r));
+      if (!S.b_fused) {
+        bx = M.bx_off[t] = A.alloc(tc_bx_bytes(S, r));
+        M.bx_sz[t] = round_up(std::max<int64_t>(tc_bx_bytes(S, r), 1), 256);
+        bx_wi[t] = inv;
+      }
     }
-    if (tmp >= 0) ws.release(tmp);
-    if (bx >= 0) ws.release(bx);
-    for (int x : {S.a, S.b})
-      if (!M.in_plan[x]) ws.release(M.off[x]);
+    if (tmp >= 0) A.release(tmp);
+    if (bx >= 0) A.release(bx);
+    for (int x : {S.a, S.b}) release_node(x);
   }
+  // place the slice-dependent arena after the slice-independent one
+  M.inv_bytes = round_up(wi.peak, 256);
+  for (int x = 0; x < nn; ++x)
+    if (!M.in_plan[x] && M.off[x] >= 0 && !in_wi[x]) M.off[x] += M.inv_bytes;
+  for (size_t t = 0; t < P.steps.size(); ++t) {
+    const Step& S = P.steps[t];
+    if (S.hoisted) continue;
+    if (M.tmp_off[t] >= 0 && !tmp_wi[t]) M.tmp_off[t] += M.inv_bytes;
+    if (M.bx_off[t] >= 0 && !bx_wi[t]) M.bx_off[t] += M.inv_bytes;
+    if (!c64 && S.tc && S.b_fused && !(M.micro && S.micro)) M.bx_off[t] = M.off[tc_roles(S).b_node];
+  }
+  ws.peak += M.inv_bytes;
   M.ws_bytes = round_up(std::max<int64_t>(ws.peak, 256), 256);
   // gather table (offsets relative to the plan-memory and workspace bases)
   for (int i : M.gather_node) {
@@ -654,37 +695,195 @@ void enqueue_step(const Exec& X, size_t t, cudaStream_t s, Recorder& R, unsigned
   if (amax) launch_amax_c64(dst, P.nodes[S.c].elems, amax + S.c, s);
 }
 
+void enqueue_gather(const Exec& X, cudaStream_t s, Recorder& R) {
+  const Plan& P = X.P;
+  if (X.M.gather.empty()) return;
+  double bytes = 0;
+  for (auto& g : X.M.gather) bytes += 2.0 * g.rest * P.B * 8.0;
+  R.begin(2, 0, bytes);
+  launch_gather_leaves(P.d_gather, (int)X.M.gather.size(), X.M.gather_max_rest, P.d_slice_ids, P.B, X.pb, X.wb, s,
+                       8);
+  R.end();
+}
+
+// fused small-step groups [g0, g1)
+void enqueue_micro(const Exec& X, int g0, int g1, cudaStream_t s, Recorder& R) {
+  const Plan& P = X.P;
+  if (g0 >= g1) return;
+  TN_CHECK(P.d_micro, TN_ERR_INVALID_ARG, "internal: fused small steps unavailable");
+  double flops = 0, bytes = 0;
+  for (int g = g0; g < g1; ++g)
+    for (int t : P.micro_groups[g]) {
+      const Step& S = P.steps[t];
+      flops += 8.0 * S.cost;
+      bytes += (double)(node_bytes(P, S.a, X.M.c64) + node_bytes(P, S.b, X.M.c64) + node_bytes(P, S.c, X.M.c64));
+    }
+  R.begin(0, flops, bytes);
+  launch_micro(P.d_micro, P.d_micro_start + g0, g1 - g0, X.pb, X.wb, s);
+  R.end();
+}
+
+void enqueue_accumulate(const Exec& X, void* amps, int accumulate, cudaStream_t s, Recorder& R) {
+  const Plan& P = X.P;
+  R.begin(3, 0, 8.0 * (double)P.nodes[P.root].elems + 16.0 * P.G * P.J * (accumulate ? 2 : 1));
+  launch_accumulate_c64(X.base(P.root), P.root_sb, P.root_sg, P.root_sj, P.G, P.J, P.d_n_valid, P.B, amps,
+                        accumulate, s, ldexp(1.0, P.nodes[P.root].exp2));
+  R.end();
+}
+
 void enqueue_batch_mem(const Plan& P, const MemPlan& M, char* pb, void* ws, void* amps, int accumulate,
                        cudaStream_t s, std::vector<LaunchRecord>* rec, unsigned* amax, bool hoisted_too) {
   Exec X{P, M, pb, (char*)ws};
   Recorder R{rec, s};
-  if (!M.gather.empty()) {
-    double bytes = 0;
-    for (auto& g : M.gather) bytes += 2.0 * g.rest * P.B * 8.0;
-    R.begin(2, 0, bytes);
-    launch_gather_leaves(P.d_gather, (int)M.gather.size(), M.gather_max_rest, P.d_slice_ids, P.B, pb,
-                         (char*)ws, s, 8);
-    R.end();
-  }
+  enqueue_gather(X, s, R);
   if (amax)
     for (int i = 0; i < P.n_leaves; ++i) launch_amax_c64(X.base(i), P.nodes[i].elems, amax + i, s);
   if (M.micro) {
-    TN_CHECK(P.d_micro && !amax, TN_ERR_INVALID_ARG, "internal: fused small steps unavailable");
-    R.begin(0, P.micro_flops, P.micro_bytes);
-    launch_micro(P.d_micro, P.d_micro_start, (int)P.micro_groups.size(), pb, (char*)ws, s);
-    R.end();
+    TN_CHECK(!amax, TN_ERR_INVALID_ARG, "internal: fused small steps during calibration");
+    enqueue_micro(X, 0, (int)P.micro_groups.size(), s, R);
   }
   for (size_t t = 0; t < P.steps.size(); ++t) {
     if (P.steps[t].hoisted && !hoisted_too) continue;
     if (M.micro && P.steps[t].micro) continue;
     enqueue_step(X, t, s, R, amax);
   }
-  if (amps) {
-    R.begin(3, 0, 8.0 * (double)P.nodes[P.root].elems + 16.0 * P.G * P.J * (accumulate ? 2 : 1));
-    launch_accumulate_c64(X.base(P.root), P.root_sb, P.root_sg, P.root_sj, P.G, P.J, P.d_n_valid, P.B, amps,
-                          accumulate, s, ldexp(1.0, P.nodes[P.root].exp2));
-    R.end();
+  if (amps) enqueue_accumulate(X, amps, accumulate, s, R);
+}
+
+// ---------------------------------------------------------------- concurrent batch graph
+// One batch as launch units -- the gather (kind 0), the slice-independent and
+// the other fused small-step groups (1, 2), one step each (3: its expansion,
+// GEMM and transpose) -- in the order of the sequential schedule.  Two units
+// depend on each other when the workspace ranges they touch (read or write)
+// overlap: the true data dependencies, and the reuse of a region freed by an
+// earlier unit.  Plan memory is read-only during a batch.
+constexpr int kBranches = 4;
+using Ranges = std::vector<std::pair<int64_t, int64_t>>;
+
+void plan_batch_graph(Plan& P) {
+  const MemPlan& M = P.mem;
+  std::vector<Ranges> rg;
+  P.unit_kind.clear();
+  P.unit_step.clear();
+  auto add = [](Ranges& r, int64_t off, int64_t bytes) {
+    if (off >= 0 && bytes > 0) r.push_back({off, off + bytes});
+  };
+  auto node = [&](Ranges& r, int x) {
+    if (!M.in_plan[x]) add(r, M.off[x], M.wsz[x]);
+  };
+  auto unit = [&](int kind, int step) {
+    P.unit_kind.push_back(kind);
+    P.unit_step.push_back(step);
+    rg.emplace_back();
+    return &rg.back();
+  };
+  if (!M.gather.empty()) {
+    Ranges* r = unit(0, -1);
+    for (int i : M.gather_node) node(*r, i);
   }
+  if (M.micro)
+    for (int part = 0; part < 2; ++part) {
+      const int g0 = part ? P.n_micro_inv : 0, g1 = part ? (int)P.micro_groups.size() : P.n_micro_inv;
+      if (g0 >= g1) continue;
+      Ranges* r = unit(1 + part, -1);
+      for (int g = g0; g < g1; ++g)
+        for (int t : P.micro_groups[g])
+          for (int x : {P.steps[t].a, P.steps[t].b, P.steps[t].c}) node(*r, x);
+    }
+  for (size_t t = 0; t < P.steps.size(); ++t) {
+    const Step& S = P.steps[t];
+    if (S.hoisted || (M.micro && S.micro)) continue;
+    Ranges* r = unit(3, (int)t);
+    for (int x : {S.a, S.b, S.c}) node(*r, x);
+    if (S.post_perm) add(*r, M.tmp_off[t], M.tmp_sz[t]);
+    add(*r, M.bx_off[t], M.bx_sz[t]);
+  }
+  const int n = (int)rg.size();
+  auto overlap = [&](int i, int j) {
+    for (auto& a : rg[i])
+      for (auto& b : rg[j])
+        if (a.first < b.second && b.first < a.second) return true;
+    return false;
+  };
+  // branches: a unit continues the branch whose last unit is its latest
+  // dependency; else takes an unused branch; else the branch idle longest.
+  // It waits, on every other branch, for the latest unit it depends on.
+  P.unit_branch.assign(n, 0);
+  P.unit_waits.assign(n, {});
+  std::vector<int> tail(kBranches, -1);
+  for (int j = 0; j < n; ++j) {
+    std::vector<char> dep(j, 0);
+    for (int i = 0; i < j; ++i) dep[i] = overlap(i, j) ? 1 : 0;
+    int b = -1;
+    for (int k = 0; k < kBranches; ++k)
+      if (tail[k] >= 0 && dep[tail[k]] && (b < 0 || tail[k] > tail[b])) b = k;
+    for (int k = 0; k < kBranches && b < 0; ++k)
+      if (tail[k] < 0) b = k;
+    if (b < 0) {
+      b = 0;
+      for (int k = 1; k < kBranches; ++k)
+        if (tail[k] < tail[b]) b = k;
+    }
+    std::vector<int> last(kBranches, -1);
+    for (int i = 0; i < j; ++i)
+      if (dep[i] && P.unit_branch[i] != b) last[P.unit_branch[i]] = std::max(last[P.unit_branch[i]], i);
+    for (int k = 0; k < kBranches; ++k)
+      if (last[k] >= 0) P.unit_waits[j].push_back(last[k]);
+    P.unit_branch[j] = b;
+    tail[b] = j;
+  }
+}
+
+// The branch streams and events of the batch graph (created before a capture:
+// creating them is not a stream operation a capture may record).
+void make_graph_resources(Plan& P) {
+  while ((int)P.branch_streams.size() < kBranches - 1) {
+    cudaStream_t st = nullptr;
+    TN_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    P.branch_streams.push_back(st);
+  }
+  while (P.unit_events.size() < P.unit_kind.size() + kBranches) {
+    cudaEvent_t e = nullptr;
+    TN_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    P.unit_events.push_back(e);
+  }
+}
+
+// Queue one batch on `s` (being captured) with the units spread over the
+// plan's branch streams; every branch joins `s` before the slice sum.
+void enqueue_batch_graph(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t s) {
+  const MemPlan& M = P.mem;
+  Exec X{P, M, (char*)P.d_plan, (char*)ws};
+  Recorder R{nullptr, s};
+  const int n = (int)P.unit_kind.size();
+  TN_CHECK((int)P.branch_streams.size() == kBranches - 1 && (int)P.unit_events.size() >= n + kBranches,
+           TN_ERR_INVALID_ARG, "internal: batch graph streams not created");
+  cudaEvent_t fork = P.unit_events[n];
+  TN_CUDA(cudaEventRecord(fork, s));
+  std::vector<char> used(kBranches, 0);
+  used[0] = 1;
+  for (int j = 0; j < n; ++j) {
+    const int b = P.unit_branch[j];
+    cudaStream_t st = b ? P.branch_streams[b - 1] : s;
+    if (!used[b]) {
+      TN_CUDA(cudaStreamWaitEvent(st, fork, 0));
+      used[b] = 1;
+    }
+    for (int i : P.unit_waits[j]) TN_CUDA(cudaStreamWaitEvent(st, P.unit_events[i], 0));
+    switch (P.unit_kind[j]) {
+      case 0: enqueue_gather(X, st, R); break;
+      case 1: enqueue_micro(X, 0, P.n_micro_inv, st, R); break;
+      case 2: enqueue_micro(X, P.n_micro_inv, (int)P.micro_groups.size(), st, R); break;
+      default: enqueue_step(X, (size_t)P.unit_step[j], st, R, nullptr); break;
+    }
+    TN_CUDA(cudaEventRecord(P.unit_events[j], st));
+  }
+  for (int b = 1; b < kBranches; ++b)
+    if (used[b]) {
+      TN_CUDA(cudaEventRecord(P.unit_events[n + b], P.branch_streams[b - 1]));
+      TN_CUDA(cudaStreamWaitEvent(s, P.unit_events[n + b], 0));
+    }
+  if (amps) enqueue_accumulate(X, amps, accumulate, s, R);
 }
 
 }  // namespace
@@ -977,6 +1176,12 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     }
     for (size_t t = 0; t < P.steps.size(); ++t)
       if (group[t] >= 0) P.micro_groups[group[t]].push_back((int)t);
+    // slice-independent groups (their last step, the group's root, depends on
+    // no sliced bond) first: they run in a launch of their own
+    std::stable_partition(P.micro_groups.begin(), P.micro_groups.end(),
+                          [&](const std::vector<int>& g) { return !P.steps[g.back()].variant; });
+    P.n_micro_inv = 0;
+    for (const auto& g : P.micro_groups) P.n_micro_inv += P.steps[g.back()].variant ? 0 : 1;
   }
   // leaf storage layouts (variant leaves: sliced edges outermost, then the batch copy's order)
   std::vector<std::vector<int>> leaf_src_layout(P.n_leaves);
@@ -999,6 +1204,7 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     P.peak_intermediate_bytes = std::max(P.peak_intermediate_bytes, per(S.c));
   }
   P.mem = plan_memory(P, P.skind == KIND_C64, leaf_src_layout, true);
+  plan_batch_graph(P);
   if (P.skind != KIND_C64) {
     const MemPlan Mc = plan_memory(P, true, leaf_src_layout, false);
     P.calib_bytes = Mc.plan_bytes + Mc.ws_bytes + total_leaf_elems * 16;
@@ -1213,10 +1419,14 @@ void run_batch(Plan& P, void* ws, void* amps, int accumulate, cudaStream_t strea
       P.graph = nullptr;
     }
     cudaGraph_t g = nullptr;
+    if (!(P.flags & TN_FLAG_SERIAL_GRAPH)) make_graph_resources(P);
     TN_CUDA(cudaStreamBeginCapture(P.capture_stream, cudaStreamCaptureModeThreadLocal));
     try {
-      enqueue_batch_mem(P, P.mem, (char*)P.d_plan, ws, amps, accumulate, P.capture_stream, nullptr, nullptr,
-                        false);
+      if (P.flags & TN_FLAG_SERIAL_GRAPH)
+        enqueue_batch_mem(P, P.mem, (char*)P.d_plan, ws, amps, accumulate, P.capture_stream, nullptr, nullptr,
+                          false);
+      else
+        enqueue_batch_graph(P, ws, amps, accumulate, P.capture_stream);
     } catch (...) {
       cudaStreamEndCapture(P.capture_stream, &g);
       if (g) cudaGraphDestroy(g);

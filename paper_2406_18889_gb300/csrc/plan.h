@@ -62,8 +62,12 @@ struct MemPlan {
   bool micro = false;                   // small steps run fused (their results never share memory)
   std::vector<int64_t> off;             // per node: byte offset
   std::vector<char> in_plan;            // per node: plan memory (1) or workspace (0)
+  std::vector<int64_t> wsz;             // per node: workspace bytes it occupies (0 in plan memory)
   std::vector<int64_t> tmp_off;         // per step: natural-layout result before the transpose
+  std::vector<int64_t> tmp_sz;
   std::vector<int64_t> bx_off;          // per step: expanded operand of a tensor-core GEMM
+  std::vector<int64_t> bx_sz;           // (0 when the producer writes it into its own result)
+  int64_t inv_bytes = 0;                // workspace [0, inv_bytes): slice-independent steps of a batch
   std::vector<GatherLeaf> gather;       // per sliced leaf
   std::vector<int> gather_node;
   int64_t gather_max_rest = 0;
@@ -102,7 +106,8 @@ struct Plan {
   GatherLeaf* d_gather = nullptr;       // gather table (device)
   int* d_err = nullptr;                 // raised by a timed-out device wait
   // fused small steps: subtrees of micro steps, each in topological order (one CTA each)
-  std::vector<std::vector<int>> micro_groups;
+  std::vector<std::vector<int>> micro_groups;  // slice-independent groups first
+  int n_micro_inv = 0;                  // how many groups are slice-independent
   MicroStep* d_micro = nullptr;
   int* d_micro_start = nullptr;
   double micro_flops = 0, micro_bytes = 0;
@@ -119,6 +124,13 @@ struct Plan {
   void* graph_amps = nullptr;
   int graph_acc = -1;
   cudaStream_t capture_stream = nullptr;
+  // concurrent batch graph: the batch's launch units (gather, fused small
+  // steps, steps), each with its branch and the units of other branches it
+  // waits for (from the workspace ranges they touch)
+  std::vector<int> unit_kind, unit_step, unit_branch;
+  std::vector<std::vector<int>> unit_waits;
+  std::vector<cudaStream_t> branch_streams;  // branches 1.. (branch 0 is the capturing stream)
+  std::vector<cudaEvent_t> unit_events;      // one per unit, then the fork and the joins
 
   ~Plan();
 };

@@ -132,6 +132,29 @@ def greedy(leaves: Sequence[FrozenSet[int]], lg: Sequence[float], keep: FrozenSe
     return pairs
 
 
+def invariant_first(leaves: Sequence[FrozenSet[int]], pairs, sliced) -> List[Tuple[int, int]]:
+    """The same tree with every step that depends on no sliced bond listed
+    before the others, each group in its original order (still children
+    before parents: a slice-independent step only consumes slice-independent
+    tensors).  The library then gives the slice-independent subtrees their
+    own workspace region, so they can run concurrently with the rest of a
+    batch.  Returns new SSA pairs."""
+    sl = set(sliced)
+    L = len(leaves)
+    variant = [bool(set(x) & sl) for x in leaves]
+    for (i, j) in pairs:
+        variant.append(variant[i] or variant[j])
+    order = [t for t in range(len(pairs)) if not variant[L + t]] + \
+            [t for t in range(len(pairs)) if variant[L + t]]
+    new_id = {i: i for i in range(L)}
+    out: List[Tuple[int, int]] = []
+    for t in order:
+        i, j = pairs[t]
+        out.append((new_id[i], new_id[j]))
+        new_id[L + t] = L + len(out) - 1
+    return out
+
+
 def replay(leaves: Sequence[FrozenSet[int]], pairs, keep: FrozenSet[int]):
     """Edge sets of every node (leaves then steps) along ``pairs``."""
     nodes = [frozenset(s) for s in leaves]
@@ -502,6 +525,7 @@ def plan_tree(tn: TensorNetwork, n_sliced: int = 0, cap_log2: Optional[float] = 
     if best is None:
         raise ValueError("no path fits the memory cap")
     _, pairs, sl, mx, cost, vcost = best
+    pairs = invariant_first(leaves, pairs, sl)
     return Tree(pairs=pairs, sliced_edges=list(sl), log2_max_intermediate=mx,
                 cost_per_slice=cost, cost_variant_per_slice=vcost, n_leaves=len(leaves))
 

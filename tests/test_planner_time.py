@@ -96,3 +96,29 @@ def test_retime_on_the_24_qubit_tree_never_worse():
     # a full binary tree over the leaves: every node consumed exactly once
     used = [x for p in new for x in p]
     assert sorted(used) == list(range(len(leaves) + len(new) - 1))
+
+
+def test_invariant_first_keeps_the_tree():
+    # A{0,1} B{1,2} C{2,3} D{3,4}, output {0,4}, bond 3 sliced: C and D depend
+    # on the slice.  Pairs ((C,D),(A,B)) list the slice-dependent step first.
+    leaves = [frozenset({0, 1}), frozenset({1, 2}), frozenset({2, 3}), frozenset({3, 4})]
+    keep = frozenset({0, 4})
+    pairs = [(2, 3), (0, 1), (4, 5)]
+    out = P.invariant_first(leaves, pairs, [3])
+    assert out == [(0, 1), (2, 3), (5, 4)]
+    stripped = [x - {3} for x in leaves]
+    assert P.replay(stripped, out, keep)[-1] == P.replay(stripped, pairs, keep)[-1] == keep
+    # already in that order: unchanged
+    assert P.invariant_first(leaves, out, [3]) == out
+
+
+def test_plan_tree_lists_slice_independent_steps_first():
+    w = W.workload("grid4x6_d14")
+    tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    tree = P.plan_tree(tn, n_sliced=6, restarts=1)
+    sl = set(tree.sliced_edges)
+    variant = [bool(set(e) & sl) for e in tn.leaf_edges]
+    for (i, j) in tree.pairs:
+        variant.append(variant[i] or variant[j])
+    v = variant[len(tn.leaf_edges):]
+    assert v == sorted(v) and not v[0] and v[-1]
