@@ -245,11 +245,19 @@ KIND_NAMES = {0: "gemm_cuda_core", 1: "bit_permute", 2: "gather", 3: "accumulate
               4: "expand_operand", 5: "gemm_tensor_core"}
 
 
-# DRAM bytes (read + write) of the step's longest launch, per configuration
-# (path, precision, slice batch, split products, hoisting), as an ncu capture
-# of that launch measured them (dram__bytes_read.sum + dram__bytes_write.sum);
-# a configuration without an entry, or whose kernels changed since, reports null
-DOMINANT_TRAFFIC = {}
+# DRAM bytes (read + write) of the tensor-core launches that can be a step's
+# longest, per configuration (path, precision, slice batch, split products,
+# hoisting) and the launch's algorithmic bytes, as one ncu capture of a step
+# measured them (dram__bytes_read.sum + dram__bytes_write.sum; the tree as
+# planned on the GB300 host).  The time tree's two longest launches take
+# ~0.21 ms each, so either can be the longest in a run.  A configuration or
+# launch without an entry, or whose kernels changed since, reports null.
+DOMINANT_TRAFFIC = {
+    ("time", "fp16", 64, False, False): {
+        1141374976: 70072320 + 1009223936,    # tile width 256: reads 70 MB, writes 1009 MB
+        1224736768: 1090625024 + 122336512,   # tile width 32: reads 1091 MB, writes 122 MB
+    },
+}
 
 
 def fp32_peak_measured(B) -> tuple:
@@ -309,7 +317,7 @@ def roofline_from_profile(prof, cfg_key=None, alu=None) -> tuple:
         r = {"bound": "hbm", "achieved": b / (t / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
              "peak_source": f"hbm_gbs {src}"}
     r["frac"] = r["achieved"] / r["peak"]
-    r["traffic"] = DOMINANT_TRAFFIC.get(cfg_key)
+    r["traffic"] = DOMINANT_TRAFFIC.get(cfg_key, {}).get(int(round(b))) if k == 5 else None
     if r["traffic"] is None:
         r["traffic_note"] = "no ncu DRAM capture of this configuration's longest launch with the current kernels"
     r["kernel"] = f"{KIND_NAMES[k]}: the step's longest launch ({t:.3f} ms)"
@@ -515,6 +523,14 @@ def run_ours(args):
                 split[name].update({"calibration_rel_l2": pr["rel_l2_chosen"],
                                     "calibration_rel_l2_without_split": pr["rel_l2_none"]})
             pl.close()
+    tuned = None
+    if args.tune and args.prec != "c64":
+        # operand type, slice batch, split placement and launch forms picked by timing under 3e-3
+        tplan, rows = E.tune_plan(prep.tn, prep.tree, tol=3e-3, batches=(16, 32, 64), flags=hoist, reps=3)
+        tplan.close()
+        tuned = {"note": "engine.tune_plan: fp16 / bf16 x slice batch, split products placed by calibration "
+                         "(TN_FLAG_HILO_AUTO, 3e-3), tensor-core launch forms tuned; the fastest within the bar "
+                         "is chosen (contraction only)", "candidates": rows}
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
         plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch, flags=hoist)
@@ -566,6 +582,7 @@ def run_ours(args):
             "note": "fp16 hi+lo operands, K accumulated one k tile at a time in FP32 (TN_FLAG_HILO | "
                     "TN_FLAG_FINE_ACC): complex64 accuracy on the tensor cores (contraction only)"},
         "bf16_split_precision": split,
+        "tuned": tuned,
         "useful_flops_per_slice": executed_per_slice,
         "subnetwork_flops": useful_per_slice,
         "subnetwork_flops_note": "8 x complex multiply-adds of one sub-network along the tree, every step "
@@ -735,6 +752,8 @@ def main(argv=None):
     ap.add_argument("--hoist", action="store_true",
                     help="contract slice-independent subtrees once, at plan creation, instead of once in every "
                          "batch (the default: every step does all of its batch's work)")
+    ap.add_argument("--tune", action="store_true",
+                    help="also run the plan tuner (operand type, slice batch, split placement, launch forms)")
     ap.add_argument("--serial-graph", action="store_true",
                     help="one chain of launches per batch graph instead of concurrent branches")
     ap.add_argument("--path", default="time", choices=["time", "refined", "greedy"],

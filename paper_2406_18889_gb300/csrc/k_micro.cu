@@ -15,6 +15,8 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
 
 #include "tn_internal.h"
 
@@ -52,12 +54,35 @@ __device__ __forceinline__ void store16<__nv_bfloat162>(char* C, char* C2, int x
 constexpr int kMicroThreads = 512;
 
 __global__ void __launch_bounds__(kMicroThreads) micro_kernel(const MicroStep* __restrict__ steps,
-                                                              const int* __restrict__ group_start,
+                                                              const MicroGroup* __restrict__ groups,
+                                                              const MicroLoad* __restrict__ loads,
                                                               const char* plan_base, char* ws_base) {
+  extern __shared__ __align__(16) char sm[];  // [descriptors | operands and inner results]
   __shared__ int2 tab[256];  // [0, 128): output bits 0..6; [128, 256): bits 7..13
-  const int g = blockIdx.x;
-  for (int s = group_start[g]; s < group_start[g + 1]; ++s) {
-    const MicroStep& d = steps[s];
+  const MicroGroup G = groups[blockIdx.x];
+  const MicroStep* ds = steps + G.first_step;
+  // one round of loads before the first step: the group's descriptors and the
+  // operands it reads from outside (gate tensors, gathered leaves); inner
+  // results then stay in shared memory, so a step costs no global round trip
+  if (G.desc_in_smem) {
+    const int4* src = reinterpret_cast<const int4*>(ds);
+    int4* dst = reinterpret_cast<int4*>(sm);
+    const int n16 = G.n_steps * (int)(sizeof(MicroStep) / 16);
+    for (int i = threadIdx.x; i < n16; i += kMicroThreads) dst[i] = src[i];
+    ds = reinterpret_cast<const MicroStep*>(sm);
+  }
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int l = G.first_load + warp; l < G.first_load + G.n_loads; l += kMicroThreads / 32) {
+      const MicroLoad L = loads[l];
+      const float2* src = reinterpret_cast<const float2*>((L.src_loc ? ws_base : plan_base) + L.src_off);
+      float2* dst = reinterpret_cast<float2*>(sm + L.smem_off);
+      for (int i = lane; i < L.elems; i += 32) dst[i] = src[i];
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < G.n_steps; ++s) {
+    const MicroStep& d = ds[s];
     const int nb = d.nbits;
     for (int j = threadIdx.x; j < 256; j += blockDim.x) {
       const int lo = j < 128 ? 0 : 7, idx = j & 127;
@@ -70,9 +95,10 @@ __global__ void __launch_bounds__(kMicroThreads) micro_kernel(const MicroStep* _
       tab[j] = make_int2(a, b);
     }
     __syncthreads();
-    const float2* A = reinterpret_cast<const float2*>((d.a_ws ? ws_base : plan_base) + d.a_off);
-    const float2* B = reinterpret_cast<const float2*>((d.b_ws ? ws_base : plan_base) + d.b_off);
-    char* C = ws_base + d.c_off;
+    auto base = [&](int loc) -> const char* { return loc == 2 ? sm : loc == 1 ? ws_base : plan_base; };
+    const float2* A = reinterpret_cast<const float2*>(base(d.a_loc) + d.a_off);
+    const float2* B = reinterpret_cast<const float2*>(base(d.b_loc) + d.b_off);
+    char* C = (d.c_loc == 2 ? sm : ws_base) + d.c_off;
     char* C2 = ws_base + d.c2_off;
     const int K = d.K, total = 1 << nb, kind = d.out_kind;
     const bool hilo = d.out_hilo != 0;
@@ -162,10 +188,25 @@ void fill_micro_weights(const GemmParams& g, MicroStep& d) {
   d.K = (int8_t)g.K;
 }
 
-void launch_micro(const MicroStep* d_steps, const int* d_group_start, int n_groups, const char* plan_base,
-                  char* ws_base, cudaStream_t s) {
+void launch_micro(const MicroStep* d_steps, const MicroGroup* d_groups, const MicroLoad* d_loads, int n_groups,
+                  int smem_bytes, const char* plan_base, char* ws_base, cudaStream_t s) {
   if (n_groups <= 0) return;
-  micro_kernel<<<(unsigned)n_groups, kMicroThreads, 0, s>>>(d_steps, d_group_start, plan_base, ws_base);
+  TN_CHECK(smem_bytes >= 0 && smem_bytes <= kMicroSmemBytes, TN_ERR_INVALID_ARG, "internal: fused launch smem");
+  {
+    // dynamic shared memory above 48 KB: opted in once per device
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    TN_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done.count(dev)) {
+      TN_CUDA(cudaFuncSetAttribute((const void*)micro_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kMicroSmemBytes));
+      done.insert(dev);
+    }
+  }
+  micro_kernel<<<(unsigned)n_groups, kMicroThreads, (size_t)smem_bytes, s>>>(d_steps, d_groups, d_loads, plan_base,
+                                                                              ws_base);
 }
 
 }  // namespace tn

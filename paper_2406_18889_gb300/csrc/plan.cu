@@ -99,8 +99,9 @@ bool decomposes(const std::vector<int>& layout, const std::vector<const std::vec
 struct Arena {
   std::vector<std::pair<int64_t, int64_t>> live;  // (off, bytes), sorted by off
   int64_t peak = 0;
+  int64_t align = 256;
   int64_t alloc(int64_t bytes) {
-    bytes = round_up(std::max<int64_t>(bytes, 1), 256);
+    bytes = round_up(std::max<int64_t>(bytes, 1), align);
     int64_t off = 0;
     for (auto& b : live) {
       if (b.first - off >= bytes) break;
@@ -134,7 +135,8 @@ Plan::~Plan() {
   if (d_gather) cudaFree(d_gather);
   if (d_err) cudaFree(d_err);
   if (d_micro) cudaFree(d_micro);
-  if (d_micro_start) cudaFree(d_micro_start);
+  if (d_micro_groups) cudaFree(d_micro_groups);
+  if (d_micro_loads) cudaFree(d_micro_loads);
 }
 
 // ---------------------------------------------------------------- layouts
@@ -719,7 +721,7 @@ void enqueue_micro(const Exec& X, int g0, int g1, cudaStream_t s, Recorder& R) {
       bytes += (double)(node_bytes(P, S.a, X.M.c64) + node_bytes(P, S.b, X.M.c64) + node_bytes(P, S.c, X.M.c64));
     }
   R.begin(0, flops, bytes);
-  launch_micro(P.d_micro, P.d_micro_start + g0, g1 - g0, X.pb, X.wb, s);
+  launch_micro(P.d_micro, P.d_micro_groups + g0, P.d_micro_loads, g1 - g0, P.micro_smem, X.pb, X.wb, s);
   R.end();
 }
 
@@ -1337,38 +1339,103 @@ std::unique_ptr<Plan> build_plan(const tn_network_desc* net, const tn_tree_desc*
     cleanup();
   }
   if (P.mem.micro) {
-    // fused small-step descriptors (scales need the calibrated exponents)
+    // fused small-step descriptors (scales need the calibrated exponents).
+    // Each group (one CTA) keeps, where they fit, its descriptors, the
+    // operands it reads from outside (copied in before its first step) and its
+    // inner results (consumed by the group's next steps) in shared memory:
+    // [descriptors | first-fit arena over the group's step order].
+    const MemPlan& M = P.mem;
+    const bool c64 = M.c64;
     std::vector<MicroStep> desc;
-    std::vector<int> start{0};
+    std::vector<MicroGroup> groups;
+    std::vector<MicroLoad> loads;
+    constexpr int64_t kDescMax = 48 * 1024;
+    P.micro_smem = 0;
     for (const auto& grp : P.micro_groups) {
+      MicroGroup G{};
+      G.first_step = (int32_t)desc.size();
+      G.n_steps = (int32_t)grp.size();
+      G.first_load = (int32_t)loads.size();
+      const int64_t desc_bytes = (int64_t)grp.size() * (int64_t)sizeof(MicroStep);
+      G.desc_in_smem = desc_bytes <= kDescMax ? 1 : 0;
+      const int64_t base = G.desc_in_smem ? round_up(desc_bytes, 16) : 0;
+      std::set<int> produced;
+      for (int t : grp) produced.insert(P.steps[t].c);
+      const int root = P.steps[grp.back()].c;
+      auto is_c64 = [&](int x) { return c64 || P.nodes[x].kind == KIND_C64; };
+      std::map<int, int64_t> soff;  // node -> arena offset
+      Arena A;
+      A.align = 16;
+      bool fits = true;
+      for (int t : grp)
+        for (int x : {P.steps[t].a, P.steps[t].b})
+          if (!produced.count(x) && !soff.count(x)) {
+            fits = fits && is_c64(x);
+            soff[x] = A.alloc(node_bytes(P, x, c64));
+          }
+      for (int t : grp) {
+        const Step& S = P.steps[t];
+        if (S.c != root) {
+          fits = fits && is_c64(S.c) && !(!c64 && P.nodes[S.c].hilo);
+          soff[S.c] = A.alloc(node_bytes(P, S.c, c64));
+        }
+        for (int x : {S.a, S.b})
+          if (soff.count(x)) A.release(soff[x]);
+      }
+      fits = fits && base + A.peak <= kMicroSmemBytes;
+      if (!fits) soff.clear();
+      for (const auto& kv : soff) {
+        const int x = kv.first;
+        if (produced.count(x)) continue;
+        MicroLoad L{};
+        L.src_off = M.off[x];
+        L.smem_off = (int32_t)(base + kv.second);
+        L.elems = (int32_t)(node_bytes(P, x, c64) / 8);
+        L.src_loc = M.in_plan[x] ? 0 : 1;
+        loads.push_back(L);
+      }
+      G.n_loads = (int32_t)(loads.size() - (size_t)G.first_load);
+      P.micro_smem = std::max<int>(P.micro_smem, (int)(base + (fits ? A.peak : 0)));
       for (int t : grp) {
         const Step& S = P.steps[t];
         const Node& NC = P.nodes[S.c];
         MicroStep d{};
         fill_micro_weights(S.gp, d);
-        d.a_off = P.mem.off[S.a];
-        d.b_off = P.mem.off[S.b];
-        d.a_ws = P.mem.in_plan[S.a] ? 0 : 1;
-        d.b_ws = P.mem.in_plan[S.b] ? 0 : 1;
-        TN_CHECK(!P.mem.in_plan[S.c], TN_ERR_INVALID_ARG, "internal: micro result in plan memory");
-        d.c_off = P.mem.off[S.c];
-        const bool c64 = P.mem.c64;
+        auto where = [&](int x, int8_t& loc, int64_t& off) {
+          if (soff.count(x)) {
+            loc = 2;
+            off = base + soff[x];
+          } else {
+            loc = M.in_plan[x] ? 0 : 1;
+            off = M.off[x];
+          }
+        };
+        where(S.a, d.a_loc, d.a_off);
+        where(S.b, d.b_loc, d.b_off);
+        TN_CHECK(!M.in_plan[S.c], TN_ERR_INVALID_ARG, "internal: micro result in plan memory");
+        where(S.c, d.c_loc, d.c_off);
         d.out_kind = (int8_t)(c64 ? KIND_C64 : NC.kind);
         d.out_hilo = (int8_t)(!c64 && NC.hilo ? 1 : 0);
+        TN_CHECK(d.c_loc == 1 || (d.out_kind == KIND_C64 && !d.out_hilo), TN_ERR_INVALID_ARG,
+                 "internal: a shared-memory micro result must be complex64");
         d.c2_off = d.c_off + (d.out_hilo ? NC.elems * 4 : 0);
         d.scale = c64 ? 1.0f : ldexpf(1.0f, P.nodes[S.a].exp2 + P.nodes[S.b].exp2 - NC.exp2);
         desc.push_back(d);
         P.micro_flops += 8.0 * S.cost;
         P.micro_bytes += (double)(node_bytes(P, S.a, c64) + node_bytes(P, S.b, c64) + node_bytes(P, S.c, c64));
       }
-      start.push_back((int)desc.size());
+      groups.push_back(G);
     }
     TN_CUDA(cudaMalloc(&P.d_micro, sizeof(MicroStep) * desc.size()));
-    TN_CUDA(cudaMalloc(&P.d_micro_start, sizeof(int) * start.size()));
+    TN_CUDA(cudaMalloc(&P.d_micro_groups, sizeof(MicroGroup) * groups.size()));
+    TN_CUDA(cudaMalloc(&P.d_micro_loads, sizeof(MicroLoad) * std::max<size_t>(loads.size(), 1)));
     TN_CUDA(cudaMemcpyAsync(P.d_micro, desc.data(), sizeof(MicroStep) * desc.size(), cudaMemcpyHostToDevice,
                             stream));
-    TN_CUDA(cudaMemcpyAsync(P.d_micro_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice,
-                            stream));
+    TN_CUDA(cudaMemcpyAsync(P.d_micro_groups, groups.data(), sizeof(MicroGroup) * groups.size(),
+                            cudaMemcpyHostToDevice, stream));
+    if (!loads.empty())
+      TN_CUDA(cudaMemcpyAsync(P.d_micro_loads, loads.data(), sizeof(MicroLoad) * loads.size(),
+                              cudaMemcpyHostToDevice, stream));
   }
   TN_CUDA(cudaMalloc(&P.d_plan, std::max<int64_t>(P.mem.plan_bytes, 256)));
   upload_leaves(P.mem, (char*)P.d_plan, KIND_C64);

@@ -109,7 +109,9 @@ struct Plan {
   std::vector<std::vector<int>> micro_groups;  // slice-independent groups first
   int n_micro_inv = 0;                  // how many groups are slice-independent
   MicroStep* d_micro = nullptr;
-  int* d_micro_start = nullptr;
+  MicroGroup* d_micro_groups = nullptr;
+  MicroLoad* d_micro_loads = nullptr;
+  int micro_smem = 0;                   // dynamic shared memory of the fused launches
   double micro_flops = 0, micro_bytes = 0;
   // root readout strides (elements)
   int64_t root_sb = 0, root_sg = 0, root_sj = 1;

@@ -172,18 +172,33 @@ bool output_position_bits(const RunDecode& d, int nbits, const int64_t ext[3], i
 constexpr int kMicroMaxBits = 14;
 struct MicroStep {
   int64_t a_off, b_off;          // operand byte offsets from their memory's base
-  int64_t c_off, c2_off;         // result (and residual) byte offsets in the workspace
+  int64_t c_off, c2_off;         // result (and residual) byte offsets from their memory's base
   int32_t a_w[kMicroMaxBits];    // element offset in A of output bit j
   int32_t b_w[kMicroMaxBits];    // element offset in B of output bit j
   int32_t ak[4], bk[4];          // contracted-index offsets
   float scale;
-  int8_t a_ws, b_ws;             // operand lives in the workspace (else plan memory)
+  int8_t a_loc, b_loc;           // operand memory: 0 plan memory, 1 workspace, 2 the group's shared memory
+  int8_t c_loc;                  // result memory: 1 workspace, 2 the group's shared memory (complex64)
   int8_t nbits, K, out_kind, out_hilo;
+  int8_t pad_[5];
 };
+static_assert(sizeof(MicroStep) % 16 == 0, "micro step descriptors are copied in 16-byte pieces");
+// complex64 operand copied into the group's shared memory before its first step
+struct MicroLoad {
+  int64_t src_off;               // byte offset from the source memory's base
+  int32_t smem_off, elems;       // destination byte offset, complex64 elements
+  int32_t src_loc, pad_;         // 0 plan memory, 1 workspace
+};
+// one CTA of the fused launch: steps [first_step, first_step + n_steps) in order
+struct MicroGroup {
+  int32_t first_step, n_steps, first_load, n_loads;
+  int32_t desc_in_smem, pad_[3]; // descriptors copied to shared memory offset 0 first
+};
+constexpr int kMicroSmemBytes = 160 * 1024;  // dynamic shared memory of a fused launch, at most
 void fill_micro_weights(const GemmParams& g, MicroStep& d);
-// steps [group_start[g], group_start[g + 1]) run in order on CTA g
-void launch_micro(const MicroStep* d_steps, const int* d_group_start, int n_groups, const char* plan_base,
-                  char* ws_base, cudaStream_t s);
+// group g of [0, n_groups) runs on CTA g with smem_bytes of dynamic shared memory
+void launch_micro(const MicroStep* d_steps, const MicroGroup* d_groups, const MicroLoad* d_loads, int n_groups,
+                  int smem_bytes, const char* plan_base, char* ws_base, cudaStream_t s);
 void launch_amax_c64(const void* x, int64_t n, unsigned* out, cudaStream_t s);
 // d_ids[0..B) = ids, *d_n_valid = n_valid, through kernel parameters (asynchronous)
 void launch_set_slice_ids(int64_t* d_ids, int32_t* d_n_valid, const int64_t* ids, int B, int32_t n_valid,

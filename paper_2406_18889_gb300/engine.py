@@ -142,6 +142,56 @@ class Plan:
             pass
 
 
+def tune_plan(tn: TensorNetwork, tree: Tree, tol: float = 3e-3, precs: Sequence[str] = ("fp16", "bf16"),
+              batches: Sequence[int] = (16, 32, 64), flags: int = 0, slice_ids=None, reps: int = 3,
+              launch_forms: bool = True):
+    """Split choices and launch forms picked by timing, under an accuracy bar.
+
+    Every candidate -- 16-bit operand type x slice batch -- is planned with
+    its split-precision (hi + lo) products placed by calibration
+    (``TN_FLAG_HILO_AUTO``: the fewest tensor-core steps split so that the
+    calibration batch's relative L2 against a complex64 pass is <= ``tol``),
+    its tensor-core launch forms tuned (``Plan.autotune``), then timed over
+    ``slice_ids`` (default all slices; ``reps`` calls after one warm-up).  The
+    fastest candidate whose calibrated error meets ``tol`` is kept.  Returns
+    (plan, table): the chosen plan, open, and one row per candidate (prec,
+    batch, slices_per_s, rel_l2, n_hilo_steps, n_tc_steps, chosen)."""
+    torch = _torch()
+    rows, best, best_plan = [], None, None
+    n_total = 1 << len(tree.sliced_edges)
+    ids = np.arange(n_total, dtype=np.int64) if slice_ids is None else np.asarray(slice_ids, dtype=np.int64)
+    for prec in precs:
+        for b in batches:
+            plan = Plan(tn, tree, prec=prec, flags=flags | B.TN_FLAG_HILO_AUTO, max_slice_batch=b, hilo_tol=tol)
+            if launch_forms:
+                plan.autotune(ids, reps=2)
+            out = torch.empty((plan.G, plan.J), dtype=torch.complex128, device="cuda")
+            plan.contract(ids, out=out)
+            s = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                plan.contract(ids, out=out)
+            e1.record(s)
+            torch.cuda.synchronize()
+            pr = plan.precision()
+            row = dict(prec=prec, batch=plan.max_slice_batch, slices_per_s=len(ids) * reps / (e0.elapsed_time(e1) / 1e3),
+                       rel_l2=pr["rel_l2_chosen"], n_hilo_steps=pr["n_hilo_steps"], n_tc_steps=pr["n_tc_steps"],
+                       chosen=False)
+            rows.append(row)
+            ok = 0 <= row["rel_l2"] <= tol
+            if ok and (best is None or row["slices_per_s"] > best["slices_per_s"]):
+                if best_plan is not None:
+                    best_plan.close()
+                best, best_plan = row, plan
+            else:
+                plan.close()
+    if best is None:
+        raise ValueError("no candidate meets the accuracy bar")
+    best["chosen"] = True
+    return best_plan, rows
+
+
 def contract_checkpointed(plan: "Plan", slice_ids, path: str, chunk: Optional[int] = None, out=None,
                           on_chunk=None):
     """Sum the given slices in chunks, saving (ids, number finished, FP64 partial
