@@ -742,7 +742,9 @@ void enqueue_batch_mem(const Plan& P, const MemPlan& M, char* pb, void* ws, void
     for (int i = 0; i < P.n_leaves; ++i) launch_amax_c64(X.base(i), P.nodes[i].elems, amax + i, s);
   if (M.micro) {
     TN_CHECK(!amax, TN_ERR_INVALID_ARG, "internal: fused small steps during calibration");
-    enqueue_micro(X, 0, (int)P.micro_groups.size(), s, R);
+    // as in the batch graph: the slice-independent groups, then the rest
+    enqueue_micro(X, 0, P.n_micro_inv, s, R);
+    enqueue_micro(X, P.n_micro_inv, (int)P.micro_groups.size(), s, R);
   }
   for (size_t t = 0; t < P.steps.size(); ++t) {
     if (P.steps[t].hoisted && !hoisted_too) continue;
