@@ -836,6 +836,26 @@ void plan_batch_graph(Plan& P) {
     P.unit_branch[j] = b;
     tail[b] = j;
   }
+  // Self-check: every two units whose ranges overlap are ordered by the
+  // graph (the earlier one happens before the later: same branch, or a chain
+  // of branch order and waits), so no two launches that share workspace run
+  // concurrently.
+  const int words = (n + 63) / 64;
+  std::vector<std::vector<uint64_t>> hb(n, std::vector<uint64_t>(words, 0));  // hb[j]: units before j
+  std::vector<int> prev(kBranches, -1);
+  auto join = [&](int j, int i) {
+    for (int w = 0; w < words; ++w) hb[j][w] |= hb[i][w];
+    hb[j][i / 64] |= uint64_t(1) << (i % 64);
+  };
+  for (int j = 0; j < n; ++j) {
+    const int b = P.unit_branch[j];
+    if (prev[b] >= 0) join(j, prev[b]);
+    for (int i : P.unit_waits[j]) join(j, i);
+    prev[b] = j;
+    for (int i = 0; i < j; ++i)
+      TN_CHECK(!overlap(i, j) || ((hb[j][i / 64] >> (i % 64)) & 1), TN_ERR_INVALID_ARG,
+               "internal: batch graph leaves two launches that share workspace unordered");
+  }
 }
 
 // The branch streams and events of the batch graph (created before a capture:
