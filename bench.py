@@ -565,7 +565,8 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        _, _, wires = sliced_wires(args.path, args.batch)
+        # the timed plan's own sliced bonds (one rank: its workload is rank 0's)
+        wires = [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
         v = oracle_slices_per_s(rank_workload(0), wires, [0, 1])
         cpu = {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
                "sample": "2 of the 64 slices, oracle O2 (naive FP64 einsum contractor, numpy matmul)"}
