@@ -211,18 +211,40 @@ PATH_DESC = {"time": "greedy and bisection + subtree reconfiguration, re-optimis
              "greedy": "greedy"}
 
 
-def sliced_wires(path: str = "greedy", batch: int = 64):
-    w = rank_workload(0)
-    prep = prepare_path(w, path, batch)
-    return w, prep, [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
+def bench_config(args, world: int) -> dict:
+    """The workload's config as both arms report it."""
+    split_slices = world > 1 and args.partition == "slices"
+    return {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
+            "hoist_invariant": bool(args.hoist), "autotune": bool(args.autotune),
+            "graph": "one chain" if args.serial_graph else "concurrent branches",
+            "path": PATH_DESC[args.path],
+            "l2": "flushed between steps (256 MiB write outside the timed events)",
+            "parallelism": (f"the 64 slices split over {world} GPUs, FP64 partials gathered and summed "
+                            "on rank 0" if split_slices else f"{world} independent block sets (one per GPU)")}
+
+
+def oracle_wires(w):
+    """Sliced bonds for the CPU oracle's samples: the greedy tree's six.  The
+    oracle contracts every sub-network along its own greedy path; on the time
+    tree's slicing that path is ~4x slower (47 s against 11 s per slice on 8
+    host cores), which would make a bounded sample of 25 slices run for many
+    minutes.  Each is one of 64 sub-networks of the same circuit."""
+    from paper_2406_18889_gb300 import engine as E
+    prep = E.prepare(w)
+    return [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
+
+
+ORACLE_SAMPLE = ("1 slice of 64 per step (the greedy tree's six sliced bonds), oracle O2 (naive FP64 einsum "
+                 "contractor along its own greedy path, numpy matmul)")
 
 
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    w, prep, wires = sliced_wires(args.path, args.batch)
-    sample = "1 slice of 64 per step, oracle O2 (naive FP64 einsum contractor, numpy matmul)"
+    w = rank_workload(0)
+    wires = oracle_wires(w)
+    sample = ORACLE_SAMPLE
     for s in range(args.warmup):
         oracle_slices_per_s(w, wires, [s % 64])
     t0 = time.perf_counter()
@@ -232,8 +254,9 @@ def run_reference(args):
     v = args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "complex128",
-            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "arm": "FP64 CPU oracle"},
+            "higher_is_better": True, "scaling": "strong" if world > 1 and args.partition == "slices" else "weak",
+            "vs_baseline": None, "dtype": "complex128",
+            "data": "synthetic", "config": bench_config(args, world),
             "cpu_baseline": {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -565,11 +588,10 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        # the timed plan's own sliced bonds (one rank: its workload is rank 0's)
-        wires = [prep.tn.wire_of_edge[e] for e in prep.tree.sliced_edges]
-        v = oracle_slices_per_s(rank_workload(0), wires, [0, 1])
+        w0 = rank_workload(0)
+        v = oracle_slices_per_s(w0, oracle_wires(w0), [0, 1])
         cpu = {"value": v, "unit": "slices/s", "cores": host_cores(), "kind": "oracle",
-               "sample": "2 of the 64 slices, oracle O2 (naive FP64 einsum contractor, numpy matmul)"}
+               "sample": ORACLE_SAMPLE.replace("1 slice of 64 per step", "2 of the 64 slices")}
     line = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -577,13 +599,7 @@ def run_ours(args):
         "dtype": "complex64" if args.prec == "c64" else
                  f"{args.prec} tensor-core operands, fp32 accumulate, complex64 elsewhere",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
-                   "hoist_invariant": bool(args.hoist), "autotune": bool(args.autotune),
-                   "graph": "one chain" if args.serial_graph else "concurrent branches",
-                   "path": PATH_DESC[args.path],
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": (f"the 64 slices split over {world} GPUs, FP64 partials gathered and summed "
-                                   "on rank 0" if split_slices else f"{world} independent block sets (one per GPU)")},
+        "config": bench_config(args, world),
         "useful_tflops": value * executed_per_slice / 1e12,
         "useful_flops_note": "flops the step's kernels execute (8 per complex multiply-add), per slice: "
                              "slice-independent subtrees run once per batch and are shared by its slices",
