@@ -14,7 +14,8 @@ Contents (each function cites the passage of arXiv 2406.18889 it follows):
   partial contraction of a fraction f of the slices (Sec. III "Composition of
   our algorithm").
 * ``postprocess``  -- probabilities |phi|^2/f (Fig. 5), per-block and global
-  top-k (Sec. III), linear XEB (Eq. 1), numerical fidelity.
+  top-k (Sec. III), linear XEB (Eq. 1), numerical fidelity, Metropolis
+  sampling from p (the MCMC baseline of Eq. 3).
 * ``theory``       -- the paper's closed forms: Porter-Thomas moments
   (App. A), ideal and approximate top-k XEB (Eqs. 2 and 4) and the exact
   finite-size order-statistics expectation used to pin them.

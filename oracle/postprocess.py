@@ -14,6 +14,11 @@
 * Numerical fidelity (Fig. 3 caption: fidelity from approximate and exact
   amplitudes; no formula given): the normalised overlap
   |<a|e>|^2 / (<a|a><e|e>) over the computed strings.
+* MCMC sampling (Sec. III, Eq. 3: samples drawn from the approximate p over a
+  candidate set score an XEB equal to the fidelity F): Metropolis chains over
+  the candidates with uniform proposals, accepting a move x -> y with
+  probability min(1, p(y) / p(x)), so that p (normalised) is the stationary
+  distribution.  The paper does not state its chain; this is the plainest one.
 """
 from __future__ import annotations
 
@@ -95,3 +100,27 @@ def relative_l2(x: np.ndarray, ref: np.ndarray) -> float:
     x = np.asarray(x, dtype=np.complex128).reshape(-1)
     ref = np.asarray(ref, dtype=np.complex128).reshape(-1)
     return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def metropolis(p: np.ndarray, n_chains: int, n_steps: int, burn: int, rng: np.random.Generator) -> np.ndarray:
+    """Candidate indices sampled with probability proportional to p (Eq. 3's
+    MCMC baseline): n_chains independent Metropolis chains, each started at a
+    uniform candidate; at every step a uniform proposal y replaces the state x
+    when u * p(x) < p(y) for u uniform in [0, 1) (so always when p(y) >= p(x),
+    and with probability p(y) / p(x) otherwise).  Returns the states of the
+    steps after the first ``burn``, chain-major within each step:
+    n_chains * (n_steps - burn) indices."""
+    p = np.asarray(p, dtype=np.float64).reshape(-1)
+    if p.size == 0 or n_chains <= 0 or not 0 <= burn < n_steps:
+        raise ValueError("empty candidate set or no sampled steps")
+    if np.any(p < 0) or not np.any(p > 0):
+        raise ValueError("p must be non-negative with some positive entry")
+    x = rng.integers(0, p.size, size=n_chains)
+    out = []
+    for t in range(n_steps):
+        y = rng.integers(0, p.size, size=n_chains)
+        u = rng.random(n_chains)
+        x = np.where(u * p[x] < p[y], y, x)
+        if t >= burn:
+            out.append(x.copy())
+    return np.concatenate(out)

@@ -148,3 +148,45 @@ def test_table_one_arithmetic():
     assert abs(per * n / full - 1) < 1e-3
     frac = task / per / n * 100
     assert abs(frac - gold["fraction_of_subtasks_percent"]["value"]) < 0.0005
+
+
+def test_metropolis_samples_follow_p():
+    # 16 candidates with random weights (and one zero): the visit frequencies of
+    # many chains converge to p / sum(p); total variation within a few
+    # standard errors of the 2e5 correlated samples
+    rng = np.random.default_rng(5)
+    p = rng.random(16) ** 3
+    p[3] = 0.0
+    s = pp.metropolis(p, n_chains=2000, n_steps=120, burn=20, rng=np.random.default_rng(6))
+    assert s.size == 2000 * 100
+    freq = np.bincount(s, minlength=16) / s.size
+    target = p / p.sum()
+    assert freq[3] == 0.0  # a zero-probability candidate is never accepted
+    assert 0.5 * np.abs(freq - target).sum() < 0.01, (freq, target)
+
+
+def test_metropolis_xeb_of_porter_thomas_and_uniform():
+    # Eq. 3 with F = 1: samples of an exponential (Porter-Thomas) q over N = 2^12
+    # strings score XEB = N sum q^2 - 1 (about 1); samples of a uniform p score 0
+    n = 12
+    N = 1 << n
+    rng = np.random.default_rng(7)
+    q = rng.exponential(size=N)
+    q /= q.sum()
+    s = pp.metropolis(q, n_chains=4096, n_steps=64, burn=32, rng=np.random.default_rng(8))
+    expect = N * float((q * q).sum()) - 1.0
+    assert abs(pp.xeb(q[s], n) - expect) < 0.05, (pp.xeb(q[s], n), expect)
+    assert 0.85 < expect < 1.15
+    u = np.full(N, 1.0 / N)
+    su = pp.metropolis(u, n_chains=512, n_steps=16, burn=4, rng=np.random.default_rng(9))
+    assert abs(pp.xeb(q[su], n)) < 0.05  # uniform samples: XEB of a uniform draw ~ 0
+
+
+def test_metropolis_rejects_bad_input():
+    rng = np.random.default_rng(0)
+    with pytest.raises(ValueError):
+        pp.metropolis(np.zeros(4), 4, 4, 0, rng)
+    with pytest.raises(ValueError):
+        pp.metropolis(np.ones(4), 4, 4, 4, rng)
+    with pytest.raises(ValueError):
+        pp.metropolis(np.array([1.0, -1.0]), 4, 4, 0, rng)
