@@ -74,7 +74,21 @@ __global__ void __launch_bounds__(256) bit_permute_kernel(const W* __restrict__ 
       base_in |= bit << pt.gin[j];
       base_out |= bit << pt.gout[j];
     }
-    for (int t = tid; t < n; t += 256) tile[pad(t)] = in[base_in + in_lo[t & 63] + in_hi[t >> 6]];
+    // eight loads per thread issued before their shared-memory stores (one
+    // round trip for the thread's share of the tile instead of one per element)
+    for (int t0 = tid; t0 < n; t0 += 256 * 8) {
+      W v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int t = t0 + q * 256;
+        if (t < n) v[q] = in[base_in + in_lo[t & 63] + in_hi[t >> 6]];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int t = t0 + q * 256;
+        if (t < n) tile[pad(t)] = v[q];
+      }
+    }
     __syncthreads();
     for (int u = tid; u < n; u += 256)
       out[base_out + out_lo[u & 63] + out_hi[u >> 6]] = tile[pad(t_lo[u & 63] | t_hi[u >> 6])];
