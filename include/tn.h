@@ -195,8 +195,8 @@ tn_status tn_plan_destroy(tn_plan_t plan);
 tn_status tn_plan_slice_batch(tn_plan_t plan, int32_t* batch);
 
 /*
- * Precision record of a reduced-precision plan (spec: split-precision
- * products on the contractions whose error measurably moves the result).
+ * Precision record of a reduced-precision plan (split-precision products
+ * only on the contractions whose error measurably moves the result).
  * With TN_FLAG_HILO_AUTO, tn_plan_create contracts the calibration slices
  * (the plan's seeded calibration batch) once in complex64 and, in the plan's
  * 16-bit precision, with every candidate placement it tries: no split; each
@@ -299,8 +299,7 @@ tn_status tn_contract_slices(tn_plan_t plan, const int64_t* slice_ids, int64_t n
                              void* stream);
 
 /*
- * Several plans (e.g. many small circuits with uneven trees, north star
- * "Batching") in one call: plan p contracts slice_ids[p][0..n_slices[p]) into
+ * Several plans (e.g. many small circuits with uneven trees) in one call: plan p contracts slice_ids[p][0..n_slices[p]) into
  * amps[p], with the semantics of tn_contract_slices for each.  All of the
  * plans' slice batches are captured into ONE CUDA graph whose up to 8
  * concurrent branches each run a share of the plans one after another

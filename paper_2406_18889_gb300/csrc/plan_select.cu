@@ -1,8 +1,8 @@
 // Plan creation choices that need measurements or several candidate plans:
 //  * the slice batch from the memory budget (max_slice_batch = 0);
 //  * the placement of split-precision (hi + lo) products (TN_FLAG_HILO_AUTO):
-//    the benchmark spec asks for hi + lo only on the contractions whose 16-bit
-//    error measurably moves the result.  Each candidate placement is a plan
+//    hi + lo only on the contractions whose 16-bit error measurably moves
+//    the result.  Each candidate placement is a plan
 //    of its own; the calibration slices are contracted once in complex64 and
 //    once per candidate, and the relative L2 of the 16-bit amplitudes against
 //    the complex64 ones decides.

@@ -121,7 +121,7 @@ def case20(case):
 
 @pytest.mark.parametrize("prec", ["c64", "fp16"])
 def test_sycamore_20_cycles_sub_slices_against_oracle(case20, prec):
-    # config 5's circuit at its full depth: four sub-networks of the production
+    # the 53-qubit circuit at its full depth (20 cycles): four sub-networks of the production
     # tree (the 2^32-cap slices with 24 more bonds fixed, the same bonds on both
     # sides) against the FP64 oracle
     from paper_2406_18889_gb300 import binding as B
