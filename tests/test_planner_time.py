@@ -6,8 +6,11 @@ Pins: the cost of two hand-worked three-tensor chains (with and without a
 sliced bond); on tiny networks, reconfiguration under this cost reaches the
 optimum found by enumerating every pairwise order; on the 24-qubit circuit,
 re-optimising a sliced tree never raises its time cost, keeps the output and
-keeps every batched intermediate within the tree's largest."""
+keeps every batched intermediate within the tree's largest; the time
+objective's choice never costs more time than the flop objective's; the
+slice-independent-first order keeps the tree."""
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -122,3 +125,26 @@ def test_plan_tree_lists_slice_independent_steps_first():
         variant.append(variant[i] or variant[j])
     v = variant[len(tn.leaf_edges):]
     assert v == sorted(v) and not v[0] and v[-1]
+
+
+def test_time_objective_never_worse_than_the_flop_tree():
+    # the time objective keeps the candidate with the lowest time_cost, and the
+    # flop-refined trees are among its candidates: its choice costs no more
+    # time (and, hoisting nothing, the flop choice no fewer multiply-adds)
+    # (the 24-qubit grid at 10 cycles, 4 sliced bonds: a few seconds of planning)
+    w = W.workload("grid4x6_d14", cycles=10, n_sliced=4)
+    tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    lg = P.log2dims(tn)
+    keep = frozenset(tn.output_edges())
+    leaves = [frozenset(e) for e in tn.leaf_edges]
+    kw = dict(n_sliced=4, restarts=1, method="greedy", refine=True, workers=os.cpu_count() or 1)
+    flop = P.plan_tree(tn, **kw)
+    fast = P.plan_tree(tn, objective="time", batch_log2=4, **kw)
+    t_flop = P.time_cost(leaves, flop.pairs, lg, keep, flop.sliced_edges, 4, P.ALPHA_TC)
+    t_fast = P.time_cost(leaves, fast.pairs, lg, keep, fast.sliced_edges, 4, P.ALPHA_TC)
+    assert t_fast <= t_flop
+    assert len(fast.sliced_edges) == 4
+    # both trees contract the whole network to the same output
+    for t in (flop, fast):
+        stripped = [x - set(t.sliced_edges) for x in leaves]
+        assert P.replay(stripped, t.pairs, keep)[-1] == keep
