@@ -330,3 +330,35 @@ def test_hilo_steps_mask_places_split_products(lib):
     h = _create(lib, prep, prec=1, flags=flags | lib.TN_FLAG_HILO_AUTO, max_slice_batch=64)
     assert not ((lib.tn_plan_steps(h)["kinds"] & 16) > 0).any()
     lib.tn_plan_destroy(h)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_plan_only_graphs_over_random_trees(lib, seed):
+    # plans over random (noisy greedy) trees and slicings of small circuits, in
+    # every precision, hoisted or not, at several batches: the workspace map in
+    # its two arenas and the concurrent batch graph are built, and the graph's
+    # self-check (launches that share workspace are ordered) holds for each
+    from paper_2406_18889_gb300 import engine as E
+    from paper_2406_18889_gb300 import network as N
+    from paper_2406_18889_gb300 import pathfind as P
+    rng = np.random.default_rng(seed)
+    w = W.workload("grid3x4_d8", cycles=int(rng.integers(6, 11)), l=int(rng.integers(3, 8)),
+                   G=int(2 ** rng.integers(0, 4)))
+    tn = N.circuit_network(w.circuit, w.open_qubits, w.closed_qubits, w.closed_bits)
+    lg = P.log2dims(tn)
+    keep = frozenset(tn.output_edges())
+    leaves = [frozenset(e) for e in tn.leaf_edges]
+    pairs = P.greedy(leaves, lg, keep, float(rng.uniform(0.5, 2.5)), float(rng.uniform(0, 0.6)), seed)
+    n_sl = int(rng.integers(0, 5))
+    sl = P.choose_slices(leaves, pairs, lg, keep, len(tn.edge_dim), n_sliced=n_sl) if n_sl else []
+    pairs = P.invariant_first(leaves, pairs, sl)
+    mx, cost, vcost = P.tree_stats(leaves, pairs, lg, keep, sl)
+    tree = P.Tree(pairs=pairs, sliced_edges=list(sl), log2_max_intermediate=mx, cost_per_slice=cost,
+                  cost_variant_per_slice=vcost, n_leaves=len(leaves))
+    prep = E.Prepared(tn, tree)
+    for prec in (0, 1, 2):
+        for hoist in (0, lib.TN_FLAG_HOIST_INVARIANT):
+            for batch in (1, 4, 64):
+                h = _create(lib, prep, prec=prec, flags=lib.TN_FLAG_PLAN_ONLY | hoist, max_slice_batch=batch)
+                assert lib.tn_plan_query(h)["workspace_bytes"] > 0
+                lib.tn_plan_destroy(h)
