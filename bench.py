@@ -30,6 +30,14 @@ import subprocess
 import sys
 import time
 
+if "--impl" in sys.argv and "reference" in sys.argv:
+    # the CPU reference arm runs on rank 0 alone, on every host core: under
+    # torchrun, whose default OMP_NUM_THREADS=1 would leave NumPy's BLAS one
+    # thread, give the threads back before NumPy loads its BLAS
+    _cores = str(len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = _cores
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
