@@ -219,10 +219,21 @@ PATH_DESC = {"time": "greedy and bisection + subtree reconfiguration, re-optimis
              "greedy": "greedy"}
 
 
+def rank_batch(args, world: int, n_slices: int = 64) -> int:
+    """A rank's slice batch: --batch, or, with the slices split over the
+    ranks, the power of two that holds a rank's share (at most --batch)."""
+    if not (world > 1 and args.partition == "slices"):
+        return args.batch
+    share, batch = -(-n_slices // world), 1
+    while batch < share:
+        batch *= 2
+    return min(args.batch, batch)
+
+
 def bench_config(args, world: int) -> dict:
     """The workload's config as both arms report it."""
     split_slices = world > 1 and args.partition == "slices"
-    return {"workload": WORKLOAD_DESC, "slice_batch": args.batch, "prec": args.prec, "hilo": args.hilo,
+    return {"workload": WORKLOAD_DESC, "slice_batch": rank_batch(args, world), "prec": args.prec, "hilo": args.hilo,
             "hoist_invariant": bool(args.hoist), "autotune": bool(args.autotune),
             "graph": "one chain" if args.serial_graph else "concurrent branches",
             "path": PATH_DESC[args.path],
@@ -398,10 +409,13 @@ def run_ours(args):
     # rank 0 (--partition slices), or every rank its own blocks (--partition blocks)
     split_slices = world > 1 and args.partition == "slices"
     w = rank_workload(0 if split_slices else rank)
-    prep = prepare_path(w, args.path, args.batch)
+    # slices split over the ranks: each rank's share runs as one batch (the
+    # power of two that holds it), and the tree is searched for that batch
+    batch = rank_batch(args, world, w.n_slices)
+    prep = prepare_path(w, args.path, batch)
     hoist = (B.TN_FLAG_HOIST_INVARIANT if args.hoist else 0) | (B.TN_FLAG_SERIAL_GRAPH if args.serial_graph else 0)
     flags = (B.TN_FLAG_HILO if args.hilo else 0) | hoist
-    plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=args.batch, flags=flags)
+    plan = E.Plan(prep.tn, prep.tree, prec=args.prec, max_slice_batch=batch, flags=flags)
     S = plan.n_slices_total
     ids = np.arange(S, dtype=np.int64)
     if args.autotune:  # per-step tensor-core launch forms, timed before (outside) the measurement
@@ -518,22 +532,24 @@ def run_ours(args):
     d2h = (h_idx.numel() + h_p.numel()) * 8 + 8
 
     # per-kernel roofline: one profiled pass (events around every launch)
-    prof = B.tn_contract_slices_profile(plan.handle, ids, amps.data_ptr(), 0, plan.workspace.data_ptr(),
+    # (this rank's own slices: all of them, or its share when slices are split)
+    mine = MR.partition(ids, rank, world) if split_slices else ids
+    prof = B.tn_contract_slices_profile(plan.handle, mine, amps.data_ptr(), 0, plan.workspace.data_ptr(),
                                         plan.workspace.numel(), stream.cuda_stream)
     alu = fp32_peak_measured(B)
-    roofline, per_kind = roofline_from_profile(prof, (args.path, args.prec, args.batch, bool(args.hilo),
+    roofline, per_kind = roofline_from_profile(prof, (args.path, args.prec, batch, bool(args.hilo),
                                                       bool(args.hoist)), alu)
-    executed_per_slice = float(prof["flops"].sum()) / S
+    executed_per_slice = float(prof["flops"].sum()) / max(len(mine), 1)
     permute = permute_bandwidth(B, torch, stream)
     # recorded kernels + slice-id uploads (one launch per 256 ids of each batch) + top-k + XEB
-    n_batches = -(-S // args.batch)
-    launches_per_step = prof["n_launches"] + n_batches * (-(-args.batch // 256)) + 2
+    n_batches = -(-len(mine) // batch)
+    launches_per_step = prof["n_launches"] + n_batches * (-(-batch // 256)) + 2
     # complex64 accuracy on the tensor cores: fp16 hi + lo operands, K accumulated
     # one k tile at a time in FP32 (relative L2 8.7e-6 on this workload, the
     # complex64 path's 8.4e-6; tests/test_gpu_precision.py holds it to 1e-5)
     fine_value = None
     if args.prec != "c64" and not args.no_c64:
-        planf = E.Plan(prep.tn, prep.tree, prec="fp16", max_slice_batch=args.batch,
+        planf = E.Plan(prep.tn, prep.tree, prec="fp16", max_slice_batch=batch,
                        flags=B.TN_FLAG_HILO | B.TN_FLAG_FINE_ACC | hoist)
         for _ in range(2):
             planf.contract(ids, out=amps)
@@ -553,7 +569,7 @@ def run_ours(args):
                          "those TN_FLAG_HILO_AUTO picks for relative L2 <= 3e-3 on the calibration batch "
                          "(contraction only)"}
         for name, fl, kw in (("all_steps", B.TN_FLAG_HILO, {}), ("auto", B.TN_FLAG_HILO_AUTO, {"hilo_tol": 3e-3})):
-            pl = E.Plan(prep.tn, prep.tree, prec="bf16", max_slice_batch=args.batch, flags=fl | hoist, **kw)
+            pl = E.Plan(prep.tn, prep.tree, prec="bf16", max_slice_batch=batch, flags=fl | hoist, **kw)
             for _ in range(2):
                 pl.contract(ids, out=amps)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -579,7 +595,7 @@ def run_ours(args):
                          "is chosen (contraction only)", "candidates": rows}
     c64_value = None
     if args.prec != "c64" and not args.no_c64:
-        plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=args.batch, flags=hoist)
+        plan64 = E.Plan(prep.tn, prep.tree, prec="c64", max_slice_batch=batch, flags=hoist)
         for _ in range(3):
             plan64.contract(ids, out=amps)
         torch.cuda.synchronize()

@@ -143,3 +143,17 @@ def test_clock_samples_filtered_to_timed_regions():
     c.windows = [(t0 + 0.16, t0 + 0.17)]
     s = c.summary()
     assert s["samples"] == 1 and s["sm_mhz"] == 900 and "no sample" in s["note"]
+
+
+def test_bench_slice_batch_per_rank_share():
+    # with the slices split over N ranks each rank runs its share as one batch
+    # (the power of two that holds it); with blocks split, the full batch
+    import argparse
+    import bench
+    args = argparse.Namespace(batch=64, partition="slices", prec="fp16", hilo=False, hoist=False,
+                              autotune=False, serial_graph=False, path="time")
+    got = {n: bench.bench_config(args, n)["slice_batch"] for n in (1, 2, 3, 4, 8)}
+    assert got == {1: 64, 2: 32, 3: 32, 4: 16, 8: 8}
+    args.partition = "blocks"
+    assert bench.bench_config(args, 8)["slice_batch"] == 64
+    assert bench.bench_config(args, 8)["parallelism"].startswith("8 independent block sets")
